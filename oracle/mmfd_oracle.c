@@ -1,0 +1,518 @@
+/*
+ * mmfd_oracle.c -- plain, slow, FP64 CPU oracle for the explicit MMFD update
+ * (Shi, Du and Chai, "Equilibrium-distribution-function based mesoscopic
+ * finite-difference methods for PDEs", arXiv 2505.17057).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py may load this library.
+ * It shares no code, header, table or constant with the CUDA path.
+ *
+ * What it computes, per step and per node x (periodic box):
+ *   Sec. II, Eq. (2-1)/(2-2):  phi(x) = sum_j sum_{k,q} a_kq f_j^eq(x + k c_j dt, t + q dt)
+ *   NSE, Eq. (2-4): rho with {a_kq}, (rho u) = sum_j c_j sum_{k,q} abar_kq f_j^eq(...)
+ *   two-level explicit: q = -1 only (Eq. (2-2-2)); three-level explicit:
+ *   Eq. (3layerMMFD-1) with a_k on level t and ahat_k on level t - dt.
+ * Three algebraically identical forms are provided:
+ *   form 1: MesoFD, Eq. (2-1): f_j(x) first, then the moments Eq. (2-1-1);
+ *   form 2: direct MMFD, Eq. (2-2) / (2-4) / (3layerMMFD-1);
+ *   form 3: central MMFD, Eq. (2-2-1) / (2-4-1) with the even/odd split Eq. (2-5)
+ *           and the central differences Eq. (CentralFD).
+ * EDFs: general quadratic form Eq. (3-3)/(3-4) with direction-dependent
+ * c_s,alpha^2 = d_0alpha c_alpha^2 (App. A); linear CDE Eq. (TforMMFD-0);
+ * NCDE Eq. (NCDEfeq); incompressible NSE He-Luo form of Remark 4.
+ * Lattices: rD2Q5I, rD2Q9, rD3Q7, rD3Q19 of App. A.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no SIMD
+ * intrinsics; summation order fixed: levels t then t - dt, k ascending,
+ * j ascending).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_D2Q5 = 0, OR_D2Q9 = 1, OR_D3Q7 = 2, OR_D3Q19 = 3 };
+enum { OR_LCDE = 0, OR_NCDE = 1, OR_NSE = 2 };
+enum { OR_FORM_MESOFD = 1, OR_FORM_MMFD = 2, OR_FORM_CENTRAL = 3 };
+enum { OR_OK = 0, OR_EARG = -1 };
+
+#define OR_QMAX 19
+
+/* Problem statement in the paper's notation. */
+typedef struct {
+    int lattice;        /* OR_D2Q5 ... OR_D3Q19 */
+    int pde;            /* OR_LCDE, OR_NCDE, OR_NSE */
+    int levels;         /* 2 or 3 */
+    int n[3];           /* nx, ny, nz (nz = 1 in 2D) */
+    double c[3];        /* c_alpha = dx_alpha / dt (App. A) */
+    double d0[3];       /* d_0alpha = c_salpha^2 / c_alpha^2 (App. A) */
+    double a[3];        /* a_k on level t (two-level: a_{k,-1}), k = -1, 0, 1 at index k + 1 */
+    double ahat[3];     /* a_k on level t - dt (three-level only) */
+    double abar[3];     /* NSE momentum set on level t, Eq. (2-4) */
+    double abarhat[3];  /* NSE momentum set on level t - dt */
+    double u[3];        /* LCDE: B = phi u, Eq. (TforMMFD-0) */
+    double Cmat[9];     /* LCDE: C = phi Cmat, Cmat = c_s^2 (beta D0 - I) + lambda u u (Eq. (TforMMFD-0)) */
+    double flux[12];    /* NCDE: B_alpha(phi) = sum_{p=0}^{3} flux[4 alpha + p] phi^p */
+    double m2[5];       /* NCDE: isotropic second moment M2(phi) = sum_{p=0}^{4} m2[p] phi^p */
+    double rho0;        /* NSE: He-Luo reference density (Remark 4) */
+} or_problem;
+
+/* Lattice tables of App. A, with the scalings of Eq. (3-4) folded in once. */
+typedef struct {
+    int dim, b;
+    int e[OR_QMAX][3];      /* integer directions, c_j = (e_j1 c_1, e_j2 c_2, e_j3 c_3) */
+    double w[OR_QMAX];      /* omega_j */
+    double cj[OR_QMAX][3];  /* c_j components */
+    int opp[OR_QMAX];       /* jbar: c_jbar = -c_j */
+    double c[3], cs2[3];
+} or_lat;
+
+static void set_e(or_lat* L, int j, int x, int y, int z) {
+    L->e[j][0] = x; L->e[j][1] = y; L->e[j][2] = z;
+}
+
+/* App. A: velocity sets and weights as functions of d_0alpha.
+ * rD3Q19: the x-z block of Eq. (D3Q19b) prints (1,0,1),(-1,0,-1),(-1,0,-1),(1,0,1);
+ * read as the four distinct diagonals (1,0,1),(-1,0,1),(-1,0,-1),(1,0,-1)
+ * (the printed set repeats two velocities and misses two). */
+static int lat_init(or_lat* L, int lattice, const double d0[3], const double c[3]) {
+    memset(L, 0, sizeof(*L));
+    double d1 = d0[0], d2 = d0[1], d3 = d0[2];
+    switch (lattice) {
+    case OR_D2Q5:
+        L->dim = 2; L->b = 5;
+        set_e(L, 0, 0, 0, 0); set_e(L, 1, 1, 0, 0); set_e(L, 2, 0, 1, 0);
+        set_e(L, 3, -1, 0, 0); set_e(L, 4, 0, -1, 0);
+        L->w[0] = 1.0 - d1 - d2;
+        L->w[1] = L->w[3] = d1 / 2.0;
+        L->w[2] = L->w[4] = d2 / 2.0;
+        break;
+    case OR_D2Q9:
+        L->dim = 2; L->b = 9;
+        set_e(L, 0, 0, 0, 0); set_e(L, 1, 1, 0, 0); set_e(L, 2, 0, 1, 0);
+        set_e(L, 3, -1, 0, 0); set_e(L, 4, 0, -1, 0); set_e(L, 5, 1, 1, 0);
+        set_e(L, 6, -1, 1, 0); set_e(L, 7, -1, -1, 0); set_e(L, 8, 1, -1, 0);
+        L->w[0] = (1.0 - d1) * (1.0 - d2);
+        L->w[1] = L->w[3] = d1 * (1.0 - d2) / 2.0;
+        L->w[2] = L->w[4] = (1.0 - d1) * d2 / 2.0;
+        L->w[5] = L->w[6] = L->w[7] = L->w[8] = d1 * d2 / 4.0;
+        break;
+    case OR_D3Q7:
+        L->dim = 3; L->b = 7;
+        set_e(L, 0, 0, 0, 0); set_e(L, 1, 1, 0, 0); set_e(L, 2, 0, 1, 0); set_e(L, 3, 0, 0, 1);
+        set_e(L, 4, -1, 0, 0); set_e(L, 5, 0, -1, 0); set_e(L, 6, 0, 0, -1);
+        L->w[0] = 1.0 - d1 - d2 - d3;
+        L->w[1] = L->w[4] = d1 / 2.0;
+        L->w[2] = L->w[5] = d2 / 2.0;
+        L->w[3] = L->w[6] = d3 / 2.0;
+        break;
+    case OR_D3Q19:
+        L->dim = 3; L->b = 19;
+        set_e(L, 0, 0, 0, 0); set_e(L, 1, 1, 0, 0); set_e(L, 2, 0, 1, 0); set_e(L, 3, 0, 0, 1);
+        set_e(L, 4, -1, 0, 0); set_e(L, 5, 0, -1, 0); set_e(L, 6, 0, 0, -1);
+        set_e(L, 7, 1, 1, 0); set_e(L, 8, -1, 1, 0); set_e(L, 9, -1, -1, 0); set_e(L, 10, 1, -1, 0);
+        set_e(L, 11, 1, 0, 1); set_e(L, 12, -1, 0, 1); set_e(L, 13, -1, 0, -1); set_e(L, 14, 1, 0, -1);
+        set_e(L, 15, 0, 1, 1); set_e(L, 16, 0, -1, 1); set_e(L, 17, 0, -1, -1); set_e(L, 18, 0, 1, -1);
+        L->w[0] = 1.0 - d1 - d2 - d3 + d1 * d2 + d1 * d3 + d2 * d3;
+        L->w[1] = L->w[4] = d1 * (1.0 - d2 - d3) / 2.0;
+        L->w[2] = L->w[5] = d2 * (1.0 - d1 - d3) / 2.0;
+        L->w[3] = L->w[6] = d3 * (1.0 - d1 - d2) / 2.0;
+        for (int j = 7; j <= 10; ++j) L->w[j] = d1 * d2 / 4.0;
+        for (int j = 11; j <= 14; ++j) L->w[j] = d1 * d3 / 4.0;
+        for (int j = 15; j <= 18; ++j) L->w[j] = d2 * d3 / 4.0;
+        break;
+    default:
+        return OR_EARG;
+    }
+    for (int a = 0; a < 3; ++a) {
+        L->c[a] = (a < L->dim) ? c[a] : 0.0;
+        L->cs2[a] = (a < L->dim) ? d0[a] * c[a] * c[a] : 0.0;
+    }
+    for (int j = 0; j < L->b; ++j) {
+        for (int a = 0; a < 3; ++a) L->cj[j][a] = L->e[j][a] * L->c[a];
+        L->opp[j] = -1;
+        for (int i = 0; i < L->b; ++i)
+            if (L->e[i][0] == -L->e[j][0] && L->e[i][1] == -L->e[j][1] && L->e[i][2] == -L->e[j][2])
+                L->opp[j] = i;
+        if (L->opp[j] < 0) return OR_EARG;
+    }
+    return OR_OK;
+}
+
+/* Eq. (3-3)/(3-4): g_j^eq(A, B, C) = omega_j (A + ctilde_j . B + Qtilde_j : C), with
+ *   ctilde_ja = c_ja / cs_a^2,
+ *   Qtilde_jaa = (c_ja^2 - cs_a^2) / (cs_a^2 (c_a^2 - cs_a^2)),
+ *   Qtilde_jab = c_ja c_jb / (2 cs_a^2 cs_b^2)   (a != b),
+ * where Q_j = c_j c_j - Delta^(2), Delta^(2) = diag(cs_a^2) (the printed diag{c_sa}
+ * is read as diag{c_sa^2}, the only reading under which Eq. (3-5) holds).
+ * The double contraction Qtilde : C runs over all ordered pairs (a, b). */
+static double geq_j(const or_lat* L, int j, double A, const double B[3], const double C[9]) {
+    double s = A;
+    for (int a = 0; a < L->dim; ++a)
+        s += L->cj[j][a] * B[a] / L->cs2[a];
+    for (int a = 0; a < L->dim; ++a) {
+        for (int b = 0; b < L->dim; ++b) {
+            double q;
+            if (a == b)
+                q = (L->cj[j][a] * L->cj[j][a] - L->cs2[a]) /
+                    (L->cs2[a] * (L->c[a] * L->c[a] - L->cs2[a]));
+            else
+                q = L->cj[j][a] * L->cj[j][b] / (2.0 * L->cs2[a] * L->cs2[b]);
+            s += q * C[3 * a + b];
+        }
+    }
+    return L->w[j] * s;
+}
+
+static int nfields(const or_problem* P, const or_lat* L) {
+    return (P->pde == OR_NSE) ? 1 + L->dim : 1;
+}
+
+static double poly(const double* p, int deg, double x) {
+    double r = 0.0;
+    for (int i = deg; i >= 0; --i) r = r * x + p[i];
+    return r;
+}
+
+/* Arguments (A, B, C) of the EDF for each PDE, from the stored fields at one node. */
+static void edf_args(const or_problem* P, const or_lat* L, const double* f,
+                     double* A, double B[3], double C[9]) {
+    memset(B, 0, 3 * sizeof(double));
+    memset(C, 0, 9 * sizeof(double));
+    if (P->pde == OR_LCDE) {
+        /* Eq. (TforMMFD-0): f_j^eq = phi ubar_j = g_j^eq(phi, phi u, phi C). */
+        double phi = f[0];
+        *A = phi;
+        for (int a = 0; a < L->dim; ++a) B[a] = phi * P->u[a];
+        for (int k = 0; k < 9; ++k) C[k] = phi * P->Cmat[k];
+    } else if (P->pde == OR_NCDE) {
+        /* Eq. (NCDEfeq): f^eq = g^eq(phi, B(phi), beta cs^2 D + C - cs^2 phi I), with the
+         * second-moment target beta cs^2 D + C = M2(phi) I (isotropic, no correction). */
+        double phi = f[0];
+        *A = phi;
+        for (int a = 0; a < L->dim; ++a) B[a] = poly(&P->flux[4 * a], 3, phi);
+        double m2 = poly(P->m2, 4, phi);
+        for (int a = 0; a < L->dim; ++a) C[3 * a + a] = m2 - L->cs2[a] * phi;
+    } else {
+        /* Remark 4 (He-Luo): f^eq = g^eq(rho, rho0 u, rho0 u u); fields are (rho, u[dim]). */
+        *A = f[0];
+        for (int a = 0; a < L->dim; ++a) B[a] = P->rho0 * f[1 + a];
+        for (int a = 0; a < L->dim; ++a)
+            for (int b = 0; b < L->dim; ++b) C[3 * a + b] = P->rho0 * f[1 + a] * f[1 + b];
+    }
+}
+
+/* f_j^eq at node index idx of a level (SoA fields, each N = nx ny nz values). */
+static double feq_at(const or_problem* P, const or_lat* L, const double* lev, long long N,
+                     long long idx, int j) {
+    double f[4], A, B[3], C[9];
+    int nf = nfields(P, L);
+    for (int i = 0; i < nf; ++i) f[i] = lev[i * N + idx];
+    edf_args(P, L, f, &A, B, C);
+    return geq_j(L, j, A, B, C);
+}
+
+static long long wrap(long long i, long long n) {
+    long long r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Index of node (x + k e_j) with periodic wrap in every direction. */
+static long long shifted(const or_problem* P, const or_lat* L, long long idx, int j, int k) {
+    long long nx = P->n[0], ny = P->n[1], nz = P->n[2];
+    long long x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+    x = wrap(x + (long long)k * L->e[j][0], nx);
+    y = wrap(y + (long long)k * L->e[j][1], ny);
+    z = wrap(z + (long long)k * L->e[j][2], nz);
+    return (z * ny + y) * nx + x;
+}
+
+/* Coefficients of level index l (0: t, 1: t - dt) for the scalar / rho moment and for the
+ * momentum moment. */
+static const double* coef(const or_problem* P, int l) { return l == 0 ? P->a : P->ahat; }
+static const double* coefbar(const or_problem* P, int l) { return l == 0 ? P->abar : P->abarhat; }
+
+/* One node, form 2 (direct MMFD): Eq. (2-2) / (2-4) / (3layerMMFD-1). */
+static void node_mmfd(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
+                      long long idx, double* out) {
+    int nf = nfields(P, L);
+    double acc[4] = {0, 0, 0, 0};
+    for (int l = 0; l < P->levels - 1; ++l) {
+        const double* a = coef(P, l);
+        const double* ab = coefbar(P, l);
+        for (int k = -1; k <= 1; ++k) {
+            for (int j = 0; j < L->b; ++j) {
+                double fe = feq_at(P, L, levs[l], N, shifted(P, L, idx, j, k), j);
+                acc[0] += a[k + 1] * fe;
+                if (P->pde == OR_NSE)
+                    for (int d = 0; d < L->dim; ++d) acc[1 + d] += ab[k + 1] * L->cj[j][d] * fe;
+            }
+        }
+    }
+    out[0] = acc[0];
+    for (int d = 1; d < nf; ++d) out[d] = acc[d] / P->rho0;
+}
+
+/* One node, form 1 (MesoFD): Eq. (2-1) gives f_j(x) per direction, then Eq. (2-1-1)
+ * (and, for the NSE, the double-distribution moments Eq. (2-4)). */
+static void node_mesofd(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
+                        long long idx, double* out) {
+    int nf = nfields(P, L);
+    double fj[OR_QMAX], fbarj[OR_QMAX];
+    for (int j = 0; j < L->b; ++j) {
+        double s = 0.0, sb = 0.0;
+        for (int l = 0; l < P->levels - 1; ++l) {
+            const double* a = coef(P, l);
+            const double* ab = coefbar(P, l);
+            for (int k = -1; k <= 1; ++k) {
+                double fe = feq_at(P, L, levs[l], N, shifted(P, L, idx, j, k), j);
+                s += a[k + 1] * fe;
+                sb += ab[k + 1] * fe;
+            }
+        }
+        fj[j] = s;
+        fbarj[j] = sb;
+    }
+    double phi = 0.0, m[3] = {0, 0, 0};
+    for (int j = 0; j < L->b; ++j) {
+        phi += fj[j];
+        for (int d = 0; d < L->dim; ++d) m[d] += L->cj[j][d] * fbarj[j];
+    }
+    out[0] = phi;
+    for (int d = 1; d < nf; ++d) out[d] = m[d - 1] / P->rho0;
+}
+
+/* Even and odd parts, Eq. (2-5): g_j^+ = (g_j + g_jbar)/2, g_j^- = (g_j - g_jbar)/2. */
+static double feq_even(const or_problem* P, const or_lat* L, const double* lev, long long N,
+                       long long idx, int j) {
+    return 0.5 * (feq_at(P, L, lev, N, idx, j) + feq_at(P, L, lev, N, idx, L->opp[j]));
+}
+static double feq_odd(const or_problem* P, const or_lat* L, const double* lev, long long N,
+                      long long idx, int j) {
+    return 0.5 * (feq_at(P, L, lev, N, idx, j) - feq_at(P, L, lev, N, idx, L->opp[j]));
+}
+
+/* One node, form 3 (central MMFD), Eq. (2-2-1) and Eq. (2-4-1), m_q = 1:
+ *   phi = sum_q [ (sum_k a_kq) phi(x) + 1/2 sum_j ( a+_1q D2_j f^eq,+ + a-_1q D1_j f^eq,- ) ]
+ *   (rho u) = sum_q [ (sum_k abar_kq) (rho u)(x)
+ *                     + 1/2 sum_j c_j ( abar+_1q D2_j f^eq,- + abar-_1q D1_j f^eq,+ ) ]
+ * with a+_1 = a_1 + a_{-1}, a-_1 = a_1 - a_{-1} (Eq. (2-1-FD1-0)) and the central
+ * differences of Eq. (CentralFD).  phi(x) and (rho u)(x) are the zeroth and first
+ * moments of f^eq at x (Eq. (3-5)). */
+static void node_central(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
+                         long long idx, double* out) {
+    int nf = nfields(P, L);
+    double acc[4] = {0, 0, 0, 0};
+    for (int l = 0; l < P->levels - 1; ++l) {
+        const double* lev = levs[l];
+        const double* a = coef(P, l);
+        const double* ab = coefbar(P, l);
+        double A0 = a[0] + a[1] + a[2];
+        double Ab0 = ab[0] + ab[1] + ab[2];
+        double ap = a[2] + a[0], am = a[2] - a[0];
+        double abp = ab[2] + ab[0], abm = ab[2] - ab[0];
+        double M0 = 0.0, M1[3] = {0, 0, 0};
+        for (int j = 0; j < L->b; ++j) {
+            double fe = feq_at(P, L, lev, N, idx, j);
+            M0 += fe;
+            for (int d = 0; d < L->dim; ++d) M1[d] += L->cj[j][d] * fe;
+        }
+        acc[0] += A0 * M0;
+        for (int d = 0; d < L->dim; ++d) acc[1 + d] += Ab0 * M1[d];
+        for (int j = 0; j < L->b; ++j) {
+            long long ip = shifted(P, L, idx, j, 1), im = shifted(P, L, idx, j, -1);
+            double ep = feq_even(P, L, lev, N, ip, j), e0 = feq_even(P, L, lev, N, idx, j),
+                   em = feq_even(P, L, lev, N, im, j);
+            double op = feq_odd(P, L, lev, N, ip, j), o0 = feq_odd(P, L, lev, N, idx, j),
+                   om = feq_odd(P, L, lev, N, im, j);
+            double d2e = ep - 2.0 * e0 + em, d1o = op - om;
+            double d2o = op - 2.0 * o0 + om, d1e = ep - em;
+            acc[0] += 0.5 * (ap * d2e + am * d1o);
+            if (P->pde == OR_NSE)
+                for (int d = 0; d < L->dim; ++d)
+                    acc[1 + d] += 0.5 * L->cj[j][d] * (abp * d2o + abm * d1e);
+        }
+    }
+    out[0] = acc[0];
+    for (int d = 1; d < nf; ++d) out[d] = acc[d] / P->rho0;
+}
+
+typedef void (*node_fn)(const or_problem*, const or_lat*, const double* [2], long long, long long,
+                        double*);
+
+static node_fn pick(int form) {
+    switch (form) {
+    case OR_FORM_MESOFD: return node_mesofd;
+    case OR_FORM_MMFD: return node_mmfd;
+    case OR_FORM_CENTRAL: return node_central;
+    default: return 0;
+    }
+}
+
+static int check(const or_problem* P, or_lat* L) {
+    if (!P) return OR_EARG;
+    if (P->levels != 2 && P->levels != 3) return OR_EARG;
+    if (P->pde < OR_LCDE || P->pde > OR_NSE) return OR_EARG;
+    if (lat_init(L, P->lattice, P->d0, P->c) != OR_OK) return OR_EARG;
+    for (int a = 0; a < 3; ++a) if (P->n[a] < 1) return OR_EARG;
+    if (L->dim == 2 && P->n[2] != 1) return OR_EARG;
+    if (P->pde == OR_NSE && P->rho0 == 0.0) return OR_EARG;
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------- exported API */
+
+int or_lattice(int lattice, const double d0[3], const double c[3], int* dim, int* b, int* e,
+               double* w, double* cs2) {
+    or_lat L;
+    if (lat_init(&L, lattice, d0, c) != OR_OK) return OR_EARG;
+    *dim = L.dim;
+    *b = L.b;
+    for (int j = 0; j < L.b; ++j) {
+        for (int a = 0; a < 3; ++a) e[3 * j + a] = L.e[j][a];
+        w[j] = L.w[j];
+    }
+    for (int a = 0; a < 3; ++a) cs2[a] = L.cs2[a];
+    return OR_OK;
+}
+
+/* All b values of g^eq(A, B, C), Eq. (3-3). */
+int or_geq(int lattice, const double d0[3], const double c[3], double A, const double B[3],
+           const double C[9], double* g) {
+    or_lat L;
+    if (lat_init(&L, lattice, d0, c) != OR_OK) return OR_EARG;
+    for (int j = 0; j < L.b; ++j) g[j] = geq_j(&L, j, A, B, C);
+    return OR_OK;
+}
+
+/* All b values of the problem's f^eq at a single node's stored fields. */
+int or_feq(const or_problem* P, const double* fields, double* feq) {
+    or_lat L;
+    if (check(P, &L) != OR_OK) return OR_EARG;
+    double A, B[3], C[9];
+    edf_args(P, &L, fields, &A, B, C);
+    for (int j = 0; j < L.b; ++j) feq[j] = geq_j(&L, j, A, B, C);
+    return OR_OK;
+}
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* One step: out (nf x N, SoA) from lev_n (level t) and lev_nm1 (level t - dt; ignored when
+ * levels == 2). */
+int or_step(const or_problem* P, int form, const double* lev_n, const double* lev_nm1, double* out) {
+    or_lat L;
+    if (check(P, &L) != OR_OK) return OR_EARG;
+    node_fn fn = pick(form);
+    if (!fn) return OR_EARG;
+    if (P->levels == 3 && !lev_nm1) return OR_EARG;
+    const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+    const int nf = nfields(P, &L);
+    const double* levs[2] = {lev_n, lev_nm1};
+#pragma omp parallel for schedule(static)
+    for (long long idx = 0; idx < N; ++idx) {
+        double o[4];
+        fn(P, &L, levs, N, idx, o);
+        for (int i = 0; i < nf; ++i) out[i * N + idx] = o[i];
+    }
+    return OR_OK;
+}
+
+/* The step's outputs at a list of node indices only (out is count x nf, node-major). */
+int or_step_nodes(const or_problem* P, int form, const double* lev_n, const double* lev_nm1,
+                  const long long* nodes, long long count, double* out) {
+    or_lat L;
+    if (check(P, &L) != OR_OK) return OR_EARG;
+    node_fn fn = pick(form);
+    if (!fn) return OR_EARG;
+    const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+    const int nf = nfields(P, &L);
+    const double* levs[2] = {lev_n, lev_nm1};
+    for (long long i = 0; i < count; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= N) return OR_EARG;
+    }
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < count; ++i) {
+        double o[4];
+        fn(P, &L, levs, N, nodes[i], o);
+        for (int f = 0; f < nf; ++f) out[i * nf + f] = o[f];
+    }
+    return OR_OK;
+}
+
+/* nsteps steps in place: on return lev_n holds level t + nsteps dt and lev_nm1 (three-level)
+ * the level before it. */
+int or_run(const or_problem* P, int form, long long nsteps, double* lev_n, double* lev_nm1) {
+    or_lat L;
+    if (check(P, &L) != OR_OK) return OR_EARG;
+    const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+    const int nf = nfields(P, &L);
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)(nf * N));
+    if (!tmp) return OR_EARG;
+    for (long long s = 0; s < nsteps; ++s) {
+        int rc = or_step(P, form, lev_n, lev_nm1, tmp);
+        if (rc != OR_OK) { free(tmp); return rc; }
+        if (P->levels == 3) memcpy(lev_nm1, lev_n, sizeof(double) * (size_t)(nf * N));
+        memcpy(lev_n, tmp, sizeof(double) * (size_t)(nf * N));
+    }
+    free(tmp);
+    return OR_OK;
+}
+
+/* Independent lattice-Boltzmann check (Sec. III.C, special case (1)): LBGK with tau = 1,
+ * written as collide-then-stream on explicit distribution arrays:
+ *   f_j(x + c_j dt, t + dt) = f_j(x, t) - (f_j - f_j^eq)/tau |_{tau = 1} = f_j^eq(x, t),
+ * with f^eq built from the moments of f (phi = sum f; NSE: rho = sum f, rho0 u = sum c f).
+ * Two-level problems only; the a's of P are not used.  Fields in place. */
+int or_lbgk_tau1_run(const or_problem* P, long long nsteps, double* fields) {
+    or_lat L;
+    if (check(P, &L) != OR_OK) return OR_EARG;
+    const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+    const int nf = nfields(P, &L);
+    double* f = (double*)malloc(sizeof(double) * (size_t)(L.b * N));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(L.b * N));
+    if (!f || !g) { free(f); free(g); return OR_EARG; }
+    /* initial populations at equilibrium */
+    for (long long x = 0; x < N; ++x)
+        for (int j = 0; j < L.b; ++j) f[j * N + x] = feq_at(P, &L, fields, N, x, j);
+    for (long long s = 0; s < nsteps; ++s) {
+        /* collide (tau = 1): post-collision populations are the equilibria of the moments of f */
+        for (long long x = 0; x < N; ++x) {
+            double m0 = 0.0, m1[3] = {0, 0, 0};
+            for (int j = 0; j < L.b; ++j) {
+                m0 += f[j * N + x];
+                for (int d = 0; d < L.dim; ++d) m1[d] += L.cj[j][d] * f[j * N + x];
+            }
+            double loc[4];
+            loc[0] = m0;
+            for (int d = 0; d < L.dim; ++d) loc[1 + d] = m1[d] / P->rho0;
+            double A, B[3], C[9];
+            edf_args(P, &L, loc, &A, B, C);
+            for (int j = 0; j < L.b; ++j) g[j * N + x] = geq_j(&L, j, A, B, C);
+        }
+        /* stream: population j moves from x to x + e_j */
+        for (long long x = 0; x < N; ++x)
+            for (int j = 0; j < L.b; ++j) f[j * N + shifted(P, &L, x, j, 1)] = g[j * N + x];
+    }
+    for (long long x = 0; x < N; ++x) {
+        double m0 = 0.0, m1[3] = {0, 0, 0};
+        for (int j = 0; j < L.b; ++j) {
+            m0 += f[j * N + x];
+            for (int d = 0; d < L.dim; ++d) m1[d] += L.cj[j][d] * f[j * N + x];
+        }
+        fields[x] = m0;
+        for (int d = 1; d < nf; ++d) fields[d * N + x] = m1[d - 1] / P->rho0;
+    }
+    free(f);
+    free(g);
+    return OR_OK;
+}
