@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit MMFD step on one GB300 (or N replicas under torchrun).
+
+Workload (default): tgv2d_4096 -- 4096x4096 periodic He-Luo NSE, D2Q9, two-level MMFD,
+Taylor-Green vortex (Re 100), FP32 storage.  One bench step = one MMFD time step over the
+whole grid (16.8M lattice-node updates).  The level buffers (201 MB each) exceed the 129 MB
+L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline per MMFD step; served p50/p99 latency vs plain FP32"
+UNIT = "MLUPS"
+SMI_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_17057_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"{workload}:{kernel}")
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={SMI_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.flush()
+        self.fh.seek(0)
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.fh.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.fh.name)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "samples": len(sms), "reasons": sorted(reasons)}
+
+
+class OracleTimer:
+    """The FP64 CPU oracle (as it stands) on the bench workload, timed on node-range samples."""
+
+    def __init__(self, workload: str):
+        from oracle import oracle as orc
+        from oracle import params as P
+        from paper_2505_17057_gb300 import configs
+        self.cores = os.cpu_count() or 1
+        orc.set_threads(self.cores)
+        if not workload.startswith("tgv2d"):
+            raise ValueError(workload)
+        n = int(workload.split("_")[1])
+        desc, fields, _ = configs.tgv2d_4096(n=n)
+        prob = P.problem_nse("D2Q9", 2, [n, n], 1.0, [1.0, 1.0], desc["a"], desc["abar"])
+        self.n = n
+        self.sampler = orc.NodeSampler(prob, fields)
+        self.sampler.run(0, 4 * n)  # warm caches / threads
+
+    def time_rows(self, rows: int, row0: int = 0):
+        t0 = time.perf_counter()
+        self.sampler.run(row0 * self.n, rows * self.n)
+        return time.perf_counter() - t0
+
+    def rows_for(self, seconds: float) -> int:
+        t = self.time_rows(16)
+        return max(1, min(self.n, int(16 * seconds / max(t, 1e-6))))
+
+    def measure(self, seconds: float):
+        rows = self.rows_for(seconds)
+        t = self.time_rows(rows, row0=self.n // 3)
+        mlups = rows * self.n / t / 1e6
+        sample = (f"rows {self.n // 3}..{self.n // 3 + rows - 1} ({rows * self.n} nodes) of one MMFD step of the "
+                  f"{self.n}x{self.n} grid, direct form, {self.cores} OpenMP threads")
+        return mlups, sample
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    timer = OracleTimer(args.workload)
+    n = timer.n
+    rows = timer.rows_for(0.25)
+    vals = []
+    t_all = 0.0
+    for i in range(args.warmup + args.steps):
+        t = timer.time_rows(rows, row0=(i * rows) % n)
+        if i >= args.warmup:
+            vals.append(rows * n / t / 1e6)
+            t_all += t
+    value = args.steps * rows * n / t_all / 1e6
+    sample = (f"{rows} rows ({rows * n} nodes) of the {n}x{n} grid per step, direct form, "
+              f"{timer.cores} OpenMP threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": n * n / value / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "grid": [n, n], "lattice": "D2Q9",
+                                              "pde": "NSE (He-Luo)", "levels": 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2505_17057_gb300 import configs, mmfd
+
+    n = int(args.workload.split("_")[1])
+    desc_kw, fields, _ = configs.tgv2d_4096(n=n, storage=args.storage)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        d = mmfd.make_desc(**desc_kw, temporal_depth=args.depth)
+        s = mmfd.Solver(d, stream=stream)
+        s.set_fields(fields)
+        info = s.get_info()
+        depth = max(1, info.temporal_depth)
+        nodes = n * n
+        bytes_per_lu = info.bytes_per_lu
+
+        def barrier():
+            if ws > 1:
+                torch.distributed.barrier()
+
+        # warm-up
+        s.step(args.warmup * depth)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            s.step(depth)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        total_ms = t_start.elapsed_time(t_end)
+        launch_ms = [a.elapsed_time(b) for a, b in ev]
+        if ws > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        steps_done = args.steps * depth
+        ms_per_step = total_ms / steps_done
+        value = ws * nodes * steps_done / (total_ms / 1e3) / 1e6
+
+        # roofline of the dominant (only) kernel: compulsory bytes per launch / launch time
+        peak, peak_kind = measured_peaks()
+        avg_launch_s = statistics.mean(launch_ms) / 1e3
+        alg_bytes = bytes_per_lu * nodes * depth
+        achieved = alg_bytes / avg_launch_s / 1e9
+        kernel_name = "k_march2d" if info.temporal_depth <= 1 else "k_tblock2d"
+        traffic = traffic_from_profile(kernel_name, args.workload)
+
+        # end to end through the public API: every step uploads the level from pinned host memory,
+        # advances it, and reads back the FP64 field sums (the step's diagnostic result)
+        e2e_steps = max(3, min(args.steps, 20))
+        pinned = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory() for f in fields]
+        host_ptrs = [p.data_ptr() for p in pinned]
+        h2d = sum(p.numel() * 4 for p in pinned)
+        d2h = 8 * len(pinned)
+        for _ in range(2):
+            mmfd.mmfd_set_fields(s.h, 0, host_ptrs, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
+            s.step(1)
+            s.reduce(mmfd.MMFD_RED_SUM)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            mmfd.mmfd_set_fields(s.h, 0, host_ptrs, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
+            s.step(1)
+            s.reduce(mmfd.MMFD_RED_SUM)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_value = ws * nodes * e2e_steps / e2e_s / 1e6
+        s.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16-offset storage, f32 arithmetic",
+                                       "fp64": "f64"}[args.storage],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [n, n], "lattice": "D2Q9", "pde": "NSE (He-Luo)",
+                   "levels": 2, "storage": args.storage, "temporal_depth": depth,
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (3 x 67 MB per level), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": kernel_name, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": args.steps,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        timer = OracleTimer(args.workload)
+        v, sample = timer.measure(10.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv2d_4096")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--depth", type=int, default=1, help="temporal blocking depth (1 = plain step)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,238 @@
+/*
+ * mmfd.h -- C ABI of the GB300 MMFD library (explicit macroscopic finite-difference
+ * form of the EDF-based mesoscopic FD scheme, Shi, Du and Chai, arXiv 2505.17057).
+ *
+ * Every function returns an int status: MMFD_OK (0), MMFD_PENDING (1, poll only) or a
+ * negative MMFD_ERR_* code.  No function throws, aborts or exits.  All device work is
+ * enqueued on the CUDA stream given in the descriptor (or the server's stream) and is
+ * asynchronous unless stated otherwise.
+ *
+ * Layout conventions for user-visible fields: a "level" is nf fields; each field is a
+ * dense nx*ny*nz array, x fastest (index (z*ny + y)*nx + x).  LCDE/NCDE: nf = 1 (phi).
+ * NSE: nf = 1 + dim, in the order (rho, u_x, u_y[, u_z]) (velocity, not momentum).
+ * Internally the library keeps each level in a padded, ghost-celled layout that the
+ * caller never sees.
+ */
+#ifndef MMFD_H
+#define MMFD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define MMFD_OK 0
+#define MMFD_PENDING 1               /* mmfd_poll: request not finished yet */
+#define MMFD_ERR_ARG (-1)            /* malformed descriptor or argument */
+#define MMFD_ERR_UNSUPPORTED (-2)    /* combination not supported (e.g. NSE on D2Q5) */
+#define MMFD_ERR_UNREPRESENTABLE (-3)/* K_xy != 0 on an axis lattice (D2Q5/D3Q7) without MMFD_FLAG_DROP_OFFDIAG */
+#define MMFD_ERR_UNSTABLE (-4)       /* max |lambda| > 1 + 1e-12 on the grid's wave numbers */
+#define MMFD_ERR_OOM (-5)            /* device allocation failed */
+#define MMFD_ERR_ADMISSION (-6)      /* server: footprint exceeds the HBM budget, or no slot */
+#define MMFD_ERR_NONFINITE (-7)      /* a non-finite value was found in the fields */
+#define MMFD_ERR_TIMEOUT (-8)        /* a bounded device wait ran out */
+#define MMFD_ERR_CUDA (-9)           /* CUDA runtime error; text in mmfd_last_error() */
+#define MMFD_ERR_STATE (-10)         /* call not valid in the object's current state */
+
+/* ------------------------------------------------------------------ enums */
+typedef enum { MMFD_LCDE = 0, MMFD_NCDE = 1, MMFD_NSE = 2 } mmfd_pde;
+typedef enum { MMFD_D2Q5 = 0, MMFD_D2Q9 = 1, MMFD_D3Q7 = 2, MMFD_D3Q19 = 3 } mmfd_lattice;
+/* Storage of the level buffers.  BF16: each value stored as bf16(v - ref[field]) and
+ * read back as ref[field] + v; all arithmetic in FP32.  FP64: arithmetic in FP64. */
+typedef enum { MMFD_FP64 = 0, MMFD_FP32 = 1, MMFD_BF16 = 2 } mmfd_storage;
+enum { MMFD_HOST = 0, MMFD_DEVICE = 1 };
+enum { MMFD_DT_F64 = 0, MMFD_DT_F32 = 1 };          /* element type of user buffers */
+enum { MMFD_COEF_EXPLICIT = 0, MMFD_COEF_TARGETS = 1 };
+
+#define MMFD_FLAG_ALLOW_UNSTABLE 0x1u   /* skip the create-time stability rejection */
+#define MMFD_FLAG_DROP_OFFDIAG 0x2u     /* axis lattices: drop K_xy (solve with diag(K)) */
+#define MMFD_FLAG_STOCHASTIC_ROUND 0x4u /* BF16 storage: stochastic instead of nearest rounding */
+
+typedef int (*mmfd_alloc_fn)(size_t bytes, void** ptr, void* ctx);
+typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
+
+/*
+ * Problem descriptor: the paper's statement of the problem (Sec. II, Eq. (2-1)-(2-4);
+ * Sec. III.D, Eq. (LCDE); App. A lattices).  Start from mmfd_desc_init().
+ *
+ *  pde, lattice, levels  PDE, rDdQb lattice, 2 (explicit two-level, Eq. (2-2-2)) or
+ *                        3 (explicit three-level, Eq. (3layerMMFD-1)).
+ *  dim, n[3]             periodic grid (n[2] = 1 in 2D).
+ *  dt, dx[3]             time step and grid spacings; c_alpha = dx_alpha / dt.
+ *  d0[3]                 lattice free parameters d_0alpha = c_salpha^2 / c_alpha^2 (App. A).
+ *                        D2Q9/D3Q19: used as given (mmfd_desc_init sets 1/3).  D2Q5/D3Q7:
+ *                        ignored for the LCDE (derived from K, u, the scheme moments).
+ *  K[3][3], u[3]         LCDE: diffusion tensor alpha D0 and constant velocity (Eq. (LCDE)).
+ *  lambda_bar            LCDE quadratic EDF parameter of Eq. (TforMMFD-0) (default 1).
+ *  flux[3][4]            NCDE: B_alpha(phi) = sum_p flux[alpha][p] phi^p.
+ *  diff[4]               NCDE: isotropic D(phi) = sum_p diff[p] phi^p (div(D grad phi)).
+ *  rho0                  NSE: He-Luo reference density (Remark 4).
+ *  coef_mode             MMFD_COEF_EXPLICIT: a, ahat (level t - dt), abar, abarhat
+ *                        (NSE momentum sets, Eq. (2-4)), each (a_{-1}, a_0, a_1).
+ *                        MMFD_COEF_TARGETS: targets = (a_0, A_10, A_11, A_21, A_22) solved by
+ *                        Eq. (X) (three-level) or a_{-1} = 1 - a_0/2, a_1 = -a_0/2 (two-level,
+ *                        Eq. (LMMFD-2-2); only targets[0] used); targets_bar likewise for the
+ *                        NSE momentum set.
+ *  storage, ref[4]       storage type; BF16 offsets per field (default ref = {rho0 or 0, 0, ..}).
+ *  flags                 MMFD_FLAG_*.
+ *  temporal_depth        steps fused per kernel launch: 0 = autotuned, 1 = none, T >= 2.
+ *  seed                  BF16 stochastic-rounding seed.
+ *  stream                cudaStream_t (NULL = legacy default stream).
+ *  alloc/free_fn/ctx     device allocator for the level buffers (NULL = cudaMalloc/cudaFree).
+ */
+typedef struct {
+    int pde, lattice, levels;
+    int dim;
+    long long n[3];
+    double dt, dx[3];
+    double d0[3];
+    double K[3][3];
+    double u[3];
+    double lambda_bar;
+    double flux[3][4];
+    double diff[4];
+    double rho0;
+    int coef_mode;
+    double a[3], ahat[3], abar[3], abarhat[3];
+    double targets[5], targets_bar[5];
+    int storage;
+    unsigned flags;
+    double ref[4];
+    int temporal_depth;
+    unsigned long long seed;
+    void* stream;
+    mmfd_alloc_fn alloc;
+    mmfd_free_fn free_fn;
+    void* alloc_ctx;
+} mmfd_desc;
+
+/* Derived constants of a created solver (read-only view, for checking and reporting). */
+typedef struct {
+    int nf;                      /* fields per level */
+    int levels_stored;           /* level buffers held on the device */
+    double a[3], ahat[3], abar[3], abarhat[3]; /* resolved coefficients (a_{-1}, a_0, a_1) */
+    double A10, A20, A21, A22;   /* scheme moments, Eq. (4-2-0) / (4-2-00) */
+    double c[3], d0[3], cs2[3];  /* lattice scaling, App. A */
+    double w[19];                /* lattice weights omega_j in App. A order */
+    double Cmat[3][3];           /* LCDE: EDF C per unit phi (Eq. (TforMMFD-0)) */
+    double m2[5];                /* NCDE: second-moment target polynomial M2(phi) */
+    double max_lambda;           /* max |amplification| found by the create-time check (-1: not checked) */
+    double bytes_per_lu;         /* compulsory HBM bytes per lattice update */
+    long long device_bytes;      /* device memory held by the level buffers */
+    int temporal_depth;          /* depth in use */
+    long long steps_done;        /* time levels advanced so far */
+    char kernel[32];             /* name of the step kernel family in use */
+} mmfd_info_t;
+
+typedef struct mmfd_solver mmfd_solver;
+
+/* Fill a descriptor with defaults (D2Q9 LCDE two-level FP32, d0 = 1/3, lambda_bar = 1,
+ * rho0 = 1, targets a_0 = 0).  Host only. */
+int mmfd_desc_init(mmfd_desc* d);
+
+/* Validate the descriptor, resolve the scheme coefficients and EDF constants, run the
+ * create-time stability check (LCDE: exact symbol; NCDE: linearised at phi = 0; NSE:
+ * linearised at rest), and allocate the level buffers.  *out owns all device memory. */
+int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
+
+/* Copy one level into the solver.  level 0 = t_n, level 1 = t_{n-1} (three-level only).
+ * fields: nf pointers, each to nx*ny*nz values of element type dtype (MMFD_DT_*), on the
+ * host (where = MMFD_HOST, pageable or pinned) or device (MMFD_DEVICE).  The data is copied;
+ * pointers are not retained.  Setting level 0 of a three-level solver also sets level 1
+ * to the same values (the equilibrium start) unless level 1 is set afterwards. */
+int mmfd_set_fields(mmfd_solver* s, int level, const void* const* fields, int where, int dtype);
+
+/* Advance nsteps time levels (Eq. (2-2-2) / Eq. (3layerMMFD-1)), asynchronously on the
+ * solver's stream. */
+int mmfd_step(mmfd_solver* s, long long nsteps);
+
+/* Copy one level out (level 0 = current t_n, 1 = t_{n-1}).  out: nf pointers to
+ * nx*ny*nz values of type dtype on host or device.  Host copies are synchronous. */
+int mmfd_fields(mmfd_solver* s, int level, void* const* out, int where, int dtype);
+
+/* Deterministic FP64 reductions of the current level (fixed-order tree, no atomics).
+ * what = MMFD_RED_SUM: out[f] = sum of field f (nf values).
+ * what = MMFD_RED_MAXABS: out[f] = max |field f|.
+ * what = MMFD_RED_NONFINITE: out[0] = number of non-finite values.
+ * Synchronous. */
+enum { MMFD_RED_SUM = 0, MMFD_RED_MAXABS = 1, MMFD_RED_NONFINITE = 2 };
+int mmfd_reduce(mmfd_solver* s, int what, double* out);
+
+/* Error norms of field `field` of the current level against a reference field ref
+ * (nx*ny*nz values, type dtype, host or device): out[0] = sum |v - ref| / sum |ref|
+ * (the paper's GRE, Sec. IV), out[1] = max |v - ref|, out[2] = max |ref|.  FP64,
+ * synchronous. */
+int mmfd_error_norms(mmfd_solver* s, int field, const void* ref, int where, int dtype, double* out);
+
+int mmfd_get_info(const mmfd_solver* s, mmfd_info_t* out);
+int mmfd_set_stream(mmfd_solver* s, void* stream);
+int mmfd_destroy(mmfd_solver* s);
+
+/* Host-only helpers (no GPU needed). */
+/* Eq. (X): (a_0, A_10, A_11, A_21, A_22) -> a = (a_{-1}, a_0, a_1), ahat likewise. */
+int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3]);
+/* Resolve a descriptor's constants without touching the GPU (info filled as by create). */
+int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out);
+
+const char* mmfd_strerror(int status);
+/* Text of the last error on this thread (CUDA error string or validation message). */
+const char* mmfd_last_error(void);
+
+/* ------------------------------------------------------------------ serving
+ * A persistent solve server with continuous batching: requests are admitted while others
+ * run, as slots and HBM budget free up; every scheduler tick advances all admitted requests
+ * of one kernel class in one batched launch (uneven grids packed together), replayed from
+ * captured CUDA graphs.  Requests never share state: each result equals the one the same
+ * request gives alone (bit-identical for the same kernel variant).
+ */
+typedef struct {
+    size_t hbm_budget;       /* bytes of device memory the server may hold for fields */
+    int max_slots;           /* concurrent requests */
+    int steps_per_tick;      /* time steps per scheduler tick */
+    int use_graphs;          /* capture and replay each tick's launches as a CUDA graph */
+    void* stream;            /* cudaStream_t for all server work */
+} mmfd_server_desc;
+
+typedef struct {
+    int status;              /* MMFD_OK or an error of this request */
+    long long steps_done;
+    double submit_s, admit_s, finish_s; /* host monotonic clock, seconds */
+    int nf;
+    long long n[3];
+} mmfd_result;
+
+typedef struct {
+    long long submitted, admitted, finished, rejected;
+    long long lattice_updates;   /* total node updates done */
+    long long ticks, launches, graph_replays;
+    size_t bytes_in_use;
+    int active;
+} mmfd_server_stats;
+
+typedef struct mmfd_server mmfd_server;
+
+int mmfd_server_create(const mmfd_server_desc* desc, mmfd_server** out);
+/* Queue a solve: the descriptor (stream and allocator fields ignored), the initial level
+ * (nf host pointers, MMFD_DT_F64 or F32, copied at submit) and the step count.  Returns
+ * MMFD_ERR_ADMISSION at once if the request could never fit the budget. */
+int mmfd_submit(mmfd_server* s, const mmfd_desc* d, const void* const* init, int dtype,
+                long long nsteps, unsigned long long* ticket);
+/* Drive the scheduler (admit, launch one tick) and report the ticket: MMFD_PENDING while it
+ * runs, MMFD_OK when done (res filled), <0 on error. */
+int mmfd_poll(mmfd_server* s, unsigned long long ticket, mmfd_result* res);
+/* Run the scheduler until every queued request is finished. */
+int mmfd_server_drain(mmfd_server* s);
+/* Copy a finished request's final level (nf pointers, host or device, type dtype). */
+int mmfd_result_fields(mmfd_server* s, unsigned long long ticket, void* const* out, int where, int dtype);
+/* Forget a finished request and free its memory. */
+int mmfd_release(mmfd_server* s, unsigned long long ticket);
+int mmfd_server_get_stats(const mmfd_server* s, mmfd_server_stats* out);
+int mmfd_server_destroy(mmfd_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMFD_H */

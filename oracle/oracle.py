@@ -252,3 +252,27 @@ def lbgk_tau1_run(prob: Problem, level_n, nsteps: int) -> List[np.ndarray]:
     if lib().or_lbgk_tau1_run(C.byref(p), int(nsteps), _dp(b)) != 0:
         raise ValueError("oracle rejected the problem")
     return _unpack(b)
+
+
+class NodeSampler:
+    """Pack one level once, then evaluate the oracle step on contiguous node ranges.
+
+    Used to time the oracle on a bounded sample of a large workload (the per-node work is
+    exactly that of a full step; only the set of nodes is bounded)."""
+
+    def __init__(self, prob: Problem, level_n, level_nm1=None, form: str = "mmfd"):
+        self.prob = prob
+        self.p = prob.to_c()
+        self.bn = _pack(level_n, prob.nf, prob.shape)
+        self.bm = _pack(level_nm1, prob.nf, prob.shape) if level_nm1 is not None else np.zeros_like(self.bn)
+        self.form = FORMS[form]
+        self.N = int(np.prod(prob.shape))
+
+    def run(self, start: int, count: int) -> np.ndarray:
+        idx = (np.arange(count, dtype=np.int64) + int(start)) % self.N
+        out = np.empty((count, self.prob.nf))
+        rc = lib().or_step_nodes(C.byref(self.p), self.form, _dp(self.bn), _dp(self.bm),
+                                 idx.ctypes.data_as(C.POINTER(C.c_longlong)), count, _dp(out))
+        if rc != 0:
+            raise ValueError("oracle rejected the problem")
+        return out

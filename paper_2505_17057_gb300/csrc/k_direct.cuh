@@ -1,0 +1,107 @@
+// k_direct.cuh -- one node per thread MMFD update (any grid shape, any lattice/PDE).
+// Neighbours are read straight from the ghosted layout through the L1/L2 caches; every
+// output is written to its interior slot and its periodic ghost images.
+#pragma once
+
+#include <type_traits>
+
+#include "kernels.h"
+#include "stencil.cuh"
+
+namespace mmfd {
+
+template <int P, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (P < N) {
+        f(std::integral_constant<int, P>{});
+        static_for<P + 1, N>(f);
+    }
+}
+
+template <int LAT, int PDE, int LEVELS, int ST>
+__global__ void __launch_bounds__(256) k_direct(Geom g, const void* __restrict__ in0v,
+                                                const void* __restrict__ in1v, void* __restrict__ outv,
+                                                Coef<typename Storage<ST>::T> cf, StepExtra ex) {
+    using Tr = Storage<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    constexpr int D = lat_dim(LAT);
+    constexpr int NP = lat_npair(LAT);
+    constexpr int NF = pde_nf(PDE, LAT);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long c0 = g.at(x, y, z);
+    T acc[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) acc[i] = T(0);
+
+#pragma unroll
+    for (int l = 0; l < LEVELS - 1; ++l) {
+        const S* in = static_cast<const S*>(l == 0 ? in0v : in1v);
+        if constexpr (PDE == PDE_LCDE) {
+            // f_j^eq = phi ubar_j (Eq. (TforMMFD-0)): the update is a fixed linear stencil.
+            T s = cf.W0[l] * Tr::load(in + c0, cf.ref[0]);
+            static_for<0, NP>([&](auto pc) {
+                constexpr int P = decltype(pc)::value;
+                const long long off = pair_offset<LAT>(g, P);
+                s += cf.Wp[l][P] * Tr::load(in + c0 + off, cf.ref[0]) + cf.Wm[l][P] * Tr::load(in + c0 - off, cf.ref[0]);
+            });
+            acc[0] += s;
+        } else {
+            T f[NF];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) f[i] = Tr::load(in + i * g.fs + c0, cf.ref[i]);
+            Basis<LAT, PDE, T> b0;
+            b0.init(f, cf);
+            acc[0] += cf.a0[l] * b0.A() + cf.ap[l] * b0.rest(cf);
+            if constexpr (PDE == PDE_NSE) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) acc[1 + a] += cf.ab0[l] * b0.mom(a);
+            }
+            static_for<0, NP>([&](auto pc) {
+                constexpr int P = decltype(pc)::value;
+                const long long off = pair_offset<LAT>(g, P);
+                T fp[NF], fm[NF];
+#pragma unroll
+                for (int i = 0; i < NF; ++i) {
+                    fp[i] = Tr::load(in + i * g.fs + c0 + off, cf.ref[i]);
+                    fm[i] = Tr::load(in + i * g.fs + c0 - off, cf.ref[i]);
+                }
+                Basis<LAT, PDE, T> bp, bm;
+                bp.init(fp, cf);
+                bm.init(fm, cf);
+                T Ep, Op, Em, Om;
+                bp.template eo<P>(cf, Ep, Op);
+                bm.template eo<P>(cf, Em, Om);
+                acc[0] += cf.ap[l] * (Ep + Em) + cf.am[l] * (Op - Om);
+                if constexpr (PDE == PDE_NSE) {
+                    const T dm = cf.abm[l] * (Ep - Em) + cf.abp[l] * (Op + Om);
+#pragma unroll
+                    for (int a = 0; a < D; ++a)
+                        if (pair_e(LAT, P, a) != 0) acc[1 + a] += T(pair_e(LAT, P, a)) * cf.fmom[a] * dm;
+                }
+            });
+        }
+    }
+    S* out = static_cast<S*>(outv);
+    const long long node = ((long long)z * g.ny + y) * g.nx + x;
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, node, i) : 0u;
+        store_with_ghosts<D>(out + i * g.fs, g, x, y, z, Tr::pack(acc[i], cf.ref[i], rnd));
+    }
+}
+
+template <int LAT, int PDE, int LEVELS, int ST>
+cudaError_t launch_direct(const LaunchArgs& a) {
+    using T = typename Storage<ST>::T;
+    dim3 block(64, 4, 1);
+    dim3 grid((a.g.nx + block.x - 1) / block.x, (a.g.ny + block.y - 1) / block.y, a.g.nz);
+    k_direct<LAT, PDE, LEVELS, ST><<<grid, block, 0, a.stream>>>(a.g, a.in0, a.in1, a.out,
+                                                                  *static_cast<const Coef<T>*>(a.coef), a.ex);
+    return cudaGetLastError();
+}
+
+}  // namespace mmfd

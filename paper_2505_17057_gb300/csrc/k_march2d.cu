@@ -1,0 +1,47 @@
+// k_march2d.cu -- instantiations of the 2D row-marching TMA kernels.
+#include "k_march2d.cuh"
+
+namespace mmfd {
+
+namespace {
+
+// Ring depth: about 64 KB of stages per CTA, between 3 and 16 rows in flight.
+template <int LAT, int PDE, int LEVELS, int ST>
+constexpr int march2d_stages() {
+    constexpr size_t per = march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 4, 1>() - 128;
+    constexpr size_t n = 65536 / per;
+    return n < 3 ? 3 : (n > 16 ? 16 : (int)n);
+}
+
+template <int LAT, int PDE, int LEVELS, int ST>
+LaunchFn pick() {
+    return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST>()>;
+}
+
+template <int LAT, int PDE>
+LaunchFn pick_ls(int levels, int st) {
+    if (levels == 2) {
+        if (st == ST_F64) return pick<LAT, PDE, 2, ST_F64>();
+        if (st == ST_F32) return pick<LAT, PDE, 2, ST_F32>();
+        if (st == ST_BF16) return pick<LAT, PDE, 2, ST_BF16>();
+    } else if (levels == 3) {
+        if (st == ST_F64) return pick<LAT, PDE, 3, ST_F64>();
+        if (st == ST_F32) return pick<LAT, PDE, 3, ST_F32>();
+        if (st == ST_BF16) return pick<LAT, PDE, 3, ST_BF16>();
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+LaunchFn find_march2d(int lat, int pde, int levels, int st) {
+    if (lat == LAT_D2Q5) return pde == PDE_LCDE ? pick_ls<LAT_D2Q5, PDE_LCDE>(levels, st) : nullptr;
+    if (lat == LAT_D2Q9) {
+        if (pde == PDE_LCDE) return pick_ls<LAT_D2Q9, PDE_LCDE>(levels, st);
+        if (pde == PDE_NCDE) return pick_ls<LAT_D2Q9, PDE_NCDE>(levels, st);
+        if (pde == PDE_NSE) return pick_ls<LAT_D2Q9, PDE_NSE>(levels, st);
+    }
+    return nullptr;
+}
+
+}  // namespace mmfd

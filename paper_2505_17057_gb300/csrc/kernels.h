@@ -1,0 +1,57 @@
+// kernels.h -- host-side entry points of the kernel families (type-erased launchers).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "mmfd_internal.h"
+
+namespace mmfd {
+
+// Up to 8 TMA tensor maps (nf fields x input levels), passed to a kernel as a grid constant.
+struct alignas(64) TmapSet {
+    CUtensorMap m[8];
+};
+
+// A launcher advances one (or `depth`) time level(s): reads level t (in0) and level t - dt
+// (in1, three-level only) and writes level t + dt (out), all in the ghosted layout `g`.
+// coef points at a Coef<double> or Coef<float> matching the storage type.
+struct LaunchArgs {
+    Geom g;
+    const void* in0;
+    const void* in1;
+    void* out;
+    const void* coef;
+    StepExtra ex;
+    cudaStream_t stream;
+    int variant;          // kernel-shape variant chosen by the tuner (family specific)
+    const TmapSet* maps;  // TMA descriptors of the input levels (march / blocked kernels)
+    int H;                // rows (2D) or planes (3D) per CTA
+    int* err;             // device error flag (bounded waits that ran out)
+};
+using LaunchFn = cudaError_t (*)(const LaunchArgs&);
+
+// One node per thread, neighbours read straight from the ghosted layout (any shape).
+LaunchFn find_direct(int lat, int pde, int levels, int st);
+// Row-marching 2D kernels fed by a TMA (cp.async.bulk.tensor) shared-memory ring.
+LaunchFn find_march2d(int lat, int pde, int levels, int st);
+// 3D plane-marching kernels (z march, x-y tile staged in shared memory by TMA).
+LaunchFn find_march3d(int lat, int pde, int levels, int st);
+
+// Encode a 2D / 3D tiled TMA descriptor over one field of a ghosted level buffer
+// (box = boxw x 1 [x 1] elements).  Returns 0 on success.
+int encode_field_map(CUtensorMap* m, void* field_base, int st, const Geom& g, int boxw, int boxh, int boxd);
+
+// Utility kernels (k_util.cu).
+cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, void* dst_level, int field,
+                        double ref, cudaStream_t s);
+cudaError_t launch_unpack(const Geom& g, int st, const void* src_level, int field, double ref, void* dst,
+                          int dst_dtype, cudaStream_t s);
+// Deterministic FP64 reductions over the interior of one field: op 0 sum, 1 max|v|,
+// 2 non-finite count; with ref != NULL: op 3 -> (sum |v - ref|, sum |ref|, max |v - ref|, max |ref|).
+cudaError_t launch_reduce(const Geom& g, int st, const void* level, int field, double fref, int op,
+                          const void* ref, int ref_dtype, double* d_partials, int nparts, double* d_out,
+                          cudaStream_t s);
+int reduce_parts_needed();
+
+}  // namespace mmfd

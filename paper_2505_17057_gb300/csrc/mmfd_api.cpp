@@ -1,0 +1,257 @@
+// mmfd_api.cpp -- the C ABI of include/mmfd.h: solver objects, level buffers in the ghosted
+// layout, set/get of fields, stepping, reductions.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/mmfd.h"
+#include "kernels.h"
+#include "params.h"
+#include "solver.h"
+
+namespace mmfd {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return MMFD_ERR_CUDA;
+}
+
+Geom make_geom(const Resolved& r) {
+    Geom g{};
+    g.dim = r.dim;
+    g.nx = (int)r.n[0];
+    g.ny = (int)r.n[1];
+    g.nz = (int)r.n[2];
+    g.es = storage_bytes(r.st);
+    g.nf = r.nf;
+    const int align = 16 / g.es;            // elements per 16 bytes
+    g.ox = align;                            // interior column 0 on a 16-byte boundary
+    g.gz = r.dim == 3 ? 1 : 0;
+    long long py = g.ox + g.nx + align;      // right ghost plus slack for vector/TMA tails
+    py = (py + 2 * align - 1) / (2 * align) * (2 * align);  // 32-byte rows
+    g.py = py;
+    g.pz = py * (g.ny + 2);
+    const long long planes = g.nz + 2 * g.gz;
+    const long long per256 = 256 / g.es;
+    g.fs = (g.pz * planes + per256 - 1) / per256 * per256;
+    return g;
+}
+
+int dev_alloc(Solver* s, size_t bytes, void** p) {
+    if (s->alloc) {
+        if (s->alloc(bytes, p, s->alloc_ctx) != 0 || !*p) return set_error(MMFD_ERR_OOM, "allocator callback failed");
+        return MMFD_OK;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MMFD_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return MMFD_OK;
+}
+
+void dev_free(Solver* s, void* p) {
+    if (!p) return;
+    if (s->alloc && s->free_fn)
+        s->free_fn(p, s->alloc_ctx);
+    else if (!s->alloc)
+        cudaFree(p);
+}
+
+}  // namespace mmfd
+
+using namespace mmfd;
+
+extern "C" {
+
+int mmfd_desc_init(mmfd_desc* d) {
+    if (!d) return MMFD_ERR_ARG;
+    std::memset(d, 0, sizeof(*d));
+    d->pde = MMFD_LCDE;
+    d->lattice = MMFD_D2Q9;
+    d->levels = 2;
+    d->dim = 2;
+    d->n[0] = d->n[1] = 64;
+    d->n[2] = 1;
+    d->dt = 1.0;
+    d->dx[0] = d->dx[1] = d->dx[2] = 1.0;
+    d->d0[0] = d->d0[1] = d->d0[2] = 1.0 / 3.0;
+    d->lambda_bar = 1.0;
+    d->rho0 = 1.0;
+    d->coef_mode = MMFD_COEF_TARGETS;
+    d->targets[0] = 0.0;
+    d->targets[1] = -1.0;
+    d->targets[2] = -1.0;
+    d->targets[3] = 0.0;
+    d->targets[4] = 0.5;
+    for (int i = 0; i < 5; ++i) d->targets_bar[i] = d->targets[i];
+    d->storage = MMFD_FP32;
+    for (int f = 0; f < 4; ++f) d->ref[f] = NAN;
+    d->temporal_depth = 1;
+    d->seed = 0x4D4D4644ull;
+    return MMFD_OK;
+}
+
+int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3]) {
+    if (!targets || !a || !ahat) return set_error(MMFD_ERR_ARG, "null argument");
+    return solve_three_level_targets(targets, a, ahat);
+}
+
+static void fill_info(const Resolved& r, mmfd_info_t* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->nf = r.nf;
+    o->levels_stored = r.levels;
+    for (int i = 0; i < 3; ++i) {
+        o->a[i] = r.a[i];
+        o->ahat[i] = r.ahat[i];
+        o->abar[i] = r.abar[i];
+        o->abarhat[i] = r.abarhat[i];
+        o->c[i] = r.c[i];
+        o->d0[i] = r.d0[i];
+        o->cs2[i] = r.cs2[i];
+        for (int j = 0; j < 3; ++j) o->Cmat[i][j] = r.Cmat[i][j];
+    }
+    o->A10 = r.A10;
+    o->A20 = r.A20;
+    o->A21 = r.A21;
+    o->A22 = r.A22;
+    for (int j = 0; j < 19; ++j) o->w[j] = r.w[j];
+    for (int k = 0; k < 5; ++k) o->m2[k] = r.m2[k];
+    o->max_lambda = r.max_lambda;
+    o->bytes_per_lu = bytes_per_lu(r);
+    o->temporal_depth = 1;
+}
+
+int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out) {
+    if (!desc || !out) return set_error(MMFD_ERR_ARG, "null argument");
+    Resolved* r = new (std::nothrow) Resolved;
+    if (!r) return MMFD_ERR_OOM;
+    std::string msg;
+    int rc = resolve(*desc, *r, &msg);
+    if (rc != MMFD_OK) {
+        delete r;
+        return set_error(rc, msg);
+    }
+    fill_info(*r, out);
+    delete r;
+    return MMFD_OK;
+}
+
+int mmfd_create(const mmfd_desc* desc, mmfd_solver** out) {
+    if (!desc || !out) return set_error(MMFD_ERR_ARG, "null argument");
+    *out = nullptr;
+    Solver* s = new (std::nothrow) Solver();
+    if (!s) return set_error(MMFD_ERR_OOM, "host allocation failed");
+    std::string msg;
+    int rc = resolve(*desc, s->r, &msg);
+    if (rc != MMFD_OK) {
+        delete s;
+        return set_error(rc, msg);
+    }
+    s->desc = *desc;
+    s->stream = static_cast<cudaStream_t>(desc->stream);
+    s->alloc = desc->alloc;
+    s->free_fn = desc->free_fn;
+    s->alloc_ctx = desc->alloc_ctx;
+    s->g = make_geom(s->r);
+    rc = solver_init_device(s);
+    if (rc != MMFD_OK) {
+        solver_free_device(s);
+        delete s;
+        return rc;
+    }
+    *out = reinterpret_cast<mmfd_solver*>(s);
+    return MMFD_OK;
+}
+
+int mmfd_set_fields(mmfd_solver* h, int level, const void* const* fields, int where, int dtype) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !fields) return set_error(MMFD_ERR_ARG, "null argument");
+    return solver_set_fields(s, level, fields, where, dtype);
+}
+
+int mmfd_step(mmfd_solver* h, long long nsteps) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || nsteps < 0) return set_error(MMFD_ERR_ARG, "bad argument");
+    return solver_step(s, nsteps);
+}
+
+int mmfd_fields(mmfd_solver* h, int level, void* const* outp, int where, int dtype) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !outp) return set_error(MMFD_ERR_ARG, "null argument");
+    return solver_get_fields(s, level, outp, where, dtype);
+}
+
+int mmfd_reduce(mmfd_solver* h, int what, double* outv) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !outv) return set_error(MMFD_ERR_ARG, "null argument");
+    return solver_reduce(s, what, outv);
+}
+
+int mmfd_error_norms(mmfd_solver* h, int field, const void* ref, int where, int dtype, double* outv) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !ref || !outv) return set_error(MMFD_ERR_ARG, "null argument");
+    return solver_error_norms(s, field, ref, where, dtype, outv);
+}
+
+int mmfd_get_info(const mmfd_solver* h, mmfd_info_t* o) {
+    const Solver* s = reinterpret_cast<const Solver*>(h);
+    if (!s || !o) return set_error(MMFD_ERR_ARG, "null argument");
+    fill_info(s->r, o);
+    o->levels_stored = s->nlev;
+    o->device_bytes = (long long)s->level_bytes * s->nlev;
+    o->temporal_depth = s->depth;
+    o->steps_done = s->steps_done;
+    std::strncpy(o->kernel, s->kernel_name, sizeof(o->kernel) - 1);
+    return MMFD_OK;
+}
+
+int mmfd_set_stream(mmfd_solver* h, void* stream) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s) return set_error(MMFD_ERR_ARG, "null argument");
+    s->stream = static_cast<cudaStream_t>(stream);
+    return MMFD_OK;
+}
+
+int mmfd_destroy(mmfd_solver* h) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s) return MMFD_OK;
+    solver_free_device(s);
+    delete s;
+    return MMFD_OK;
+}
+
+const char* mmfd_strerror(int status) {
+    switch (status) {
+    case MMFD_OK: return "ok";
+    case MMFD_PENDING: return "pending";
+    case MMFD_ERR_ARG: return "invalid argument";
+    case MMFD_ERR_UNSUPPORTED: return "unsupported combination";
+    case MMFD_ERR_UNREPRESENTABLE: return "diffusion tensor not representable on this lattice";
+    case MMFD_ERR_UNSTABLE: return "scheme unstable for these parameters";
+    case MMFD_ERR_OOM: return "out of device memory";
+    case MMFD_ERR_ADMISSION: return "request exceeds the server budget";
+    case MMFD_ERR_NONFINITE: return "non-finite value in the fields";
+    case MMFD_ERR_TIMEOUT: return "device wait timed out";
+    case MMFD_ERR_CUDA: return "CUDA error";
+    case MMFD_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+const char* mmfd_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+

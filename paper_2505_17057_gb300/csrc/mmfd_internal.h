@@ -1,0 +1,86 @@
+// mmfd_internal.h -- definitions shared by the host library and the sm_103a kernels.
+//
+// The MMFD update (arXiv 2505.17057, Eq. (2-2), (2-4), (3layerMMFD-1)) is linear in the
+// arguments (A, B, C) of the quadratic EDF Eq. (3-3), so the kernels evaluate it in the
+// paired central form of Eq. (2-2-1)/(2-4-1): for every +/- velocity pair p (representative
+// direction e_p) and every neighbour y = x +/- e_p they need only
+//     E_p(y) = omega_p (A + Qtilde_p : C)(y)          (even part of f_p^eq)
+//     O_p(y) = omega_p (ctilde_p . B)(y)               (odd part of f_p^eq)
+// and
+//     phi'(x) = sum_l [ a_0 A(x) + a+ f_0^eq(x) + sum_p a+ (E_p(x+e_p) + E_p(x-e_p))
+//                                              + a- (O_p(x+e_p) - O_p(x-e_p)) ]
+//     m'_a(x) = sum_l [ abar_0 B_a(x) + c_a sum_p e_pa ( abar- (E_p(x+e_p) - E_p(x-e_p))
+//                                                   + abar+ (O_p(x+e_p) + O_p(x-e_p)) ) ]
+// with a+ = a_1 + a_{-1}, a- = a_1 - a_{-1} (Eq. (2-1-FD1-0)) per time level l.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mmfd {
+
+enum Pde { PDE_LCDE = 0, PDE_NCDE = 1, PDE_NSE = 2 };
+enum Lat { LAT_D2Q5 = 0, LAT_D2Q9 = 1, LAT_D3Q7 = 2, LAT_D3Q19 = 3 };
+enum St { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2 };
+
+constexpr int kMaxPair = 9;
+
+// Representative direction of velocity pair p (the other member is -e_p).
+__host__ __device__ constexpr int lat_dim(int lat) { return (lat == LAT_D2Q5 || lat == LAT_D2Q9) ? 2 : 3; }
+__host__ __device__ constexpr int lat_npair(int lat) {
+    return lat == LAT_D2Q5 ? 2 : lat == LAT_D2Q9 ? 4 : lat == LAT_D3Q7 ? 3 : 9;
+}
+__host__ __device__ constexpr int pair_e(int lat, int p, int a) {
+    // D2Q5 / D3Q7: the coordinate axes.  D2Q9: x, y, (1,1), (-1,1).
+    // D3Q19: x, y, z, (1,1,0), (-1,1,0), (1,0,1), (-1,0,1), (0,1,1), (0,-1,1).
+    return (lat == LAT_D2Q5 || lat == LAT_D3Q7) ? (p == a ? 1 : 0)
+         : (lat == LAT_D2Q9)
+             ? (p < 2 ? (p == a ? 1 : 0)
+                : p == 2 ? (a < 2 ? 1 : 0)
+                         : (a == 0 ? -1 : a == 1 ? 1 : 0))
+             : (p < 3 ? (p == a ? 1 : 0)
+                : p == 3 ? (a == 0 ? 1 : a == 1 ? 1 : 0)
+                : p == 4 ? (a == 0 ? -1 : a == 1 ? 1 : 0)
+                : p == 5 ? (a == 0 ? 1 : a == 2 ? 1 : 0)
+                : p == 6 ? (a == 0 ? -1 : a == 2 ? 1 : 0)
+                : p == 7 ? (a == 1 ? 1 : a == 2 ? 1 : 0)
+                         : (a == 1 ? -1 : a == 2 ? 1 : 0));
+}
+__host__ __device__ constexpr int pde_nf(int pde, int lat) { return pde == PDE_NSE ? 1 + lat_dim(lat) : 1; }
+
+// Padded, ghost-celled layout of one level: every field is a (nz + 2 gz) x (ny + 2) x py
+// array; interior node (x, y, z) sits at column ox + x, row y + 1, plane z + gz.  Ghost
+// cells hold the periodic images, so stencil loads need no wrap arithmetic.  ox is chosen
+// so that interior column 0 starts on a 16-byte boundary and py * es is a multiple of 16.
+struct Geom {
+    int dim, nx, ny, nz;
+    int ox, gz;
+    long long py, pz, fs;  // row pitch, plane pitch, field stride (elements)
+    int nf, es;
+    __host__ __device__ long long at(int x, int y, int z) const {
+        return (long long)(z + gz) * pz + (long long)(y + 1) * py + ox + x;
+    }
+};
+
+// Per-launch coefficients in the compute type T (host folds the constants).
+template <typename T>
+struct Coef {
+    // pair p: E_p = eA A + eC . (Cxx, Cyy, Czz, Cxy, Cxz, Cyz); O_p = oB . B
+    T eA[kMaxPair], eC[kMaxPair][6], oB[kMaxPair][3];
+    T rA, rC[3];                       // rest direction: f_0^eq = rA A + rC . diag(C)
+    T a0[2], ap[2], am[2];             // scalar / rho set per level (0: t, 1: t - dt)
+    T ab0[2], abp[2], abm[2];          // momentum set per level
+    T fmom[3];                         // c_a / rho0 (momentum -> velocity)
+    T W0[2], Wp[2][kMaxPair], Wm[2][kMaxPair];   // LCDE: collapsed linear stencil per level
+    T flux[3][4], m2[5];               // NCDE polynomials
+    T ePhi[kMaxPair], eM2[kMaxPair], rPhi, rM2;  // NCDE: E_p = ePhi phi + eM2 M2(phi)
+    T ref[4];                          // BF16 offsets per field
+};
+
+struct StepExtra {
+    unsigned long long seed;  // stochastic rounding
+    long long step;           // global step index of the level being written
+    int sr;                   // 1: stochastic rounding (BF16 storage only)
+};
+
+}  // namespace mmfd

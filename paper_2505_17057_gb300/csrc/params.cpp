@@ -1,0 +1,410 @@
+// params.cpp -- problem descriptor -> scheme coefficients, EDF constants and the folded
+// coefficient blocks the kernels consume.  Host only.
+//
+// Sources (arXiv 2505.17057): coefficient moments Eq. (4-2)/(4-2-0) (two-level, all terms on
+// q = -1) and Eq. (4-2-00) (three-level, left-hand side at t + dt, Remark 1(5)); Eq. (X) for
+// the three-level design; Eq. (LMMFD-2-2) for the two-level one; lattices of App. A; EDF
+// Eq. (3-3)/(3-4); diffusion mapping alpha = -(A_22/A_10) dt beta c_s^2 (Eq. (M-NCDE-6)) with
+// the second-order moment equation Eq. (ME-NCDE-3-2-1); stability symbol Eq. (TforMMFD-3).
+#include "params.h"
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+namespace mmfd {
+
+namespace {
+
+bool finite(double v) { return std::isfinite(v); }
+
+// Weight of a lattice direction e (App. A) from d_0alpha.
+double weight(int lat, const int e[3], const double d[3]) {
+    const int nz = (e[0] != 0) + (e[1] != 0) + (e[2] != 0);
+    switch (lat) {
+    case LAT_D2Q5:
+        if (nz == 0) return 1.0 - d[0] - d[1];
+        return e[0] ? d[0] / 2 : d[1] / 2;
+    case LAT_D3Q7:
+        if (nz == 0) return 1.0 - d[0] - d[1] - d[2];
+        return e[0] ? d[0] / 2 : e[1] ? d[1] / 2 : d[2] / 2;
+    case LAT_D2Q9: {
+        // product of one-dimensional factors w(0) = 1 - d, w(+-1) = d / 2
+        double wx = e[0] ? d[0] / 2 : 1.0 - d[0];
+        double wy = e[1] ? d[1] / 2 : 1.0 - d[1];
+        return wx * wy;
+    }
+    case LAT_D3Q19:
+        if (nz == 0) return 1.0 - d[0] - d[1] - d[2] + d[0] * d[1] + d[0] * d[2] + d[1] * d[2];
+        if (nz == 1) {
+            if (e[0]) return d[0] * (1.0 - d[1] - d[2]) / 2;
+            if (e[1]) return d[1] * (1.0 - d[0] - d[2]) / 2;
+            return d[2] * (1.0 - d[0] - d[1]) / 2;
+        }
+        if (nz == 2) {
+            if (!e[2]) return d[0] * d[1] / 4;
+            if (!e[1]) return d[0] * d[2] / 4;
+            return d[1] * d[2] / 4;
+        }
+        return 0.0;
+    }
+    return 0.0;
+}
+
+// Directions of App. A in the paper's order (for the info block).
+int lattice_dirs(int lat, int e[19][3]) {
+    static const int d2q9[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                   {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+    static const int d3q19[19][3] = {{0, 0, 0},  {1, 0, 0},  {0, 1, 0},   {0, 0, 1},  {-1, 0, 0},
+                                     {0, -1, 0}, {0, 0, -1}, {1, 1, 0},   {-1, 1, 0}, {-1, -1, 0},
+                                     {1, -1, 0}, {1, 0, 1},  {-1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                                     {0, 1, 1},  {0, -1, 1}, {0, -1, -1}, {0, 1, -1}};
+    int b = 0;
+    if (lat == LAT_D2Q5 || lat == LAT_D2Q9) {
+        b = lat == LAT_D2Q5 ? 5 : 9;
+        for (int j = 0; j < b; ++j) std::memcpy(e[j], d2q9[j], sizeof(e[j]));
+    } else {
+        b = lat == LAT_D3Q7 ? 7 : 19;
+        for (int j = 0; j < b; ++j) std::memcpy(e[j], d3q19[j], sizeof(e[j]));
+    }
+    return b;
+}
+
+// Scheme moments A_10, A_20, A_21, A_22 from the coefficients.
+void scheme_moments(int levels, const double a[3], const double ah[3], double& A10, double& A20,
+                    double& A21, double& A22) {
+    // a[k + 1] = a_k.
+    const double s = a[0] + a[1] + a[2];
+    const double k1 = a[2] - a[0];
+    const double k2 = a[2] + a[0];
+    if (levels == 2) {
+        // every term at q = -1, left-hand side at t (Eq. (4-2-0))
+        A10 = -s;
+        A20 = 0.5 * s;
+        A21 = -k1;
+        A22 = 0.5 * k2;
+    } else {
+        // a_k at q = 0, ahat_k at q = -1, left-hand side at t + dt (Eq. (4-2-00a))
+        const double sh = ah[0] + ah[1] + ah[2];
+        A10 = -sh - 1.0;
+        A20 = 0.5 * (sh - 1.0);
+        A21 = -(ah[2] - ah[0]);
+        A22 = 0.5 * (k2 + ah[2] + ah[0]);
+    }
+}
+
+}  // namespace
+
+int solve_three_level_targets(const double t[5], double a[3], double ah[3]) {
+    const double a0 = t[0], A10 = t[1], A11 = t[2], A21 = t[3], A22 = t[4];
+    for (int i = 0; i < 5; ++i)
+        if (!finite(t[i])) return MMFD_ERR_ARG;
+    // Eq. (X): X = A^{-1} b, b = (1 - a_0, 1 + A_10, A_11, A_21, A_22)
+    a[2] = 0.5 * (-a0 + A10 + A11 + A21 + 2.0);
+    a[0] = 0.5 * (-a0 + A10 - A11 - A21 + 2.0);
+    a[1] = a0;
+    ah[1] = 0.5 * (-2.0 * a0 - 4.0 * A22 + 2.0);
+    ah[2] = 0.5 * (a0 - A10 - A21 + 2.0 * A22 - 2.0);
+    ah[0] = 0.5 * (a0 - A10 + A21 + 2.0 * A22 - 2.0);
+    return MMFD_OK;
+}
+
+static int coeffs_for(const mmfd_desc& d, const double* explicit_a, const double* explicit_ah,
+                      const double* targets, double a[3], double ah[3]) {
+    if (d.coef_mode == MMFD_COEF_EXPLICIT) {
+        for (int i = 0; i < 3; ++i) {
+            a[i] = explicit_a[i];
+            ah[i] = d.levels == 3 ? explicit_ah[i] : 0.0;
+        }
+    } else if (d.coef_mode == MMFD_COEF_TARGETS) {
+        if (d.levels == 2) {
+            // Eq. (LMMFD-2-2), m = 1: A_00 = 1, A_10 = A_11 = -1
+            const double a0 = targets[0];
+            a[0] = 1.0 - 0.5 * a0;
+            a[1] = a0;
+            a[2] = -0.5 * a0;
+            ah[0] = ah[1] = ah[2] = 0.0;
+        } else if (solve_three_level_targets(targets, a, ah) != MMFD_OK) {
+            return MMFD_ERR_ARG;
+        }
+    } else {
+        return MMFD_ERR_ARG;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!finite(a[i]) || !finite(ah[i])) return MMFD_ERR_ARG;
+    return MMFD_OK;
+}
+
+static int fail(std::string* msg, int code, const char* why) {
+    if (msg) *msg = why;
+    return code;
+}
+
+int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
+    std::memset(&r, 0, sizeof(r));
+    if (d.pde < PDE_LCDE || d.pde > PDE_NSE) return fail(msg, MMFD_ERR_ARG, "unknown pde");
+    if (d.lattice < LAT_D2Q5 || d.lattice > LAT_D3Q19) return fail(msg, MMFD_ERR_ARG, "unknown lattice");
+    if (d.levels != 2 && d.levels != 3) return fail(msg, MMFD_ERR_ARG, "levels must be 2 or 3");
+    if (d.storage < ST_F64 || d.storage > ST_BF16) return fail(msg, MMFD_ERR_ARG, "unknown storage");
+    const int dim = lat_dim(d.lattice);
+    if (d.dim != dim) return fail(msg, MMFD_ERR_ARG, "dim does not match the lattice");
+    for (int a = 0; a < 3; ++a) {
+        const long long n = d.n[a];
+        if (a < dim && (n < 1 || n > (1ll << 20))) return fail(msg, MMFD_ERR_ARG, "grid size out of range");
+        if (a >= dim && n != 1) return fail(msg, MMFD_ERR_ARG, "n[2] must be 1 in 2D");
+    }
+    if (!(d.dt > 0) || !finite(d.dt)) return fail(msg, MMFD_ERR_ARG, "dt must be positive");
+    for (int a = 0; a < dim; ++a)
+        if (!(d.dx[a] > 0) || !finite(d.dx[a])) return fail(msg, MMFD_ERR_ARG, "dx must be positive");
+    if ((d.pde == PDE_NSE || d.pde == PDE_NCDE) && (d.lattice == LAT_D2Q5 || d.lattice == LAT_D3Q7))
+        return fail(msg, MMFD_ERR_UNSUPPORTED,
+                    "NSE and NCDE need the quadratic EDF moments of D2Q9/D3Q19 (axis lattices cannot carry C)");
+
+    r.pde = d.pde;
+    r.lat = d.lattice;
+    r.levels = d.levels;
+    r.dim = dim;
+    r.nf = pde_nf(d.pde, d.lattice);
+    r.st = d.storage;
+    for (int a = 0; a < 3; ++a) r.n[a] = d.n[a];
+
+    if (coeffs_for(d, d.a, d.ahat, d.targets, r.a, r.ahat) != MMFD_OK)
+        return fail(msg, MMFD_ERR_ARG, "bad scheme coefficients");
+    if (d.pde == PDE_NSE) {
+        if (coeffs_for(d, d.abar, d.abarhat, d.targets_bar, r.abar, r.abarhat) != MMFD_OK)
+            return fail(msg, MMFD_ERR_ARG, "bad momentum coefficients");
+    }
+    // A_00 = 1 (Eq. (4-2-0)); a scheme violating it does not conserve mass.
+    const double A00 = r.a[0] + r.a[1] + r.a[2] + (d.levels == 3 ? r.ahat[0] + r.ahat[1] + r.ahat[2] : 0.0);
+    if (std::fabs(A00 - 1.0) > 1e-12) return fail(msg, MMFD_ERR_ARG, "coefficients violate A_00 = 1");
+    if (d.pde == PDE_NSE) {
+        const double Ab00 = r.abar[0] + r.abar[1] + r.abar[2] +
+                            (d.levels == 3 ? r.abarhat[0] + r.abarhat[1] + r.abarhat[2] : 0.0);
+        if (std::fabs(Ab00 - 1.0) > 1e-12) return fail(msg, MMFD_ERR_ARG, "momentum coefficients violate Abar_00 = 1");
+    }
+    scheme_moments(d.levels, r.a, r.ahat, r.A10, r.A20, r.A21, r.A22);
+
+    for (int a = 0; a < 3; ++a) r.c[a] = a < dim ? d.dx[a] / d.dt : 0.0;
+
+    // ---- lattice parameters and the EDF's C per unit phi (LCDE)
+    const bool axis = (d.lattice == LAT_D2Q5 || d.lattice == LAT_D3Q7);
+    std::memset(r.Cmat, 0, sizeof(r.Cmat));
+    if (d.pde == PDE_LCDE) {
+        for (int a = 0; a < dim; ++a)
+            for (int b = 0; b < dim; ++b)
+                if (!finite(d.K[a][b]) || std::fabs(d.K[a][b] - d.K[b][a]) > 1e-14 * (1 + std::fabs(d.K[a][b])))
+                    return fail(msg, MMFD_ERR_ARG, "K must be finite and symmetric");
+        if (r.A10 == 0.0 || r.A22 == 0.0) return fail(msg, MMFD_ERR_ARG, "A_10 and A_22 must be nonzero for a CDE");
+    }
+    if (axis) {
+        // Linear EDF (C = 0) with direction-dependent c_salpha^2 chosen so that the recovered
+        // diffusion K_eff = -(dt/A_10)[A_22 diag(c_s^2) - (A_21 - A_20) u u] (Eq. (ME-NCDE-3-2-1))
+        // has the requested diagonal.  The off-diagonal cannot be carried (no c_x c_y != 0).
+        bool offdiag = false;
+        for (int a = 0; a < dim; ++a)
+            for (int b = 0; b < dim; ++b)
+                if (a != b && d.K[a][b] != 0.0) offdiag = true;
+        if (offdiag && !(d.flags & MMFD_FLAG_DROP_OFFDIAG))
+            return fail(msg, MMFD_ERR_UNREPRESENTABLE,
+                        "off-diagonal diffusion cannot be represented on an axis lattice (set MMFD_FLAG_DROP_OFFDIAG)");
+        double sum = 0.0;
+        for (int a = 0; a < dim; ++a) {
+            const double cs2 = (-r.A10 * d.K[a][a] / d.dt + (r.A21 - r.A20) * d.u[a] * d.u[a]) / r.A22;
+            r.cs2[a] = cs2;
+            r.d0[a] = cs2 / (r.c[a] * r.c[a]);
+            if (!(r.d0[a] > 0.0) || !finite(r.d0[a])) return fail(msg, MMFD_ERR_ARG, "derived d_0 must be positive");
+            sum += r.d0[a];
+        }
+        if (!(sum < 1.0)) return fail(msg, MMFD_ERR_UNSTABLE, "derived d_0 sum >= 1: negative rest weight (App. A)");
+    } else {
+        for (int a = 0; a < dim; ++a) {
+            r.d0[a] = d.d0[a];
+            if (!(r.d0[a] > 0.0 && r.d0[a] < 1.0)) return fail(msg, MMFD_ERR_ARG, "d_0 must lie in (0, 1)");
+            r.cs2[a] = r.d0[a] * r.c[a] * r.c[a];
+        }
+        if (d.pde == PDE_LCDE) {
+            // C = c_s^2 (beta D0 - I) + lambda_bar u u with c_s^2 beta D0 = -A_10 K / (A_22 dt)
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b)
+                    r.Cmat[a][b] = -r.A10 * d.K[a][b] / (r.A22 * d.dt) + d.lambda_bar * d.u[a] * d.u[b];
+            for (int a = 0; a < dim; ++a) r.Cmat[a][a] -= r.cs2[a];
+        }
+    }
+    if (d.pde == PDE_NCDE) {
+        if (r.A10 == 0.0 || r.A22 == 0.0) return fail(msg, MMFD_ERR_ARG, "A_10 and A_22 must be nonzero for a CDE");
+        // alpha D = G(phi) I with G' = D(phi), G(0) = 0 (Eq. (M-NCDE-6)): second-moment target
+        // beta c_s^2 D = -(A_10 / (A_22 dt)) G(phi) I.
+        std::memset(r.m2, 0, sizeof(r.m2));
+        for (int p = 0; p < 4; ++p) r.m2[p + 1] = -r.A10 * d.diff[p] / ((p + 1) * r.A22 * d.dt);
+    }
+    if (d.pde == PDE_NSE && !(d.rho0 > 0.0)) return fail(msg, MMFD_ERR_ARG, "rho0 must be positive");
+
+    // ---- weights in App. A order
+    int e[19][3];
+    const int b = lattice_dirs(d.lattice, e);
+    for (int j = 0; j < b; ++j) {
+        r.w[j] = weight(d.lattice, e[j], r.d0);
+        if (!(r.w[j] >= 0.0)) return fail(msg, MMFD_ERR_ARG, "lattice weights must be non-negative (App. A)");
+    }
+
+    // ---- BF16 offsets
+    for (int f = 0; f < 4; ++f) {
+        double v = d.ref[f];
+        if (std::isnan(v)) v = (d.pde == PDE_NSE && f == 0) ? d.rho0 : 0.0;
+        r.ref[f] = v;
+    }
+
+    // ---- folded kernel coefficients (double)
+    Coef<double>& c = r.cd;
+    std::memset(&c, 0, sizeof(c));
+    const int NP = lat_npair(d.lattice);
+    const int zero[3] = {0, 0, 0};
+    const double w0 = weight(d.lattice, zero, r.d0);
+    const double rho0 = d.pde == PDE_NSE ? d.rho0 : 1.0;
+    for (int p = 0; p < NP; ++p) {
+        int ep[3];
+        double cp[3];
+        for (int a = 0; a < 3; ++a) {
+            ep[a] = a < dim ? pair_e(d.lattice, p, a) : 0;
+            cp[a] = ep[a] * r.c[a];
+        }
+        const double wp = weight(d.lattice, ep, r.d0);
+        c.eA[p] = wp;
+        for (int a = 0; a < dim; ++a) {
+            // Qtilde_paa = (c_pa^2 - cs_a^2) / (cs_a^2 (c_a^2 - cs_a^2)) (Eq. (3-4))
+            c.eC[p][a] = wp * (cp[a] * cp[a] - r.cs2[a]) / (r.cs2[a] * (r.c[a] * r.c[a] - r.cs2[a]));
+            c.oB[p][a] = wp * cp[a] / r.cs2[a];
+        }
+        // off-diagonal: both orderings of Qtilde_pab = c_pa c_pb / (2 cs_a^2 cs_b^2)
+        c.eC[p][3] = wp * cp[0] * cp[1] / (r.cs2[0] * r.cs2[1]);
+        if (dim == 3) {
+            c.eC[p][4] = wp * cp[0] * cp[2] / (r.cs2[0] * r.cs2[2]);
+            c.eC[p][5] = wp * cp[1] * cp[2] / (r.cs2[1] * r.cs2[2]);
+        }
+        if (axis) {
+            // linear EDF: no C terms at all
+            for (int k = 0; k < 6; ++k) c.eC[p][k] = 0.0;
+        }
+    }
+    c.rA = w0;
+    for (int a = 0; a < dim; ++a) c.rC[a] = axis ? 0.0 : -w0 / (r.c[a] * r.c[a] - r.cs2[a]);
+
+    const double* sets[2] = {r.a, r.ahat};
+    const double* bsets[2] = {r.abar, r.abarhat};
+    for (int l = 0; l < 2; ++l) {
+        c.a0[l] = sets[l][1];
+        c.ap[l] = sets[l][2] + sets[l][0];
+        c.am[l] = sets[l][2] - sets[l][0];
+        c.ab0[l] = bsets[l][1];
+        c.abp[l] = bsets[l][2] + bsets[l][0];
+        c.abm[l] = bsets[l][2] - bsets[l][0];
+    }
+    for (int a = 0; a < dim; ++a) c.fmom[a] = r.c[a] / rho0;
+
+    if (d.pde == PDE_LCDE) {
+        // f^eq = phi ubar: E_p = phi ebar_p, O_p = phi obar_p -> collapsed stencil weights
+        double rbar = c.rA;
+        for (int a = 0; a < dim; ++a) rbar += c.rC[a] * r.Cmat[a][a];
+        for (int l = 0; l < 2; ++l) c.W0[l] = c.a0[l] + c.ap[l] * rbar;
+        for (int p = 0; p < NP; ++p) {
+            double eb = c.eA[p];
+            for (int a = 0; a < dim; ++a) eb += c.eC[p][a] * r.Cmat[a][a];
+            eb += c.eC[p][3] * r.Cmat[0][1];
+            if (dim == 3) eb += c.eC[p][4] * r.Cmat[0][2] + c.eC[p][5] * r.Cmat[1][2];
+            double ob = 0.0;
+            for (int a = 0; a < dim; ++a) ob += c.oB[p][a] * d.u[a];
+            for (int l = 0; l < 2; ++l) {
+                c.Wp[l][p] = c.ap[l] * eb + c.am[l] * ob;
+                c.Wm[l][p] = c.ap[l] * eb - c.am[l] * ob;
+            }
+        }
+    } else if (d.pde == PDE_NCDE) {
+        for (int a = 0; a < dim; ++a)
+            for (int k = 0; k < 4; ++k) c.flux[a][k] = d.flux[a][k];
+        for (int k = 0; k < 5; ++k) c.m2[k] = r.m2[k];
+        for (int p = 0; p < NP; ++p) {
+            double ephi = c.eA[p], em2 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                ephi -= c.eC[p][a] * r.cs2[a];
+                em2 += c.eC[p][a];
+            }
+            c.ePhi[p] = ephi;
+            c.eM2[p] = em2;
+        }
+        c.rPhi = c.rA;
+        c.rM2 = 0.0;
+        for (int a = 0; a < dim; ++a) {
+            c.rPhi -= c.rC[a] * r.cs2[a];
+            c.rM2 += c.rC[a];
+        }
+    } else {
+        // He-Luo: fold rho0 into the u u and u terms
+        for (int p = 0; p < NP; ++p) {
+            for (int k = 0; k < 6; ++k) c.eC[p][k] *= rho0;
+            for (int a = 0; a < 3; ++a) c.oB[p][a] *= rho0;
+        }
+        for (int a = 0; a < 3; ++a) c.rC[a] *= rho0;
+    }
+    for (int f = 0; f < 4; ++f) c.ref[f] = r.ref[f];
+
+    // float copy
+    {
+        const double* src = reinterpret_cast<const double*>(&r.cd);
+        float* dst = reinterpret_cast<float*>(&r.cf);
+        static_assert(sizeof(Coef<double>) == 2 * sizeof(Coef<float>), "Coef layout");
+        for (size_t i = 0; i < sizeof(Coef<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
+    }
+
+    // ---- create-time stability check (LCDE: exact symbol on the grid's wave numbers)
+    r.max_lambda = -1.0;
+    if (d.pde == PDE_LCDE) {
+        std::vector<double> th[3];
+        for (int a = 0; a < 3; ++a) {
+            const long long n = a < dim ? d.n[a] : 1;
+            const double two_pi = 6.283185307179586;
+            if (n <= 96) {
+                for (long long m = 0; m < n; ++m) th[a].push_back(two_pi * m / n);
+            } else {
+                // the grid's smallest wave numbers (where convection-driven growth lives) and a
+                // uniform sweep through the rest of the band
+                for (long long m = 0; m <= 16; ++m) th[a].push_back(two_pi * m / n);
+                for (int m = 1; m <= 64; ++m) th[a].push_back(two_pi * (double)((long long)((double)m * n / 128.0)) / n);
+            }
+        }
+        double lmax = 0.0;
+        for (double tz : th[2])
+            for (double ty : th[1])
+                for (double tx : th[0]) {
+                    std::complex<double> A[2];
+                    for (int l = 0; l < 2; ++l) {
+                        std::complex<double> s(c.W0[l], 0.0);
+                        for (int p = 0; p < NP; ++p) {
+                            const double ph = pair_e(d.lattice, p, 0) * tx + pair_e(d.lattice, p, 1) * ty +
+                                              (dim == 3 ? pair_e(d.lattice, p, 2) * tz : 0.0);
+                            s += c.Wp[l][p] * std::polar(1.0, ph) + c.Wm[l][p] * std::polar(1.0, -ph);
+                        }
+                        A[l] = s;
+                    }
+                    double m;
+                    if (d.levels == 2) {
+                        m = std::abs(A[0]);
+                    } else {
+                        // roots of lambda^2 - p1 lambda - p0 (Eq. (3-level))
+                        const std::complex<double> disc = std::sqrt(A[0] * A[0] + 4.0 * A[1]);
+                        m = std::max(std::abs(0.5 * (A[0] + disc)), std::abs(0.5 * (A[0] - disc)));
+                    }
+                    if (m > lmax) lmax = m;
+                }
+        r.max_lambda = lmax;
+        if (lmax > 1.0 + 1e-12 && !(d.flags & MMFD_FLAG_ALLOW_UNSTABLE))
+            return fail(msg, MMFD_ERR_UNSTABLE, "max |lambda| > 1 on the grid's wave numbers");
+    }
+    return MMFD_OK;
+}
+
+double bytes_per_lu(const Resolved& r) {
+    return (double)storage_bytes(r.st) * r.nf * (r.levels - 1 + 1);
+}
+
+}  // namespace mmfd

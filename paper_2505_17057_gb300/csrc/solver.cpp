@@ -1,0 +1,307 @@
+// solver.cpp -- device side of a solver: level buffers, transfers, stepping, reductions.
+#include "solver.h"
+
+#include <cstdlib>
+#include <cstring>
+
+namespace mmfd {
+
+namespace {
+
+long long nodes(const Solver* s) { return (long long)s->g.nx * s->g.ny * s->g.nz; }
+
+int ensure_stage(Solver* s) {
+    const size_t need = (size_t)nodes(s) * sizeof(double);
+    if (s->stage && s->stage_bytes >= need) return MMFD_OK;
+    if (s->stage) {
+        dev_free(s, s->stage);
+        s->stage = nullptr;
+    }
+    int rc = dev_alloc(s, need, &s->stage);
+    if (rc != MMFD_OK) return rc;
+    s->stage_bytes = need;
+    return MMFD_OK;
+}
+
+int level_index(const Solver* s, int level, int* idx) {
+    if (level == 0) {
+        *idx = s->cur;
+        return MMFD_OK;
+    }
+    if (level == 1 && s->nlev == 3) {
+        *idx = s->prev();
+        return MMFD_OK;
+    }
+    return set_error(MMFD_ERR_ARG, "level must be 0 (t_n) or, for three-level solvers, 1 (t_{n-1})");
+}
+
+}  // namespace
+
+int solver_init_device(Solver* s) {
+    s->nlev = s->r.levels == 3 ? 3 : 2;
+    s->level_bytes = (size_t)s->g.fs * s->g.nf * s->g.es;
+    for (int i = 0; i < s->nlev; ++i) {
+        int rc = dev_alloc(s, s->level_bytes, &s->lev[i]);
+        if (rc != MMFD_OK) return rc;
+        cudaError_t e = cudaMemsetAsync(s->lev[i], 0, s->level_bytes, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    int rc = dev_alloc(s, (size_t)(reduce_parts_needed() + 64) * sizeof(double), reinterpret_cast<void**>(&s->d_red));
+    if (rc != MMFD_OK) return rc;
+    rc = dev_alloc(s, 256, reinterpret_cast<void**>(&s->d_flag));
+    if (rc != MMFD_OK) return rc;
+    cudaError_t e = cudaMemsetAsync(s->d_flag, 0, 256, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    s->cur = 0;
+    return solver_pick_kernels(s);
+}
+
+void solver_free_device(Solver* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int i = 0; i < 3; ++i) {
+        dev_free(s, s->lev[i]);
+        s->lev[i] = nullptr;
+    }
+    dev_free(s, s->stage);
+    s->stage = nullptr;
+    dev_free(s, s->d_red);
+    s->d_red = nullptr;
+    dev_free(s, s->d_flag);
+    s->d_flag = nullptr;
+}
+
+int solver_check_flag(Solver* s) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
+    if (h != 0) {
+        cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->stream);
+        return set_error(MMFD_ERR_TIMEOUT, "a kernel's bounded wait for its TMA copies ran out");
+    }
+    return MMFD_OK;
+}
+
+int solver_set_fields(Solver* s, int level, const void* const* fields, int where, int dtype) {
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    if (where != MMFD_HOST && where != MMFD_DEVICE) return set_error(MMFD_ERR_ARG, "where must be HOST or DEVICE");
+    int idx;
+    int rc = level_index(s, level, &idx);
+    if (rc != MMFD_OK) return rc;
+    const size_t esz = dtype == MMFD_DT_F64 ? 8 : 4;
+    const size_t bytes = (size_t)nodes(s) * esz;
+    if (where == MMFD_HOST && (rc = ensure_stage(s)) != MMFD_OK) return rc;
+    for (int f = 0; f < s->g.nf; ++f) {
+        if (!fields[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
+        const void* src = fields[f];
+        if (where == MMFD_HOST) {
+            cudaError_t e = cudaMemcpyAsync(s->stage, src, bytes, cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+            src = s->stage;
+        }
+        cudaError_t e = launch_pack(s->g, s->r.st, src, dtype, s->lev[idx], f, s->r.ref[f], s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
+        if (s->nlev == 3 && level == 0) {
+            // equilibrium start: level t - dt := level t until set explicitly
+            e = launch_pack(s->g, s->r.st, src, dtype, s->lev[s->prev()], f, s->r.ref[f], s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
+        }
+    }
+    s->fields_set = true;
+    return MMFD_OK;
+}
+
+int solver_step(Solver* s, long long nsteps) {
+    if (!s->fields_set) return set_error(MMFD_ERR_STATE, "set the fields before stepping");
+    long long done = 0;
+    while (done < nsteps) {
+        const long long left = nsteps - done;
+        const bool blocked = s->fn_block && s->depth > 1 && left >= s->depth;
+        LaunchArgs a;
+        a.g = s->g;
+        a.in0 = s->lev[s->cur];
+        a.in1 = s->nlev == 3 ? s->lev[s->prev()] : nullptr;
+        a.coef = s->coef();
+        a.ex.seed = s->desc.seed;
+        a.ex.step = s->steps_done + 1;
+        a.ex.sr = (s->r.st == ST_BF16 && (s->desc.flags & MMFD_FLAG_STOCHASTIC_ROUND)) ? 1 : 0;
+        a.stream = s->stream;
+        a.variant = s->variant;
+        a.H = s->H;
+        a.err = s->d_flag;
+        a.maps = nullptr;
+        if (s->use_tma) {
+            const int nf = s->g.nf;
+            for (int f = 0; f < nf; ++f) {
+                s->launch_maps.m[f] = s->tmaps[s->cur][f];
+                if (s->nlev == 3) s->launch_maps.m[nf + f] = s->tmaps[s->prev()][f];
+            }
+            a.maps = &s->launch_maps;
+        }
+        if (blocked) {
+            // the blocked kernel writes level t + depth dt into next(); for three-level
+            // solvers it also leaves level t + (depth - 1) dt in the buffer that becomes prev.
+            a.out = s->lev[s->next()];
+            cudaError_t e = s->fn_block(a);
+            if (e != cudaSuccess) return cuda_fail(e, "blocked step kernel");
+            s->cur = s->next();
+            s->steps_done += s->depth;
+            done += s->depth;
+        } else {
+            a.out = s->lev[s->next()];
+            cudaError_t e = s->fn(a);
+            if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+            s->cur = s->next();
+            s->steps_done += 1;
+            done += 1;
+        }
+    }
+    return MMFD_OK;
+}
+
+int solver_get_fields(Solver* s, int level, void* const* out, int where, int dtype) {
+    int frc = solver_check_flag(s);
+    if (frc != MMFD_OK) return frc;
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    if (where != MMFD_HOST && where != MMFD_DEVICE) return set_error(MMFD_ERR_ARG, "where must be HOST or DEVICE");
+    int idx;
+    int rc = level_index(s, level, &idx);
+    if (rc != MMFD_OK) return rc;
+    const size_t esz = dtype == MMFD_DT_F64 ? 8 : 4;
+    const size_t bytes = (size_t)nodes(s) * esz;
+    if (where == MMFD_HOST && (rc = ensure_stage(s)) != MMFD_OK) return rc;
+    for (int f = 0; f < s->g.nf; ++f) {
+        if (!out[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
+        void* dst = where == MMFD_HOST ? s->stage : out[f];
+        cudaError_t e = launch_unpack(s->g, s->r.st, s->lev[idx], f, s->r.ref[f], dst, dtype, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "unpack kernel");
+        if (where == MMFD_HOST) {
+            e = cudaMemcpyAsync(out[f], s->stage, bytes, cudaMemcpyDeviceToHost, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+            e = cudaStreamSynchronize(s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        }
+    }
+    return MMFD_OK;
+}
+
+int solver_reduce(Solver* s, int what, double* out) {
+    if (what < MMFD_RED_SUM || what > MMFD_RED_NONFINITE) return set_error(MMFD_ERR_ARG, "unknown reduction");
+    int frc = solver_check_flag(s);
+    if (frc != MMFD_OK) return frc;
+    const int nf = s->g.nf;
+    double* d_out = s->d_red + reduce_parts_needed();
+    double host[4 * 4];
+    for (int f = 0; f < nf; ++f) {
+        cudaError_t e = launch_reduce(s->g, s->r.st, s->lev[s->cur], f, s->r.ref[f], what, nullptr, 0, s->d_red,
+                                      reduce_parts_needed(), d_out + 4 * f, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce kernel");
+    }
+    cudaError_t e = cudaMemcpyAsync(host, d_out, sizeof(double) * 4 * nf, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (what == MMFD_RED_NONFINITE) {
+        double t = 0;
+        for (int f = 0; f < nf; ++f) t += host[4 * f];
+        out[0] = t;
+    } else {
+        for (int f = 0; f < nf; ++f) out[f] = host[4 * f];
+    }
+    return MMFD_OK;
+}
+
+int solver_error_norms(Solver* s, int field, const void* ref, int where, int dtype, double* out) {
+    if (field < 0 || field >= s->g.nf) return set_error(MMFD_ERR_ARG, "bad field index");
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    const void* dref = ref;
+    if (where == MMFD_HOST) {
+        int rc = ensure_stage(s);
+        if (rc != MMFD_OK) return rc;
+        const size_t bytes = (size_t)nodes(s) * (dtype == MMFD_DT_F64 ? 8 : 4);
+        cudaError_t e = cudaMemcpyAsync(s->stage, ref, bytes, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+        dref = s->stage;
+    }
+    double* d_out = s->d_red + reduce_parts_needed();
+    cudaError_t e = launch_reduce(s->g, s->r.st, s->lev[s->cur], field, s->r.ref[field], 3, dref, dtype, s->d_red,
+                                  reduce_parts_needed(), d_out, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce kernel");
+    double host[4];
+    e = cudaMemcpyAsync(host, d_out, sizeof(host), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    out[0] = host[1] > 0 ? host[0] / host[1] : host[0];
+    out[1] = host[2];
+    out[2] = host[3];
+    return MMFD_OK;
+}
+
+namespace {
+
+// Rows per CTA for the 2D march kernels: balance the 2-row halo overhead against the wave
+// quantisation of (strips x segments) CTAs over the resident CTA slots.
+int pick_rows(int nx, int ny, int cta_cols, int resident) {
+    static const int cand[] = {16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 128, 160, 192, 256};
+    const long long strips = (nx + cta_cols - 1) / cta_cols;
+    double best = -1.0;
+    int bestH = 64;
+    for (int H : cand) {
+        const long long segs = (ny + H - 1) / H;
+        const long long blocks = strips * segs;
+        const long long waves = (blocks + resident - 1) / resident;
+        const double fill = (double)blocks / (double)(waves * resident);
+        const double halo = (double)H / (double)(H + 2);
+        const double eff = fill * halo;
+        if (eff > best + 1e-9) {
+            best = eff;
+            bestH = H;
+        }
+        if (segs == 1) break;
+    }
+    return bestH;
+}
+
+}  // namespace
+
+int solver_pick_kernels(Solver* s) {
+    s->fn_block = nullptr;
+    s->depth = 1;
+    s->variant = 0;
+    s->use_tma = false;
+    s->fn = nullptr;
+    const char* force = std::getenv("MMFD_FORCE_KERNEL");
+    const bool want_direct = force && std::strcmp(force, "direct") == 0;
+    if (s->r.dim == 2 && s->g.nx >= 128 && !want_direct) {
+        s->fn = find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        if (s->fn) {
+            const int es = s->g.es;
+            const int boxw = 128 + 2 * (16 / es);
+            for (int b = 0; b < s->nlev; ++b)
+                for (int f = 0; f < s->g.nf; ++f) {
+                    char* base = static_cast<char*>(s->lev[b]) + (size_t)f * s->g.fs * es;
+                    if (encode_field_map(&s->tmaps[b][f], base, s->r.st, s->g, boxw, 1, 1) != 0) {
+                        s->fn = nullptr;
+                        break;
+                    }
+                }
+        }
+        if (s->fn) {
+            int dev = 0, sms = 152;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            s->use_tma = true;
+            s->kernel_name = "k_march2d";
+            s->H = pick_rows(s->g.nx, s->g.ny, 512, sms * 3);
+            return MMFD_OK;
+        }
+    }
+    s->fn = find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+    s->kernel_name = "k_direct";
+    if (!s->fn) return set_error(MMFD_ERR_UNSUPPORTED, "no kernel for this lattice/PDE/levels/storage");
+    return MMFD_OK;
+}
+
+}  // namespace mmfd

@@ -1,0 +1,155 @@
+// stencil.cuh -- device building blocks of the MMFD update (see mmfd_internal.h for the
+// paired central form the kernels evaluate).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "mmfd_internal.h"
+
+namespace mmfd {
+
+// ------------------------------------------------------------------ storage traits
+template <int ST> struct Storage;
+template <> struct Storage<ST_F64> {
+    using S = double;
+    using T = double;
+    __device__ static T load(const S* p, T) { return *p; }
+    __device__ static S pack(T v, T, unsigned) { return v; }
+};
+template <> struct Storage<ST_F32> {
+    using S = float;
+    using T = float;
+    __device__ static T load(const S* p, T) { return *p; }
+    __device__ static S pack(T v, T, unsigned) { return v; }
+};
+template <> struct Storage<ST_BF16> {
+    using S = __nv_bfloat16;
+    using T = float;
+    __device__ static T load(const S* p, T ref) { return ref + __bfloat162float(*p); }
+    // round-to-nearest-even of the offset (rnd == 0), or stochastic rounding with the
+    // 16 random low bits `rnd` added before truncation.
+    __device__ static S pack(T v, T ref, unsigned rnd) {
+        float d = v - ref;
+        if (rnd == 0u) return __float2bfloat16_rn(d);
+        unsigned b = __float_as_uint(d);
+        if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(d);  // inf / nan
+        b += (rnd & 0xffffu);
+        return __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
+};
+
+// SplitMix64 finaliser as a counter-based hash (stochastic rounding bits).
+__device__ __forceinline__ unsigned sr_bits(unsigned long long seed, long long step, long long node, int f) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(step * 8 + f + 1) +
+                           0xD1B54A32D192ED03ull * (unsigned long long)node;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (unsigned)(z & 0xffffu) | 1u;  // never 0 (0 selects nearest rounding)
+}
+
+// ------------------------------------------------------------------ node basis
+// Fields at one node -> E_p, O_p of pair p (PDE-specific arguments of Eq. (3-3)).
+template <int LAT, int PDE, typename T>
+struct Basis;
+
+// NCDE (Eq. (NCDEfeq)): A = phi, B_a = flux_a(phi), C = (M2(phi) - cs_a^2 phi) I folded into
+// E_p = ePhi_p phi + eM2_p M2(phi).
+template <int LAT, typename T>
+struct Basis<LAT, PDE_NCDE, T> {
+    static constexpr int D = lat_dim(LAT);
+    T phi, m2, B[3];
+    __device__ __forceinline__ void init(const T* f, const Coef<T>& c) {
+        phi = f[0];
+        m2 = (((c.m2[4] * phi + c.m2[3]) * phi + c.m2[2]) * phi + c.m2[1]) * phi + c.m2[0];
+#pragma unroll
+        for (int a = 0; a < D; ++a) B[a] = ((c.flux[a][3] * phi + c.flux[a][2]) * phi + c.flux[a][1]) * phi + c.flux[a][0];
+    }
+    __device__ __forceinline__ T A() const { return phi; }
+    __device__ __forceinline__ T rest(const Coef<T>& c) const { return c.rPhi * phi + c.rM2 * m2; }
+    template <int P>
+    __device__ __forceinline__ void eo(const Coef<T>& c, T& E, T& O) const {
+        E = c.ePhi[P] * phi + c.eM2[P] * m2;
+        T o = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (pair_e(LAT, P, a) != 0) o += c.oB[P][a] * B[a];
+        O = o;
+    }
+    __device__ __forceinline__ T mom(int) const { return T(0); }
+};
+
+// NSE, He-Luo (Remark 4): A = rho, B = rho0 u, C = rho0 u u; rho0 is folded into eC and oB,
+// so E_p = eA rho + eC . (u u), O_p = oB . u.
+template <int LAT, typename T>
+struct Basis<LAT, PDE_NSE, T> {
+    static constexpr int D = lat_dim(LAT);
+    T rho, u[3];
+    __device__ __forceinline__ void init(const T* f, const Coef<T>&) {
+        rho = f[0];
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[a] = f[1 + a];
+    }
+    __device__ __forceinline__ T A() const { return rho; }
+    __device__ __forceinline__ T cc(int k) const {
+        // (xx, yy, zz, xy, xz, yz)
+        return k == 0 ? u[0] * u[0] : k == 1 ? u[1] * u[1] : k == 2 ? u[2] * u[2]
+             : k == 3 ? u[0] * u[1] : k == 4 ? u[0] * u[2] : u[1] * u[2];
+    }
+    __device__ __forceinline__ T rest(const Coef<T>& c) const {
+        T r = c.rA * rho;
+#pragma unroll
+        for (int a = 0; a < D; ++a) r += c.rC[a] * u[a] * u[a];
+        return r;
+    }
+    template <int P>
+    __device__ __forceinline__ void eo(const Coef<T>& c, T& E, T& O) const {
+        T e = c.eA[P] * rho;
+#pragma unroll
+        for (int a = 0; a < D; ++a) e += c.eC[P][a] * u[a] * u[a];
+        if (pair_e(LAT, P, 0) * pair_e(LAT, P, 1) != 0) e += c.eC[P][3] * u[0] * u[1];
+        if (D == 3) {
+            if (pair_e(LAT, P, 0) * pair_e(LAT, P, 2) != 0) e += c.eC[P][4] * u[0] * u[2];
+            if (pair_e(LAT, P, 1) * pair_e(LAT, P, 2) != 0) e += c.eC[P][5] * u[1] * u[2];
+        }
+        T o = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (pair_e(LAT, P, a) != 0) o += c.oB[P][a] * u[a];
+        E = e;
+        O = o;
+    }
+    __device__ __forceinline__ T mom(int a) const { return u[a]; }
+};
+
+// ------------------------------------------------------------------ ghost write-through
+// Write value v of node (x, y, z) to its interior slot and to every periodic ghost image
+// (x == 0 also lands at x = nx, x == nx - 1 also at x = -1; likewise y, z; all combinations).
+template <int DIM, typename S>
+__device__ __forceinline__ void store_with_ghosts(S* f, const Geom& g, int x, int y, int z, S v) {
+    int xs[3], ys[3], zs[3];
+    int nxs = 0, nys = 0, nzs = 0;
+    xs[nxs++] = x;
+    if (x == 0) xs[nxs++] = g.nx;
+    if (x == g.nx - 1) xs[nxs++] = -1;
+    ys[nys++] = y;
+    if (y == 0) ys[nys++] = g.ny;
+    if (y == g.ny - 1) ys[nys++] = -1;
+    zs[nzs++] = z;
+    if (DIM == 3) {
+        if (z == 0) zs[nzs++] = g.nz;
+        if (z == g.nz - 1) zs[nzs++] = -1;
+    }
+    for (int k = 0; k < nzs; ++k)
+        for (int j = 0; j < nys; ++j)
+            for (int i = 0; i < nxs; ++i) f[g.at(xs[i], ys[j], zs[k])] = v;
+}
+
+template <int LAT>
+__device__ __forceinline__ long long pair_offset(const Geom& g, int p) {
+    return (long long)pair_e(LAT, p, 0) + (long long)pair_e(LAT, p, 1) * g.py +
+           (lat_dim(LAT) == 3 ? (long long)pair_e(LAT, p, 2) * g.pz : 0ll);
+}
+
+}  // namespace mmfd
