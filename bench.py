@@ -149,6 +149,103 @@ class OracleTimer:
         return mlups, sample
 
 
+def serving_bench(count, seed, mmfd, stream, budget_gb=40.0, slots=64, steps_per_tick=16):
+    """Config 5: a seeded Poisson stream of mixed CDE/NCDE/NSE solves.
+
+    plain: each request alone through the single-solve API (create, upload, step, read back),
+    first-come first-served; latency from a FIFO replay of the measured service times.
+    served: the continuous-batching server, real time, open-loop arrivals.
+    Arrival rate: 0.8 x the plain path's capacity.
+    """
+    import numpy as np
+    from paper_2505_17057_gb300 import serving
+
+    reqs = serving.make_stream(count, seed=seed, storage_mix=True)
+    total_lu = float(sum(r.nodes * r.steps for r in reqs))
+    # plain per-solve FP32
+    service, plain_out = [], []
+    for r in reqs:
+        d = dict(r.desc)
+        d["storage"] = "fp32"
+        t0 = time.perf_counter()
+        s = mmfd.Solver(mmfd.make_desc(**d), stream=stream)
+        s.set_fields(r.fields)
+        s.step(r.steps)
+        out = s.fields(0)
+        s.close()
+        service.append(time.perf_counter() - t0)
+        plain_out.append(out)
+    capacity = count / sum(service)
+    arrivals = serving.poisson_arrivals(count, 0.8 * capacity, seed=seed)
+    t_free, plain_lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        start = max(a, t_free)
+        t_free = start + sv
+        plain_lat.append(t_free - a)
+    plain_makespan = t_free - arrivals[0]
+
+    def served(storage_mode):
+        srv = mmfd.Server(int(budget_gb * (1 << 30)), max_slots=slots, steps_per_tick=steps_per_tick,
+                          use_graphs=True, stream=stream)
+        descs = []
+        for r in reqs:
+            d = dict(r.desc)
+            if storage_mode == "fp32":
+                d["storage"] = "fp32"
+            descs.append(mmfd.make_desc(**d))
+        finish = np.zeros(count)
+        outs = [None] * count
+        pending = {}
+        i, done = 0, 0
+        t0 = time.perf_counter()
+        while done < count:
+            now = time.perf_counter() - t0
+            while i < count and arrivals[i] <= now:
+                pending[srv.submit(descs[i], reqs[i].fields, reqs[i].steps)] = i
+                i += 1
+            progressed = False
+            for t in list(pending):
+                rc, res = srv.poll(t)
+                if rc == mmfd.MMFD_OK:
+                    k = pending.pop(t)
+                    outs[k] = srv.result(t)
+                    finish[k] = time.perf_counter() - t0
+                    srv.release(t)
+                    done += 1
+                    progressed = True
+            if not pending and i < count:
+                wait = arrivals[i] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.001))
+            elif not progressed:
+                time.sleep(0.0001)
+        st = srv.stats()
+        srv.close()
+        lat = finish - arrivals
+        makespan = float(finish.max() - arrivals[0])
+        return lat, makespan, outs, st
+
+    def summary(lat, makespan):
+        lat_ms = np.asarray(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mlups": total_lu / makespan / 1e6, "makespan_s": makespan}
+
+    lat32, mk32, out32, st32 = served("fp32")
+    latmix, mkmix, outmix, stmix = served("mixed")
+    err32 = max(max(float(np.abs(a - b).max() / max(1e-30, np.abs(b).max())) for a, b in zip(o, p))
+                for o, p in zip(out32, plain_out))
+    errmix = max(max(float(np.abs(a - b).max() / max(1e-30, np.abs(b).max())) for a, b in zip(o, p))
+                 for o, p in zip(outmix, plain_out))
+    res = {"requests": count, "seed": seed, "arrival_rate_per_s": 0.8 * capacity, "total_lattice_updates": total_lu,
+           "plain_fp32": summary(plain_lat, plain_makespan),
+           "served_fp32": {**summary(lat32, mk32), "max_rel_err_vs_plain": err32,
+                           "ticks": st32["ticks"], "launches": st32["launches"], "graph_replays": st32["graph_replays"]},
+           "served_mixed_fp32_bf16": {**summary(latmix, mkmix), "max_rel_err_vs_plain_fp32": errmix},
+           "budget_gb": budget_gb, "max_slots": slots, "steps_per_tick": steps_per_tick}
+    res["served_fp32_vs_plain_mlups"] = res["served_fp32"]["mlups"] / res["plain_fp32"]["mlups"]
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -292,6 +389,9 @@ def run_ours(args):
                 "steps": e2e_steps},
         "gpu_launches": args.steps,
     }
+    if args.serve > 0:
+        with torch.cuda.stream(stream):
+            line["serving"] = serving_bench(args.serve, 5, mmfd, stream)
     if ws == 1 and not args.no_cpu_baseline:
         timer = OracleTimer(args.workload)
         v, sample = timer.measure(10.0)
@@ -312,6 +412,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--depth", type=int, default=1, help="temporal blocking depth (1 = plain step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", type=int, default=200, help="requests in the serving run (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -176,6 +176,13 @@ int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3])
 /* Resolve a descriptor's constants without touching the GPU (info filled as by create). */
 int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out);
 
+/* Diagnostic: launch a kernel whose mbarrier wait can never complete and check that the
+ * bounded wait gives up after budget_cycles SM clocks.  Returns MMFD_ERR_TIMEOUT when the
+ * failure path works (the expected result), MMFD_OK if the wait unexpectedly completed, or
+ * MMFD_ERR_CUDA.  Nothing traps; the CUDA context stays usable.  No counterpart in the paper:
+ * it exercises the library's own failure detection. */
+int mmfd_selftest_wait_timeout(void* stream, long long budget_cycles);
+
 const char* mmfd_strerror(int status);
 /* Text of the last error on this thread (CUDA error string or validation message). */
 const char* mmfd_last_error(void);

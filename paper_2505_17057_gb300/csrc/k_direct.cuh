@@ -18,20 +18,21 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
+// The update of one node (x, y, z): reads levels t (in0) and t - dt (in1) in the ghosted
+// layout, writes level t + dt (out) and its periodic ghost images.  Shared by the one-solve
+// kernel below and the batched multi-request kernel, so a request computes the same bits
+// alone and inside a batch.
 template <int LAT, int PDE, int LEVELS, int ST>
-__global__ void __launch_bounds__(256) k_direct(Geom g, const void* __restrict__ in0v,
-                                                const void* __restrict__ in1v, void* __restrict__ outv,
-                                                Coef<typename Storage<ST>::T> cf, StepExtra ex) {
+__device__ __forceinline__ void direct_node(const Geom& g, const void* __restrict__ in0v,
+                                            const void* __restrict__ in1v, void* __restrict__ outv,
+                                            const Coef<typename Storage<ST>::T>& cf, const StepExtra& ex,
+                                            int x, int y, int z) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
     constexpr int D = lat_dim(LAT);
     constexpr int NP = lat_npair(LAT);
     constexpr int NF = pde_nf(PDE, LAT);
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
     const long long c0 = g.at(x, y, z);
     T acc[NF];
 #pragma unroll
@@ -92,6 +93,17 @@ __global__ void __launch_bounds__(256) k_direct(Geom g, const void* __restrict__
         const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, node, i) : 0u;
         store_with_ghosts<D>(out + i * g.fs, g, x, y, z, Tr::pack(acc[i], cf.ref[i], rnd));
     }
+}
+
+template <int LAT, int PDE, int LEVELS, int ST>
+__global__ void __launch_bounds__(256) k_direct(Geom g, const void* __restrict__ in0v,
+                                                const void* __restrict__ in1v, void* __restrict__ outv,
+                                                Coef<typename Storage<ST>::T> cf, StepExtra ex) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    direct_node<LAT, PDE, LEVELS, ST>(g, in0v, in1v, outv, cf, ex, x, y, z);
 }
 
 template <int LAT, int PDE, int LEVELS, int ST>

@@ -5,12 +5,12 @@ namespace mmfd {
 
 namespace {
 
-// Ring depth: about 64 KB of stages per CTA, between 3 and 16 rows in flight.
+// Ring depth per warp: about 8 KB of stages, between 3 and 12 rows in flight.
 template <int LAT, int PDE, int LEVELS, int ST>
 constexpr int march2d_stages() {
-    constexpr size_t per = march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 4, 1>() - 128;
-    constexpr size_t n = 65536 / per;
-    return n < 3 ? 3 : (n > 16 ? 16 : (int)n);
+    constexpr size_t per = (size_t)pde_nf(PDE, LAT) * (LEVELS - 1) * MarchCfg<ST>::SLOT;
+    constexpr size_t n = 8192 / per;
+    return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
 }
 
 template <int LAT, int PDE, int LEVELS, int ST>

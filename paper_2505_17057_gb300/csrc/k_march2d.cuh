@@ -1,21 +1,22 @@
-// k_march2d.cuh -- 2D MMFD step: row-marching CTAs fed by a TMA shared-memory ring.
+// k_march2d.cuh -- 2D MMFD step: row-marching warps, each fed by its own TMA shared-memory ring.
 //
-// A CTA owns a strip of NW * 128 columns and H rows.  Each warp owns 128 columns (4
-// consecutive nodes per lane).  Thread 0 streams the input rows y0-1 .. y0+H of every stored
-// field and input level through an NSTAGE-deep ring: one cp.async.bulk.tensor.2d box of
-// 128 + 2 * (16 bytes) columns per warp, per field, per row, completing on the stage's
-// mbarrier.  Every input row is read from shared memory once and pushed into register
-// accumulators of the three output rows it touches (r-1, r, r+1) -- the paired central form
-// of the MMFD update (see mmfd_internal.h).  After row r the accumulators of row r-1 are
-// complete and are stored with 16-byte vector stores (plus periodic ghost images at the
-// domain edges).  Waits are bounded: on timeout the CTA records KERR_TMA_TIMEOUT in the
-// solver's device flag, waits (bounded) for its own copies still in flight, and exits.
+// A warp owns items of 128 columns x H rows (4 consecutive nodes per lane).  Its lane 0
+// streams the input rows y0-1 .. y0+H of every stored field and input level through a private
+// NSTAGE-deep ring: one cp.async.bulk.tensor.2d box of 128 + 2 x (16 bytes) columns per field
+// per row, completing on the stage's mbarrier.  Every input row is read from shared memory
+// once and pushed into register accumulators of the three output rows it touches
+// (r-1, r, r+1) -- the paired central form of the MMFD update (see mmfd_internal.h).  After
+// row r the accumulators of row r-1 are complete and are stored with vector stores (plus the
+// periodic ghost images at the domain edges).  No CTA-wide barrier is used after start-up.
+// Waits are bounded: on timeout the warp records KERR_TMA_TIMEOUT in the solver's device flag,
+// waits (bounded) for its own copies still in flight, and exits.
 #pragma once
 
 #include <type_traits>
 
 #include "k_direct.cuh"
 #include "kernels.h"
+#include "pack2.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
 
@@ -65,10 +66,24 @@ __device__ __forceinline__ void stg4(void* p, const typename Storage<ST>::S s[4]
     }
 }
 
+// Work decomposition: an item is (128-column warp strip, H-row segment).  Every warp walks its
+// own sequence of items (item = global warp id, + total warps, ...) as one stream of input
+// rows; lane 0 keeps NSTAGE rows of that stream in flight through the warp's private ring, so
+// the prefetch runs across item boundaries and warps never wait for one another.
+struct RowCursor {
+    int item;  // current item
+    int row;   // input row index within the item (0 .. nrows - 1)
+};
+
+__device__ __forceinline__ int march_item_rows(int item, int strips, int H, int ny) {
+    const int seg = item / strips;
+    return min(H, ny - seg * H) + 2;
+}
+
 template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE>
 __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ TmapSet maps, Geom g,
                                                      void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
-                                                     StepExtra ex, int H, int* __restrict__ err) {
+                                                     StepExtra ex, int H, int nitems, int* __restrict__ err) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
@@ -77,152 +92,198 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     constexpr int NIN = NF * (LEVELS - 1);
     constexpr int NP = lat_npair(LAT);
     constexpr int D = 2;
+    constexpr uint32_t kTx = (uint32_t)(NIN * Cfg::BOXW * Cfg::ES);
+    constexpr size_t kRingBytes = (size_t)NSTAGE * NIN * Cfg::SLOT;
 
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    unsigned char* ring = smem + 128;
-
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations must sit on 128-byte boundaries whatever the dynamic-smem base is
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * (NW * kWarpCols);
-    const int y0 = blockIdx.y * H;
-    const int heff = min(H, g.ny - y0);
-    const int nrows = heff + 2;
-    constexpr uint32_t kTx = (uint32_t)(NIN * NW * Cfg::BOXW * Cfg::ES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem) + warp * NSTAGE;
+    unsigned char* ring = smem + 128 * ((NW * NSTAGE * 8 + 127) / 128) + warp * kRingBytes;
 
-    auto slot = [&](int s, int q, int w) -> unsigned char* {
-        return ring + (size_t)((s * NIN + q) * NW + w) * Cfg::SLOT;
-    };
-    auto issue = [&](int i) {
-        const int s = i % NSTAGE;
+    const int strips = (g.nx + kWarpCols - 1) / kWarpCols;
+    const int wstride = gridDim.x * NW;
+    const int wid = blockIdx.x * NW + warp;
+    if (wid >= nitems) return;
+
+    auto slot = [&](int s, int q) -> unsigned char* { return ring + (size_t)(s * NIN + q) * Cfg::SLOT; };
+
+    // producer (lane 0): row stream cursor and count of rows issued
+    RowCursor pc{wid, 0};
+    long long issued = 0;
+    auto issue_next = [&]() {
+        if (pc.item >= nitems) return;
+        const int s = (int)(issued % NSTAGE);
         mbar_arrive_expect_tx(&full[s], kTx);
-        const int prow = y0 + i;  // padded row of input row y0 - 1 + i
+        const int xcol = (pc.item % strips) * kWarpCols;             // padded column of the box
+        const int prow = (pc.item / strips) * H + pc.row;            // padded row of input row y0 - 1 + row
 #pragma unroll
-        for (int q = 0; q < NIN; ++q)
-#pragma unroll
-            for (int w = 0; w < NW; ++w) tma_load_2d(slot(s, q, w), &maps.m[q], &full[s], x0 + w * kWarpCols, prow);
+        for (int q = 0; q < NIN; ++q) tma_load_2d(slot(s, q), &maps.m[q], &full[s], xcol, prow);
+        ++issued;
+        if (++pc.row == march_item_rows(pc.item, strips, H, g.ny)) {
+            pc.item += wstride;
+            pc.row = 0;
+        }
     };
 
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < NSTAGE; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
 #pragma unroll
         for (int q = 0; q < NIN; ++q) tma_prefetch_desc(&maps.m[q]);
+        for (int k = 0; k < NSTAGE; ++k) issue_next();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int first = nrows < NSTAGE ? nrows : NSTAGE;
-        for (int i = 0; i < first; ++i) issue(i);
-    }
+    __syncwarp();
 
-    T accP[kLaneNodes][NF], accC[kLaneNodes][NF], accN[kLaneNodes][NF];
-#pragma unroll
-    for (int k = 0; k < kLaneNodes; ++k)
-#pragma unroll
-        for (int f = 0; f < NF; ++f) accP[k][f] = accC[k][f] = accN[k][f] = T(0);
-
-    const int xb = x0 + warp * kWarpCols + lane * kLaneNodes;  // first node of this lane
+    // Accumulators of the three output rows r-1, r, r+1 this lane is building.  Each holds
+    // the lane's 4 nodes as two packed pairs: pair 0 = nodes (0, 2), pair 1 = nodes (1, 3).
+    using V = typename Pair2<T>::type;
+    V acc0[2][NF], acc1[2][NF], acc2[2][NF];
     S* out = static_cast<S*>(outv);
-    int i = 0;
+    long long consumed = 0;
     bool failed = false;
-    for (; i < nrows; ++i) {
-        const int s = i % NSTAGE;
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((i / NSTAGE) & 1));
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
+
+    // Push one input row into (P = row r-1, Cr = row r, N = row r+1) and, when row r-1 is
+    // complete, store it and clear it (it becomes the next "row r+1").
+    auto row_body = [&](int i, int y0, int xb, V (&P)[2][NF], V (&Cr)[2][NF], V (&N)[2][NF]) -> bool {
+        const int s = (int)(consumed % NSTAGE);
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((consumed / NSTAGE) & 1));
+        if (__any_sync(0xffffffffu, !ok)) return false;
 #pragma unroll
         for (int l = 0; l < LEVELS - 1; ++l) {
-            // raw fields of the 6 nodes xb-1 .. xb+4 of this input row
-            T raw[6][NF];
+            // input groups of node offsets: A = (-1, 1), B = (0, 2), C = (1, 3), D = (2, 4)
+            V grp[4][NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                const unsigned char* base = slot(s, l * NF + f, warp);
+                const unsigned char* base = slot(s, l * NF + f);
                 const S* sp = reinterpret_cast<const S*>(base);
                 T v4[4];
                 lds4<ST>(base + (size_t)(Cfg::ALIGN + lane * kLaneNodes) * Cfg::ES, cf.ref[f], v4);
-                raw[0][f] = Tr::load(sp + Cfg::ALIGN + lane * kLaneNodes - 1, cf.ref[f]);
-                raw[1][f] = v4[0];
-                raw[2][f] = v4[1];
-                raw[3][f] = v4[2];
-                raw[4][f] = v4[3];
-                raw[5][f] = Tr::load(sp + Cfg::ALIGN + lane * kLaneNodes + 4, cf.ref[f]);
+                const T left = Tr::load(sp + Cfg::ALIGN + lane * kLaneNodes - 1, cf.ref[f]);
+                const T right = Tr::load(sp + Cfg::ALIGN + lane * kLaneNodes + 4, cf.ref[f]);
+                grp[0][f] = mk2(left, v4[1]);
+                grp[1][f] = mk2(v4[0], v4[2]);
+                grp[2][f] = mk2(v4[1], v4[3]);
+                grp[3][f] = mk2(v4[2], right);
             }
-            static_for<0, 6>([&](auto cc) {
-                constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. 4
+            static_for<0, 4>([&](auto gc) {
+                constexpr int G = decltype(gc)::value;
+                constexpr int SX = G - 1;  // x offset of the group's first node
+                const V* in = grp[G];
                 if constexpr (PDE == PDE_LCDE) {
-                    const T phi = raw[C + 1][0];
-                    if constexpr (C >= 0 && C < 4) accC[C][0] += cf.W0[l] * phi;
-                    static_for<0, NP>([&](auto pc) {
-                        constexpr int P = decltype(pc)::value;
-                        constexpr int EX = pair_e(LAT, P, 0), EY = pair_e(LAT, P, 1);
-                        constexpr int TP = C - EX, TM = C + EX;
-                        if constexpr (TP >= 0 && TP < 4) {
-                            if constexpr (EY == 1) accP[TP][0] += cf.Wp[l][P] * phi;
-                            else accC[TP][0] += cf.Wp[l][P] * phi;
+                    const V phi = in[0];
+                    if constexpr (SX == 0 || SX == 1) Cr[SX][0] = fma2(bc2(cf.W0[l]), phi, Cr[SX][0]);
+                    static_for<0, NP>([&](auto pcc) {
+                        constexpr int P_ = decltype(pcc)::value;
+                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                        constexpr int OP = SX - EX, OM = SX + EX;
+                        if constexpr (OP == 0 || OP == 1) {
+                            if constexpr (EY == 1) P[OP][0] = fma2(bc2(cf.Wp[l][P_]), phi, P[OP][0]);
+                            else Cr[OP][0] = fma2(bc2(cf.Wp[l][P_]), phi, Cr[OP][0]);
                         }
-                        if constexpr (TM >= 0 && TM < 4) {
-                            if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P] * phi;
-                            else accC[TM][0] += cf.Wm[l][P] * phi;
+                        if constexpr (OM == 0 || OM == 1) {
+                            if constexpr (EY == 1) N[OM][0] = fma2(bc2(cf.Wm[l][P_]), phi, N[OM][0]);
+                            else Cr[OM][0] = fma2(bc2(cf.Wm[l][P_]), phi, Cr[OM][0]);
                         }
                     });
                 } else {
-                    Basis<LAT, PDE, T> b;
-                    b.init(raw[C + 1], cf);
-                    if constexpr (C >= 0 && C < 4) {
-                        accC[C][0] += cf.a0[l] * b.A() + cf.ap[l] * b.rest(cf);
-                        if constexpr (PDE == PDE_NSE) {
+                    // packed basis of the group (arguments of Eq. (3-3))
+                    V A, B[2], m2v, uxx, uyy, uxy;
+                    if constexpr (PDE == PDE_NSE) {
+                        A = in[0];
+                        B[0] = in[1];
+                        B[1] = in[2];
+                        uxx = mul2(in[1], in[1]);
+                        uyy = mul2(in[2], in[2]);
+                        uxy = mul2(in[1], in[2]);
+                    } else {
+                        const V phi = in[0];
+                        A = phi;
+                        m2v = fma2(fma2(fma2(fma2(bc2(cf.m2[4]), phi, bc2(cf.m2[3])), phi, bc2(cf.m2[2])), phi,
+                                        bc2(cf.m2[1])), phi, bc2(cf.m2[0]));
 #pragma unroll
-                            for (int a = 0; a < D; ++a) accC[C][1 + a] += cf.ab0[l] * b.mom(a);
+                        for (int a = 0; a < D; ++a)
+                            B[a] = fma2(fma2(fma2(bc2(cf.flux[a][3]), phi, bc2(cf.flux[a][2])), phi,
+                                             bc2(cf.flux[a][1])), phi, bc2(cf.flux[a][0]));
+                    }
+                    if constexpr (SX == 0 || SX == 1) {
+                        V rest;
+                        if constexpr (PDE == PDE_NSE)
+                            rest = fma2(bc2(cf.rC[1]), uyy, fma2(bc2(cf.rC[0]), uxx, mul2(bc2(cf.rA), A)));
+                        else
+                            rest = fma2(bc2(cf.rM2), m2v, mul2(bc2(cf.rPhi), A));
+                        Cr[SX][0] = fma2(bc2(cf.ap[l]), rest, fma2(bc2(cf.a0[l]), A, Cr[SX][0]));
+                        if constexpr (PDE == PDE_NSE) {
+                            Cr[SX][1] = fma2(bc2(cf.ab0[l]), B[0], Cr[SX][1]);
+                            Cr[SX][2] = fma2(bc2(cf.ab0[l]), B[1], Cr[SX][2]);
                         }
                     }
-                    static_for<0, NP>([&](auto pc) {
-                        constexpr int P = decltype(pc)::value;
-                        constexpr int EX = pair_e(LAT, P, 0), EY = pair_e(LAT, P, 1);
-                        constexpr int TP = C - EX, TM = C + EX;
-                        constexpr bool HP = TP >= 0 && TP < 4, HM = TM >= 0 && TM < 4;
+                    static_for<0, NP>([&](auto pcc) {
+                        constexpr int P_ = decltype(pcc)::value;
+                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                        constexpr int OP = SX - EX, OM = SX + EX;
+                        constexpr bool HP = (OP == 0 || OP == 1), HM = (OM == 0 || OM == 1);
                         if constexpr (HP || HM) {
-                            T E, O;
-                            b.template eo<P>(cf, E, O);
-                            const T sE = cf.ap[l] * E, sO = cf.am[l] * O;
-                            T mE = T(0), mO = T(0);
+                            V E, O;
                             if constexpr (PDE == PDE_NSE) {
-                                mE = cf.abm[l] * E;
-                                mO = cf.abp[l] * O;
+                                E = fma2(bc2(cf.eC[P_][1]), uyy, fma2(bc2(cf.eC[P_][0]), uxx, mul2(bc2(cf.eA[P_]), A)));
+                                if constexpr (EX * EY != 0) E = fma2(bc2(cf.eC[P_][3]), uxy, E);
+                            } else {
+                                E = fma2(bc2(cf.eM2[P_]), m2v, mul2(bc2(cf.ePhi[P_]), A));
                             }
-                            auto add = [&](T (&acc)[kLaneNodes][NF], int node, T sv, T mv) {
-                                acc[node][0] += sv;
+                            if constexpr (EX != 0 && EY != 0)
+                                O = fma2(bc2(cf.oB[P_][1]), B[1], mul2(bc2(cf.oB[P_][0]), B[0]));
+                            else if constexpr (EX != 0)
+                                O = mul2(bc2(cf.oB[P_][0]), B[0]);
+                            else
+                                O = mul2(bc2(cf.oB[P_][1]), B[1]);
+                            const V sE = mul2(bc2(cf.ap[l]), E);
+                            auto push = [&](V (&acc)[2][NF], int o, bool plus) {
+                                // scalar / rho: a+ E +- a- O
+                                acc[o][0] = plus ? fma2(bc2(cf.am[l]), O, add2(acc[o][0], sE))
+                                                 : fma2(bc2(-cf.am[l]), O, add2(acc[o][0], sE));
                                 if constexpr (PDE == PDE_NSE) {
-                                    if constexpr (EX != 0) acc[node][1] += T(EX) * cf.fmom[0] * mv;
-                                    if constexpr (EY != 0) acc[node][2] += T(EY) * cf.fmom[1] * mv;
+                                    // momentum: e_a (c_a / rho0) (abar+ O +- abar- E)
+                                    const V mv = plus ? fma2(bc2(cf.abm[l]), E, mul2(bc2(cf.abp[l]), O))
+                                                      : fma2(bc2(-cf.abm[l]), E, mul2(bc2(cf.abp[l]), O));
+                                    if constexpr (EX != 0) acc[o][1] = fma2(bc2(T(EX) * cf.fmom[0]), mv, acc[o][1]);
+                                    if constexpr (EY != 0) acc[o][2] = fma2(bc2(T(EY) * cf.fmom[1]), mv, acc[o][2]);
                                 }
                             };
                             if constexpr (HP) {
-                                if constexpr (EY == 1) add(accP, TP, sE + sO, mO + mE);
-                                else add(accC, TP, sE + sO, mO + mE);
+                                if constexpr (EY == 1) push(P, OP, true);
+                                else push(Cr, OP, true);
                             }
                             if constexpr (HM) {
-                                if constexpr (EY == 1) add(accN, TM, sE - sO, mO - mE);
-                                else add(accC, TM, sE - sO, mO - mE);
+                                if constexpr (EY == 1) push(N, OM, false);
+                                else push(Cr, OM, false);
                             }
                         }
                     });
                 }
             });
         }
+        ++consumed;
+        __syncwarp();  // every lane is done reading stage s
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue_next();
+        }
         // row y0 - 1 + i - 1 is complete
-        if (i >= 2) {
+        if (i >= 2 && xb < g.nx) {
             const int yo = y0 + i - 2;
             const long long nb = (long long)yo * g.nx;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
+                const T vals[4] = {lo(P[0][f]), lo(P[1][f]), hi(P[0][f]), hi(P[1][f])};
                 S sv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k, f) : 0u;
-                    sv[k] = Tr::pack(accP[k][f], cf.ref[f], rnd);
+                    sv[k] = Tr::pack(vals[k], cf.ref[f], rnd);
                 }
                 S* fo = out + (size_t)f * g.fs;
                 const bool interior = xb > 0 && xb + 3 < g.nx - 1 && yo > 0 && yo < g.ny - 1;
@@ -236,32 +297,40 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
             }
         }
 #pragma unroll
-        for (int k = 0; k < kLaneNodes; ++k)
+        for (int o = 0; o < 2; ++o)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                accP[k][f] = accC[k][f];
-                accC[k][f] = accN[k][f];
-                accN[k][f] = T(0);
-            }
-        __syncthreads();  // every warp is done with stage s
-        if (threadIdx.x == 0 && i + NSTAGE < nrows) {
-            fence_proxy_async_smem();
-            issue(i + NSTAGE);
+            for (int f = 0; f < NF; ++f) P[o][f] = bc2(T(0));
+        return true;
+    };
+
+    for (int item = wid; item < nitems && !failed; item += wstride) {
+        const int x0 = (item % strips) * kWarpCols;
+        const int y0 = (item / strips) * H;
+        const int nrows = march_item_rows(item, strips, H, g.ny);
+        const int xb = x0 + lane * kLaneNodes;
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc0[o][f] = acc1[o][f] = acc2[o][f] = bc2(T(0));
+        // rows rotate through the three accumulator sets without register moves
+        for (int i = 0; i < nrows && !failed; i += 3) {
+            if (!row_body(i, y0, xb, acc0, acc1, acc2)) { failed = true; break; }
+            if (i + 1 < nrows && !row_body(i + 1, y0, xb, acc1, acc2, acc0)) { failed = true; break; }
+            if (i + 2 < nrows && !row_body(i + 2, y0, xb, acc2, acc0, acc1)) { failed = true; break; }
         }
     }
-    if (failed) {
-        if (threadIdx.x == 0) {
-            atomicExch(err, KERR_TMA_TIMEOUT);
-            const int last = min(nrows, i + NSTAGE);
-            for (int j = i; j < last; ++j) mbar_wait_bounded(&full[j % NSTAGE], (uint32_t)((j / NSTAGE) & 1));
-        }
-        __syncthreads();
+    if (failed && lane == 0) {
+        atomicExch(err, KERR_TMA_TIMEOUT);
+        // wait (bounded) for every copy this warp issued but did not consume
+        for (long long k = consumed; k < issued; ++k)
+            mbar_wait_bounded(&full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1));
     }
+    __syncwarp();
 }
 
 template <int ST, int LEVELS, int NF, int NW, int NSTAGE>
 constexpr size_t march2d_smem() {
-    return 128 + (size_t)NSTAGE * NF * (LEVELS - 1) * NW * MarchCfg<ST>::SLOT;
+    return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * NF * (LEVELS - 1) * MarchCfg<ST>::SLOT;
 }
 
 template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE>
@@ -270,16 +339,40 @@ cudaError_t launch_march2d_t(const LaunchArgs& a) {
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE>();
     auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static int resident = 0;
+    if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, smem);
+        if (e != cudaSuccess) return e;
+        resident = (per_sm > 0 ? per_sm : 1) * sms;
     }
-    const int H = a.H > 0 ? a.H : 64;
-    dim3 grid((a.g.nx + NW * kWarpCols - 1) / (NW * kWarpCols), (a.g.ny + H - 1) / H, 1);
+    const int strips = (a.g.nx + kWarpCols - 1) / kWarpCols;
+    int H = a.H;
+    if (H <= 0) {
+        // rows per item: maximise (useful rows / streamed rows) x (fill of the resident warp slots)
+        const long long wslots = (long long)resident * NW;
+        double best = -1.0;
+        for (int h = 8; h <= 256; ++h) {
+            const long long items = (long long)strips * ((a.g.ny + h - 1) / h);
+            const long long rounds = (items + wslots - 1) / wslots;
+            const double fill = (double)items / (double)(rounds * wslots);
+            const double eff = fill * (double)h / (double)(h + 2);
+            if (eff > best + 1e-9) {
+                best = eff;
+                H = h;
+            }
+            if (h >= a.g.ny) break;
+        }
+    }
+    const int nitems = strips * ((a.g.ny + H - 1) / H);
+    const int blocks_needed = (nitems + NW - 1) / NW;
+    const int grid = blocks_needed < resident ? blocks_needed : resident;
     kern<<<grid, NW * 32, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
-                                             a.err);
+                                             nitems, a.err);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,7 @@
 namespace mmfd {
 
 // Up to 8 TMA tensor maps (nf fields x input levels), passed to a kernel as a grid constant.
-struct alignas(64) TmapSet {
+struct TmapSet {
     CUtensorMap m[8];
 };
 

@@ -239,33 +239,6 @@ int solver_error_norms(Solver* s, int field, const void* ref, int where, int dty
     return MMFD_OK;
 }
 
-namespace {
-
-// Rows per CTA for the 2D march kernels: balance the 2-row halo overhead against the wave
-// quantisation of (strips x segments) CTAs over the resident CTA slots.
-int pick_rows(int nx, int ny, int cta_cols, int resident) {
-    static const int cand[] = {16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 128, 160, 192, 256};
-    const long long strips = (nx + cta_cols - 1) / cta_cols;
-    double best = -1.0;
-    int bestH = 64;
-    for (int H : cand) {
-        const long long segs = (ny + H - 1) / H;
-        const long long blocks = strips * segs;
-        const long long waves = (blocks + resident - 1) / resident;
-        const double fill = (double)blocks / (double)(waves * resident);
-        const double halo = (double)H / (double)(H + 2);
-        const double eff = fill * halo;
-        if (eff > best + 1e-9) {
-            best = eff;
-            bestH = H;
-        }
-        if (segs == 1) break;
-    }
-    return bestH;
-}
-
-}  // namespace
-
 int solver_pick_kernels(Solver* s) {
     s->fn_block = nullptr;
     s->depth = 1;
@@ -289,12 +262,9 @@ int solver_pick_kernels(Solver* s) {
                 }
         }
         if (s->fn) {
-            int dev = 0, sms = 152;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             s->use_tma = true;
             s->kernel_name = "k_march2d";
-            s->H = pick_rows(s->g.nx, s->g.ny, 512, sms * 3);
+            s->H = 0;  // chosen by the launcher from the kernel's occupancy
             return MMFD_OK;
         }
     }

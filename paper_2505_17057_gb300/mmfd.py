@@ -110,6 +110,7 @@ SIGNATURES = {
     "mmfd_destroy": (C.c_int, [_VP]),
     "mmfd_solve_three_level": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mmfd_describe": (C.c_int, [C.POINTER(mmfd_desc), C.POINTER(mmfd_info_t)]),
+    "mmfd_selftest_wait_timeout": (C.c_int, [_VP, C.c_longlong]),
     "mmfd_strerror": (C.c_char_p, [C.c_int]),
     "mmfd_last_error": (C.c_char_p, []),
     "mmfd_server_create": (C.c_int, [C.POINTER(mmfd_server_desc), _PV]),
@@ -225,6 +226,11 @@ def mmfd_get_info(h: int) -> mmfd_info_t:
     info = mmfd_info_t()
     check(lib.mmfd_get_info(h, C.byref(info)), "mmfd_get_info")
     return info
+
+
+def mmfd_selftest_wait_timeout(stream: Optional[int], budget_cycles: int) -> int:
+    """Returns the status code (MMFD_ERR_TIMEOUT is the expected, passing result)."""
+    return lib.mmfd_selftest_wait_timeout(stream, int(budget_cycles))
 
 
 def mmfd_set_stream(h: int, stream: int) -> None:
@@ -419,3 +425,103 @@ def info_dict(info: mmfd_info_t) -> dict:
                 pass
         out[name] = v
     return out
+
+
+# ------------------------------------------------------------------ solve server
+
+def mmfd_server_create(hbm_budget: int, max_slots: int = 64, steps_per_tick: int = 16, use_graphs: bool = True,
+                       stream: Optional[int] = None) -> int:
+    d = mmfd_server_desc()
+    d.hbm_budget = int(hbm_budget)
+    d.max_slots = int(max_slots)
+    d.steps_per_tick = int(steps_per_tick)
+    d.use_graphs = 1 if use_graphs else 0
+    d.stream = stream
+    h = C.c_void_p()
+    check(lib.mmfd_server_create(C.byref(d), C.byref(h)), "mmfd_server_create")
+    return h.value
+
+
+def mmfd_submit(srv: int, d: mmfd_desc, ptrs: Sequence[int], dtype: int, nsteps: int) -> int:
+    t = C.c_ulonglong()
+    check(lib.mmfd_submit(srv, C.byref(d), _ptr_array(ptrs), dtype, int(nsteps), C.byref(t)), "mmfd_submit")
+    return t.value
+
+
+def mmfd_poll(srv: int, ticket: int):
+    r = mmfd_result()
+    rc = lib.mmfd_poll(srv, ticket, C.byref(r))
+    if rc < 0:
+        raise MMFDError(rc, "mmfd_poll")
+    return rc, r
+
+
+def mmfd_server_drain(srv: int) -> None:
+    check(lib.mmfd_server_drain(srv), "mmfd_server_drain")
+
+
+def mmfd_result_fields(srv: int, ticket: int, ptrs: Sequence[int], where: int, dtype: int) -> None:
+    check(lib.mmfd_result_fields(srv, ticket, _ptr_array(ptrs), where, dtype), "mmfd_result_fields")
+
+
+def mmfd_release(srv: int, ticket: int) -> None:
+    check(lib.mmfd_release(srv, ticket), "mmfd_release")
+
+
+def mmfd_server_get_stats(srv: int) -> mmfd_server_stats:
+    s = mmfd_server_stats()
+    check(lib.mmfd_server_get_stats(srv, C.byref(s)), "mmfd_server_get_stats")
+    return s
+
+
+def mmfd_server_destroy(srv: int) -> None:
+    check(lib.mmfd_server_destroy(srv), "mmfd_server_destroy")
+
+
+class Server:
+    """A solve server; requests go in as numpy fields, results come out as numpy fields."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 64, steps_per_tick: int = 16, use_graphs: bool = True,
+                 stream=None):
+        self.stream_obj = stream
+        sp = stream.cuda_stream if stream is not None else None
+        self.h = mmfd_server_create(hbm_budget, max_slots, steps_per_tick, use_graphs, sp)
+        self.meta = {}
+
+    def submit(self, desc: mmfd_desc, fields, nsteps: int) -> int:
+        arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+        t = mmfd_submit(self.h, desc, [a.ctypes.data for a in arrs], MMFD_DT_F64, nsteps)
+        shape = arrs[0].shape
+        self.meta[t] = (len(arrs), shape)
+        return t
+
+    def poll(self, ticket: int):
+        return mmfd_poll(self.h, ticket)
+
+    def drain(self):
+        mmfd_server_drain(self.h)
+
+    def result(self, ticket: int):
+        nf, shape = self.meta[ticket]
+        outs = [np.empty(shape, dtype=np.float64) for _ in range(nf)]
+        mmfd_result_fields(self.h, ticket, [o.ctypes.data for o in outs], MMFD_HOST, MMFD_DT_F64)
+        return outs
+
+    def release(self, ticket: int):
+        mmfd_release(self.h, ticket)
+        self.meta.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = mmfd_server_get_stats(self.h)
+        return {name: getattr(s, name) for name, _ in s._fields_}
+
+    def close(self):
+        if self.h:
+            mmfd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

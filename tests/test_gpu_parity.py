@@ -213,3 +213,18 @@ def test_determinism_and_resume(mm):
     r = s2.fields(0)
     s2.close()
     assert all(np.array_equal(x, y) for x, y in zip(a, r))
+
+
+def test_bounded_wait_reports_timeout(mm):
+    # a wait that can never complete gives up after its budget and reports MMFD_ERR_TIMEOUT;
+    # the context remains usable for a normal solve afterwards
+    import torch
+    s = torch.cuda.Stream()
+    rc = mm.mmfd_selftest_wait_timeout(s.cuda_stream, 2_000_000)
+    assert rc == mm.MMFD_ERR_TIMEOUT
+    rng = np.random.default_rng(15)
+    kw, prob = G.case("D2Q9", "NSE", 2, [140, 20], "fp64")
+    L0 = G.random_level(prob, rng)
+    _, _, out, _ = run_gpu(mm, kw, L0, None, steps=2)
+    ref, _ = orc.run(prob, L0, None, nsteps=2)
+    assert G.rel_err(out, ref) < 1e-12
