@@ -6,16 +6,28 @@ namespace mmfd {
 namespace {
 
 // Ring depth per warp: about 8 KB of stages, between 3 and 12 rows in flight.
-template <int LAT, int PDE, int LEVELS, int ST>
+template <int LAT, int PDE, int LEVELS, int ST, int LN>
 constexpr int march2d_stages() {
-    constexpr size_t per = (size_t)pde_nf(PDE, LAT) * (LEVELS - 1) * MarchCfg<ST>::SLOT;
+    constexpr size_t per = (march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 1, 1, LN>() - 256);
     constexpr size_t n = 8192 / per;
     return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
 }
 
+template <int LAT, int PDE, int LEVELS, int ST, int LN>
+cudaError_t launch_variant(const LaunchArgs& a) {
+    return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST, LN>(), LN>(a);
+}
+
+// 4 nodes per lane (128-column items: the TMA box of 128 + 2 x 16 bytes stays within the
+// 256-element box limit)
+template <int LAT, int PDE, int LEVELS, int ST>
+cudaError_t launch_any(const LaunchArgs& a) {
+    return launch_variant<LAT, PDE, LEVELS, ST, 4>(a);
+}
+
 template <int LAT, int PDE, int LEVELS, int ST>
 LaunchFn pick() {
-    return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST>()>;
+    return launch_any<LAT, PDE, LEVELS, ST>;
 }
 
 template <int LAT, int PDE>

@@ -16,22 +16,10 @@
 
 #include "k_direct.cuh"
 #include "kernels.h"
-#include "pack2.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
 
 namespace mmfd {
-
-constexpr int kLaneNodes = 4;
-constexpr int kWarpCols = 32 * kLaneNodes;
-
-template <int ST>
-struct MarchCfg {
-    static constexpr int ES = (int)sizeof(typename Storage<ST>::S);
-    static constexpr int ALIGN = 16 / ES;                        // halo elements per side
-    static constexpr int BOXW = kWarpCols + 2 * ALIGN;           // TMA box width (elements)
-    static constexpr int SLOT = ((BOXW * ES + 127) / 128) * 128; // bytes per (warp, field) slot
-};
 
 // Four consecutive values of storage type S from shared memory (aligned) into T.
 template <int ST>
@@ -80,20 +68,70 @@ __device__ __forceinline__ int march_item_rows(int item, int strips, int H, int 
     return min(H, ny - seg * H) + 2;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE>
+// Even / odd parts E_p, O_p of the pairs a node must push (bit p of MASK set), from the node's
+// basis.  On D2Q9 the two diagonal pairs (1,1) and (-1,1) share omega_p and the diagonal
+// Qtilde terms by the lattice's symmetry (App. A), so their common even part is formed once:
+// E_{(+-1,1)} = Ed +- q_xy uxy, O_{(+-1,1)} = +-k_x B_x + k_y B_y.
+template <int LAT, int PDE, int MASK, typename T>
+__device__ __forceinline__ void pair_eo(const Coef<T>& cf, T rho_or_phi, const T* B, T m2, T uxx, T uyy, T uxy,
+                                        T (&E)[4], T (&O)[4]) {
+    if constexpr (PDE == PDE_NSE) {
+        if constexpr (MASK & 1) E[0] = cf.eC[0][1] * uyy + (cf.eC[0][0] * uxx + cf.eA[0] * rho_or_phi);
+        if constexpr (MASK & 2) E[1] = cf.eC[1][1] * uyy + (cf.eC[1][0] * uxx + cf.eA[1] * rho_or_phi);
+        if constexpr (LAT == LAT_D2Q9 && (MASK & 12)) {
+            const T Ed = cf.eC[2][1] * uyy + (cf.eC[2][0] * uxx + cf.eA[2] * rho_or_phi);
+            if constexpr (MASK & 4) E[2] = cf.eC[2][3] * uxy + Ed;
+            if constexpr (MASK & 8) E[3] = Ed - cf.eC[2][3] * uxy;
+        }
+    } else {
+        if constexpr (MASK & 1) E[0] = cf.eM2[0] * m2 + cf.ePhi[0] * rho_or_phi;
+        if constexpr (MASK & 2) E[1] = cf.eM2[1] * m2 + cf.ePhi[1] * rho_or_phi;
+        if constexpr (LAT == LAT_D2Q9 && (MASK & 12)) {
+            const T Ed = cf.eM2[2] * m2 + cf.ePhi[2] * rho_or_phi;
+            E[2] = Ed;
+            E[3] = Ed;
+        }
+    }
+    if constexpr (MASK & 1) O[0] = cf.oB[0][0] * B[0];
+    if constexpr (MASK & 2) O[1] = cf.oB[1][1] * B[1];
+    if constexpr (LAT == LAT_D2Q9 && (MASK & 12)) {
+        const T tx = cf.oB[2][0] * B[0];
+        if constexpr (MASK & 4) O[2] = cf.oB[2][1] * B[1] + tx;
+        if constexpr (MASK & 8) O[3] = cf.oB[2][1] * B[1] - tx;
+    }
+}
+
+// Bit mask of the pairs whose plus or minus target of input node offset C (-1 .. LN) lands
+// on one of the lane's LN output nodes.
+template <int LAT, int LN>
+__host__ __device__ constexpr int pushed_pairs(int C) {
+    int m = 0;
+    for (int p = 0; p < lat_npair(LAT); ++p) {
+        const int ex = pair_e(LAT, p, 0);
+        const int tp = C - ex, tm = C + ex;
+        if ((tp >= 0 && tp < LN) || (tm >= 0 && tm < LN)) m |= 1 << p;
+    }
+    return m;
+}
+
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN>
 __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ TmapSet maps, Geom g,
                                                      void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                      StepExtra ex, int H, int nitems, int* __restrict__ err) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
-    using Cfg = MarchCfg<ST>;
+    constexpr int ES = (int)sizeof(S);
+    constexpr int ALIGN = 16 / ES;
+    constexpr int COLS = 32 * LN;                         // columns per warp item
+    constexpr int BOXW = COLS + 2 * ALIGN;                // TMA box width (elements)
+    constexpr int SLOT = ((BOXW * ES + 127) / 128) * 128; // bytes per (stage, field) slot
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr int NIN = NF * (LEVELS - 1);
     constexpr int NP = lat_npair(LAT);
-    constexpr int D = 2;
-    constexpr uint32_t kTx = (uint32_t)(NIN * Cfg::BOXW * Cfg::ES);
-    constexpr size_t kRingBytes = (size_t)NSTAGE * NIN * Cfg::SLOT;
+    constexpr uint32_t kTx = (uint32_t)(NIN * BOXW * ES);
+    constexpr size_t kRingBytes = (size_t)NSTAGE * NIN * SLOT;
+    static_assert(BOXW <= 256, "TMA box too wide");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations must sit on 128-byte boundaries whatever the dynamic-smem base is
@@ -103,25 +141,26 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     uint64_t* full = reinterpret_cast<uint64_t*>(smem) + warp * NSTAGE;
     unsigned char* ring = smem + 128 * ((NW * NSTAGE * 8 + 127) / 128) + warp * kRingBytes;
 
-    const int strips = (g.nx + kWarpCols - 1) / kWarpCols;
+    const int strips = (g.nx + COLS - 1) / COLS;
     const int wstride = gridDim.x * NW;
     const int wid = blockIdx.x * NW + warp;
     if (wid >= nitems) return;
 
-    auto slot = [&](int s, int q) -> unsigned char* { return ring + (size_t)(s * NIN + q) * Cfg::SLOT; };
+    auto slot = [&](int s, int q) -> unsigned char* { return ring + (size_t)(s * NIN + q) * SLOT; };
 
-    // producer (lane 0): row stream cursor and count of rows issued
+    // producer (lane 0): row stream cursor, ring position of the next issue
     RowCursor pc{wid, 0};
+    int ps = 0;                 // stage of the next issue
     long long issued = 0;
     auto issue_next = [&]() {
         if (pc.item >= nitems) return;
-        const int s = (int)(issued % NSTAGE);
-        mbar_arrive_expect_tx(&full[s], kTx);
-        const int xcol = (pc.item % strips) * kWarpCols;             // padded column of the box
-        const int prow = (pc.item / strips) * H + pc.row;            // padded row of input row y0 - 1 + row
+        mbar_arrive_expect_tx(&full[ps], kTx);
+        const int xcol = (pc.item % strips) * COLS;   // padded column of the box
+        const int prow = (pc.item / strips) * H + pc.row;  // padded row of input row y0 - 1 + row
 #pragma unroll
-        for (int q = 0; q < NIN; ++q) tma_load_2d(slot(s, q), &maps.m[q], &full[s], xcol, prow);
+        for (int q = 0; q < NIN; ++q) tma_load_2d(slot(ps, q), &maps.m[q], &full[ps], xcol, prow);
         ++issued;
+        ps = ps + 1 == NSTAGE ? 0 : ps + 1;
         if (++pc.row == march_item_rows(pc.item, strips, H, g.ny)) {
             pc.item += wstride;
             pc.row = 0;
@@ -138,185 +177,177 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     }
     __syncwarp();
 
-    // Accumulators of the three output rows r-1, r, r+1 this lane is building.  Each holds
-    // the lane's 4 nodes as two packed pairs: pair 0 = nodes (0, 2), pair 1 = nodes (1, 3).
-    using V = typename Pair2<T>::type;
-    V acc0[2][NF], acc1[2][NF], acc2[2][NF];
+    T accP[LN][NF], accC[LN][NF], accN[LN][NF];
     S* out = static_cast<S*>(outv);
+    int cs = 0;              // stage of the next row to consume
+    uint32_t cphase = 0;     // its mbarrier phase parity
     long long consumed = 0;
     bool failed = false;
-
-    // Push one input row into (P = row r-1, Cr = row r, N = row r+1) and, when row r-1 is
-    // complete, store it and clear it (it becomes the next "row r+1").
-    auto row_body = [&](int i, int y0, int xb, V (&P)[2][NF], V (&Cr)[2][NF], V (&N)[2][NF]) -> bool {
-        const int s = (int)(consumed % NSTAGE);
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((consumed / NSTAGE) & 1));
-        if (__any_sync(0xffffffffu, !ok)) return false;
-#pragma unroll
-        for (int l = 0; l < LEVELS - 1; ++l) {
-            // input groups of node offsets: A = (-1, 1), B = (0, 2), C = (1, 3), D = (2, 4)
-            V grp[4][NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const unsigned char* base = slot(s, l * NF + f);
-                const S* sp = reinterpret_cast<const S*>(base);
-                T v4[4];
-                lds4<ST>(base + (size_t)(Cfg::ALIGN + lane * kLaneNodes) * Cfg::ES, cf.ref[f], v4);
-                const T left = Tr::load(sp + Cfg::ALIGN + lane * kLaneNodes - 1, cf.ref[f]);
-                const T right = Tr::load(sp + Cfg::ALIGN + lane * kLaneNodes + 4, cf.ref[f]);
-                grp[0][f] = mk2(left, v4[1]);
-                grp[1][f] = mk2(v4[0], v4[2]);
-                grp[2][f] = mk2(v4[1], v4[3]);
-                grp[3][f] = mk2(v4[2], right);
-            }
-            static_for<0, 4>([&](auto gc) {
-                constexpr int G = decltype(gc)::value;
-                constexpr int SX = G - 1;  // x offset of the group's first node
-                const V* in = grp[G];
-                if constexpr (PDE == PDE_LCDE) {
-                    const V phi = in[0];
-                    if constexpr (SX == 0 || SX == 1) Cr[SX][0] = fma2(bc2(cf.W0[l]), phi, Cr[SX][0]);
-                    static_for<0, NP>([&](auto pcc) {
-                        constexpr int P_ = decltype(pcc)::value;
-                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                        constexpr int OP = SX - EX, OM = SX + EX;
-                        if constexpr (OP == 0 || OP == 1) {
-                            if constexpr (EY == 1) P[OP][0] = fma2(bc2(cf.Wp[l][P_]), phi, P[OP][0]);
-                            else Cr[OP][0] = fma2(bc2(cf.Wp[l][P_]), phi, Cr[OP][0]);
-                        }
-                        if constexpr (OM == 0 || OM == 1) {
-                            if constexpr (EY == 1) N[OM][0] = fma2(bc2(cf.Wm[l][P_]), phi, N[OM][0]);
-                            else Cr[OM][0] = fma2(bc2(cf.Wm[l][P_]), phi, Cr[OM][0]);
-                        }
-                    });
-                } else {
-                    // packed basis of the group (arguments of Eq. (3-3))
-                    V A, B[2], m2v, uxx, uyy, uxy;
-                    if constexpr (PDE == PDE_NSE) {
-                        A = in[0];
-                        B[0] = in[1];
-                        B[1] = in[2];
-                        uxx = mul2(in[1], in[1]);
-                        uyy = mul2(in[2], in[2]);
-                        uxy = mul2(in[1], in[2]);
-                    } else {
-                        const V phi = in[0];
-                        A = phi;
-                        m2v = fma2(fma2(fma2(fma2(bc2(cf.m2[4]), phi, bc2(cf.m2[3])), phi, bc2(cf.m2[2])), phi,
-                                        bc2(cf.m2[1])), phi, bc2(cf.m2[0]));
-#pragma unroll
-                        for (int a = 0; a < D; ++a)
-                            B[a] = fma2(fma2(fma2(bc2(cf.flux[a][3]), phi, bc2(cf.flux[a][2])), phi,
-                                             bc2(cf.flux[a][1])), phi, bc2(cf.flux[a][0]));
-                    }
-                    if constexpr (SX == 0 || SX == 1) {
-                        V rest;
-                        if constexpr (PDE == PDE_NSE)
-                            rest = fma2(bc2(cf.rC[1]), uyy, fma2(bc2(cf.rC[0]), uxx, mul2(bc2(cf.rA), A)));
-                        else
-                            rest = fma2(bc2(cf.rM2), m2v, mul2(bc2(cf.rPhi), A));
-                        Cr[SX][0] = fma2(bc2(cf.ap[l]), rest, fma2(bc2(cf.a0[l]), A, Cr[SX][0]));
-                        if constexpr (PDE == PDE_NSE) {
-                            Cr[SX][1] = fma2(bc2(cf.ab0[l]), B[0], Cr[SX][1]);
-                            Cr[SX][2] = fma2(bc2(cf.ab0[l]), B[1], Cr[SX][2]);
-                        }
-                    }
-                    static_for<0, NP>([&](auto pcc) {
-                        constexpr int P_ = decltype(pcc)::value;
-                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                        constexpr int OP = SX - EX, OM = SX + EX;
-                        constexpr bool HP = (OP == 0 || OP == 1), HM = (OM == 0 || OM == 1);
-                        if constexpr (HP || HM) {
-                            V E, O;
-                            if constexpr (PDE == PDE_NSE) {
-                                E = fma2(bc2(cf.eC[P_][1]), uyy, fma2(bc2(cf.eC[P_][0]), uxx, mul2(bc2(cf.eA[P_]), A)));
-                                if constexpr (EX * EY != 0) E = fma2(bc2(cf.eC[P_][3]), uxy, E);
-                            } else {
-                                E = fma2(bc2(cf.eM2[P_]), m2v, mul2(bc2(cf.ePhi[P_]), A));
-                            }
-                            if constexpr (EX != 0 && EY != 0)
-                                O = fma2(bc2(cf.oB[P_][1]), B[1], mul2(bc2(cf.oB[P_][0]), B[0]));
-                            else if constexpr (EX != 0)
-                                O = mul2(bc2(cf.oB[P_][0]), B[0]);
-                            else
-                                O = mul2(bc2(cf.oB[P_][1]), B[1]);
-                            const V sE = mul2(bc2(cf.ap[l]), E);
-                            auto push = [&](V (&acc)[2][NF], int o, bool plus) {
-                                // scalar / rho: a+ E +- a- O
-                                acc[o][0] = plus ? fma2(bc2(cf.am[l]), O, add2(acc[o][0], sE))
-                                                 : fma2(bc2(-cf.am[l]), O, add2(acc[o][0], sE));
-                                if constexpr (PDE == PDE_NSE) {
-                                    // momentum: e_a (c_a / rho0) (abar+ O +- abar- E)
-                                    const V mv = plus ? fma2(bc2(cf.abm[l]), E, mul2(bc2(cf.abp[l]), O))
-                                                      : fma2(bc2(-cf.abm[l]), E, mul2(bc2(cf.abp[l]), O));
-                                    if constexpr (EX != 0) acc[o][1] = fma2(bc2(T(EX) * cf.fmom[0]), mv, acc[o][1]);
-                                    if constexpr (EY != 0) acc[o][2] = fma2(bc2(T(EY) * cf.fmom[1]), mv, acc[o][2]);
-                                }
-                            };
-                            if constexpr (HP) {
-                                if constexpr (EY == 1) push(P, OP, true);
-                                else push(Cr, OP, true);
-                            }
-                            if constexpr (HM) {
-                                if constexpr (EY == 1) push(N, OM, false);
-                                else push(Cr, OM, false);
-                            }
-                        }
-                    });
-                }
-            });
-        }
-        ++consumed;
-        __syncwarp();  // every lane is done reading stage s
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue_next();
-        }
-        // row y0 - 1 + i - 1 is complete
-        if (i >= 2 && xb < g.nx) {
-            const int yo = y0 + i - 2;
-            const long long nb = (long long)yo * g.nx;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const T vals[4] = {lo(P[0][f]), lo(P[1][f]), hi(P[0][f]), hi(P[1][f])};
-                S sv[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k, f) : 0u;
-                    sv[k] = Tr::pack(vals[k], cf.ref[f], rnd);
-                }
-                S* fo = out + (size_t)f * g.fs;
-                const bool interior = xb > 0 && xb + 3 < g.nx - 1 && yo > 0 && yo < g.ny - 1;
-                if (interior) {
-                    stg4<ST>(fo + g.at(xb, yo, 0), sv);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (xb + k < g.nx) store_with_ghosts<2>(fo, g, xb + k, yo, 0, sv[k]);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < 2; ++o)
-#pragma unroll
-            for (int f = 0; f < NF; ++f) P[o][f] = bc2(T(0));
-        return true;
-    };
-
     for (int item = wid; item < nitems && !failed; item += wstride) {
-        const int x0 = (item % strips) * kWarpCols;
+        const int x0 = (item % strips) * COLS;
         const int y0 = (item / strips) * H;
         const int nrows = march_item_rows(item, strips, H, g.ny);
-        const int xb = x0 + lane * kLaneNodes;
+        const int xb = x0 + lane * LN;
 #pragma unroll
-        for (int o = 0; o < 2; ++o)
+        for (int k = 0; k < LN; ++k)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc0[o][f] = acc1[o][f] = acc2[o][f] = bc2(T(0));
-        // rows rotate through the three accumulator sets without register moves
-        for (int i = 0; i < nrows && !failed; i += 3) {
-            if (!row_body(i, y0, xb, acc0, acc1, acc2)) { failed = true; break; }
-            if (i + 1 < nrows && !row_body(i + 1, y0, xb, acc1, acc2, acc0)) { failed = true; break; }
-            if (i + 2 < nrows && !row_body(i + 2, y0, xb, acc2, acc0, acc1)) { failed = true; break; }
+            for (int f = 0; f < NF; ++f) accP[k][f] = accC[k][f] = accN[k][f] = T(0);
+
+        for (int i = 0; i < nrows; ++i) {
+            const int s = cs;
+            const bool ok = mbar_wait_bounded(&full[s], cphase);
+            if (__any_sync(0xffffffffu, !ok)) {
+                failed = true;
+                break;
+            }
+#pragma unroll
+            for (int l = 0; l < LEVELS - 1; ++l) {
+                // raw fields of the LN + 2 nodes xb-1 .. xb+LN of this input row
+                T raw[LN + 2][NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const unsigned char* base = slot(s, l * NF + f);
+                    const S* sp = reinterpret_cast<const S*>(base);
+#pragma unroll
+                    for (int k4 = 0; k4 < LN; k4 += 4) {
+                        T v4[4];
+                        lds4<ST>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
+                        raw[1 + k4][f] = v4[0];
+                        raw[2 + k4][f] = v4[1];
+                        raw[3 + k4][f] = v4[2];
+                        raw[4 + k4][f] = v4[3];
+                    }
+                    raw[0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
+                    raw[LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
+                }
+                static_for<0, LN + 2>([&](auto cc) {
+                    constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. LN
+                    constexpr bool OWN = C >= 0 && C < LN;
+                    if constexpr (PDE == PDE_LCDE) {
+                        const T phi = raw[C + 1][0];
+                        if constexpr (OWN) accC[C][0] += cf.W0[l] * phi;
+                        static_for<0, NP>([&](auto pcc) {
+                            constexpr int P_ = decltype(pcc)::value;
+                            constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                            constexpr int TP = C - EX, TM = C + EX;
+                            if constexpr (TP >= 0 && TP < LN) {
+                                if constexpr (EY == 1) accP[TP][0] += cf.Wp[l][P_] * phi;
+                                else accC[TP][0] += cf.Wp[l][P_] * phi;
+                            }
+                            if constexpr (TM >= 0 && TM < LN) {
+                                if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P_] * phi;
+                                else accC[TM][0] += cf.Wm[l][P_] * phi;
+                            }
+                        });
+                    } else {
+                        constexpr int MASK = pushed_pairs<LAT, LN>(C);
+                        const T* f = raw[C + 1];
+                        T A, B[2], m2 = T(0), uxx = T(0), uyy = T(0), uxy = T(0);
+                        if constexpr (PDE == PDE_NSE) {
+                            A = f[0];
+                            B[0] = f[1];
+                            B[1] = f[2];
+                            uxx = f[1] * f[1];
+                            uyy = f[2] * f[2];
+                            uxy = f[1] * f[2];
+                        } else {
+                            const T phi = f[0];
+                            A = phi;
+                            m2 = (((cf.m2[4] * phi + cf.m2[3]) * phi + cf.m2[2]) * phi + cf.m2[1]) * phi + cf.m2[0];
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+                                B[a] = ((cf.flux[a][3] * phi + cf.flux[a][2]) * phi + cf.flux[a][1]) * phi + cf.flux[a][0];
+                        }
+                        if constexpr (OWN) {
+                            T rest;
+                            if constexpr (PDE == PDE_NSE) rest = cf.rC[1] * uyy + (cf.rC[0] * uxx + cf.rA * A);
+                            else rest = cf.rM2 * m2 + cf.rPhi * A;
+                            accC[C][0] += cf.ap[l] * rest + cf.a0[l] * A;
+                            if constexpr (PDE == PDE_NSE) {
+                                accC[C][1] += cf.ab0[l] * B[0];
+                                accC[C][2] += cf.ab0[l] * B[1];
+                            }
+                        }
+                        T E[4], O[4];
+                        pair_eo<LAT, PDE, MASK>(cf, A, B, m2, uxx, uyy, uxy, E, O);
+                        static_for<0, NP>([&](auto pcc) {
+                            constexpr int P_ = decltype(pcc)::value;
+                            constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                            constexpr int TP = C - EX, TM = C + EX;
+                            constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
+                            if constexpr (HP || HM) {
+                                // rho / phi: a+ E +- a- O; momentum: abar+ O +- abar- E (Eq. (2-4-1))
+                                const T sE = cf.ap[l] * E[P_];
+                                T mO = T(0);
+                                if constexpr (PDE == PDE_NSE) mO = cf.abp[l] * O[P_];
+                                auto push = [&](T (&acc)[LN][NF], int node, T sv, T mv) {
+                                    acc[node][0] += sv;
+                                    if constexpr (PDE == PDE_NSE) {
+                                        if constexpr (EX != 0) acc[node][1] += (T(EX) * cf.fmom[0]) * mv;
+                                        if constexpr (EY != 0) acc[node][2] += (T(EY) * cf.fmom[1]) * mv;
+                                    }
+                                };
+                                if constexpr (HP) {
+                                    const T sv = cf.am[l] * O[P_] + sE;
+                                    T mv = T(0);
+                                    if constexpr (PDE == PDE_NSE) mv = cf.abm[l] * E[P_] + mO;
+                                    if constexpr (EY == 1) push(accP, TP, sv, mv);
+                                    else push(accC, TP, sv, mv);
+                                }
+                                if constexpr (HM) {
+                                    const T sv = sE - cf.am[l] * O[P_];
+                                    T mv = T(0);
+                                    if constexpr (PDE == PDE_NSE) mv = mO - cf.abm[l] * E[P_];
+                                    if constexpr (EY == 1) push(accN, TM, sv, mv);
+                                    else push(accC, TM, sv, mv);
+                                }
+                            }
+                        });
+                    }
+                });
+            }
+            ++consumed;
+            cs = cs + 1 == NSTAGE ? 0 : cs + 1;
+            if (cs == 0) cphase ^= 1u;
+            __syncwarp();  // every lane is done reading stage s
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue_next();
+            }
+            // row y0 - 1 + i - 1 is complete
+            if (i >= 2 && xb < g.nx) {
+                const int yo = y0 + i - 2;
+                const long long nb = (long long)yo * g.nx;
+                const bool interior = xb > 0 && xb + LN - 1 < g.nx - 1 && yo > 0 && yo < g.ny - 1;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    S* fo = out + (size_t)f * g.fs;
+#pragma unroll
+                    for (int k4 = 0; k4 < LN; k4 += 4) {
+                        S sv[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
+                            sv[k] = Tr::pack(accP[k4 + k][f], cf.ref[f], rnd);
+                        }
+                        if (interior) {
+                            stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (xb + k4 + k < g.nx) store_with_ghosts<2>(fo, g, xb + k4 + k, yo, 0, sv[k]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < LN; ++k)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    accP[k][f] = accC[k][f];
+                    accC[k][f] = accN[k][f];
+                    accN[k][f] = T(0);
+                }
         }
     }
     if (failed && lane == 0) {
@@ -328,17 +359,19 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     __syncwarp();
 }
 
-template <int ST, int LEVELS, int NF, int NW, int NSTAGE>
+template <int ST, int LEVELS, int NF, int NW, int NSTAGE, int LN>
 constexpr size_t march2d_smem() {
-    return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * NF * (LEVELS - 1) * MarchCfg<ST>::SLOT;
+    constexpr int ES = (int)sizeof(typename Storage<ST>::S);
+    constexpr int SLOT = (((32 * LN + 2 * (16 / ES)) * ES + 127) / 128) * 128;
+    return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * NF * (LEVELS - 1) * SLOT;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN>
 cudaError_t launch_march2d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
-    constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE>();
-    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE>;
+    constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE, LN>();
+    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -350,7 +383,8 @@ cudaError_t launch_march2d_t(const LaunchArgs& a) {
         if (e != cudaSuccess) return e;
         resident = (per_sm > 0 ? per_sm : 1) * sms;
     }
-    const int strips = (a.g.nx + kWarpCols - 1) / kWarpCols;
+    constexpr int COLS = 32 * LN;
+    const int strips = (a.g.nx + COLS - 1) / COLS;
     int H = a.H;
     if (H <= 0) {
         // rows per item: maximise (useful rows / streamed rows) x (fill of the resident warp slots)
