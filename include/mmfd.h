@@ -166,6 +166,24 @@ int mmfd_reduce(mmfd_solver* s, int what, double* out);
  * synchronous. */
 int mmfd_error_norms(mmfd_solver* s, int field, const void* ref, int where, int dtype, double* out);
 
+/* mmfd_reduce_static: the deterministic FP64 reduction of mmfd_reduce (what = MMFD_RED_SUM,
+ * MMFD_RED_MAXABS or MMFD_RED_NONFINITE) over one dense device array, for callers that cannot
+ * allocate device memory at the point of use (cudaFree synchronises the whole device and both
+ * cudaMalloc and cudaFree can block in the driver, which an asynchronous pipeline stage, an
+ * allocator's own bookkeeping path or a component held to a fixed memory budget cannot afford).
+ * No counterpart in the paper.  It allocates nothing: its per-block partials live in a fixed
+ * 8 KB file-scope device array (1024 doubles) that every GPU loading the library holds until
+ * the process exits.
+ *   field  device pointer to count values of type dtype (MMFD_DT_F64 / MMFD_DT_F32), dense;
+ *   count  1 .. 2^27 elements (larger counts return MMFD_ERR_ARG: the scratch has one slot
+ *          per 2^17 elements);
+ *   out    device pointer to one double, written asynchronously on `stream`.
+ * The first call on a device looks up the scratch array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the array and
+ * each overwrites the slots it uses, so nothing needs clearing; calls that overlap on the GPU
+ * (other streams or threads) race on it and must be serialised by the caller. */
+int mmfd_reduce_static(const void* field, int dtype, long long count, int what, double* out, void* stream);
+
 int mmfd_get_info(const mmfd_solver* s, mmfd_info_t* out);
 int mmfd_set_stream(mmfd_solver* s, void* stream);
 int mmfd_destroy(mmfd_solver* s);

@@ -105,6 +105,7 @@ SIGNATURES = {
     "mmfd_fields": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
     "mmfd_reduce": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_double)]),
     "mmfd_error_norms": (C.c_int, [_VP, C.c_int, _VP, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "mmfd_reduce_static": (C.c_int, [_VP, C.c_int, C.c_longlong, C.c_int, _VP, _VP]),
     "mmfd_get_info": (C.c_int, [_VP, C.POINTER(mmfd_info_t)]),
     "mmfd_set_stream": (C.c_int, [_VP, _VP]),
     "mmfd_destroy": (C.c_int, [_VP]),
@@ -220,6 +221,11 @@ def mmfd_error_norms(h: int, field: int, ref_ptr: int, where: int, dtype: int) -
     out = (C.c_double * 3)()
     check(lib.mmfd_error_norms(h, field, ref_ptr, where, dtype, out), "mmfd_error_norms")
     return list(out)
+
+
+def mmfd_reduce_static(field_ptr: int, dtype: int, count: int, what: int, out_ptr: int,
+                       stream: Optional[int]) -> None:
+    check(lib.mmfd_reduce_static(field_ptr, dtype, int(count), what, out_ptr, stream), "mmfd_reduce_static")
 
 
 def mmfd_get_info(h: int) -> mmfd_info_t:
