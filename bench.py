@@ -230,6 +230,28 @@ def serving_bench(count, seed, mmfd, stream, budget_gb=40.0, slots=64, steps_per
         return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                 "mlups": total_lu / makespan / 1e6, "makespan_s": makespan}
 
+    def burst(storage_mode):
+        # saturated: every request is queued at t = 0; aggregate MLUPS = total updates / makespan
+        srv = mmfd.Server(int(budget_gb * (1 << 30)), max_slots=slots, steps_per_tick=steps_per_tick,
+                          use_graphs=True, stream=stream)
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            d = dict(r.desc)
+            if storage_mode == "fp32":
+                d["storage"] = "fp32"
+            tickets.append(srv.submit(mmfd.make_desc(**d), r.fields, r.steps))
+        pending = set(tickets)
+        while pending:
+            for t in list(pending):
+                rc, _ = srv.poll(t)
+                if rc == mmfd.MMFD_OK:
+                    srv.release(t)
+                    pending.discard(t)
+        mk = time.perf_counter() - t0
+        srv.close()
+        return total_lu / mk / 1e6
+
     lat32, mk32, out32, st32 = served("fp32")
     latmix, mkmix, outmix, stmix = served("mixed")
     err32 = max(max(float(np.abs(a - b).max() / max(1e-30, np.abs(b).max())) for a, b in zip(o, p))
@@ -243,6 +265,10 @@ def serving_bench(count, seed, mmfd, stream, budget_gb=40.0, slots=64, steps_per
            "served_mixed_fp32_bf16": {**summary(latmix, mkmix), "max_rel_err_vs_plain_fp32": errmix},
            "budget_gb": budget_gb, "max_slots": slots, "steps_per_tick": steps_per_tick}
     res["served_fp32_vs_plain_mlups"] = res["served_fp32"]["mlups"] / res["plain_fp32"]["mlups"]
+    # saturated throughput (capacity): plain = sum of service times; served = burst makespan
+    res["capacity_mlups"] = {"plain_fp32": total_lu / sum(service) / 1e6, "served_fp32": burst("fp32"),
+                             "served_mixed_fp32_bf16": burst("mixed")}
+    res["capacity_served_fp32_vs_plain"] = res["capacity_mlups"]["served_fp32"] / res["capacity_mlups"]["plain_fp32"]
     return res
 
 
@@ -285,8 +311,12 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2505_17057_gb300 import configs, mmfd
 
-    n = int(args.workload.split("_")[1])
-    desc_kw, fields, _ = configs.tgv2d_4096(n=n, storage=args.storage)
+    kind, n = args.workload.split("_")
+    n = int(n)
+    maker = {"tgv2d": configs.tgv2d_4096, "cde3d": configs.cde3d_512, "nse3d": configs.nse3d_512,
+             "ncde2d": configs.ncde2d_1024, "lcde2d": configs.lcde2d_8192}[kind]
+    desc_kw, fields, _ = maker(n=n, storage=args.storage)
+    dim = 3 if kind.endswith("3d") else 2
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         d = mmfd.make_desc(**desc_kw, temporal_depth=args.depth)
@@ -294,7 +324,7 @@ def run_ours(args):
         s.set_fields(fields)
         info = s.get_info()
         depth = max(1, info.temporal_depth)
-        nodes = n * n
+        nodes = n ** dim
         bytes_per_lu = info.bytes_per_lu
 
         def barrier():
@@ -336,7 +366,7 @@ def run_ours(args):
         avg_launch_s = statistics.mean(launch_ms) / 1e3
         alg_bytes = bytes_per_lu * nodes * depth
         achieved = alg_bytes / avg_launch_s / 1e9
-        kernel_name = "k_march2d" if info.temporal_depth <= 1 else "k_tblock2d"
+        kernel_name = info.kernel.decode()
         traffic = traffic_from_profile(kernel_name, args.workload)
 
         # end to end through the public API: every step uploads the level from pinned host memory,
@@ -376,10 +406,11 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16-offset storage, f32 arithmetic",
                                        "fp64": "f64"}[args.storage],
         "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [n, n], "lattice": "D2Q9", "pde": "NSE (He-Luo)",
-                   "levels": 2, "storage": args.storage, "temporal_depth": depth,
+        "config": {"workload": args.workload, "grid": [n] * dim, "lattice": desc_kw["lattice"],
+                   "pde": {"NSE": "NSE (He-Luo)"}.get(desc_kw["pde"], desc_kw["pde"]),
+                   "levels": desc_kw["levels"], "storage": args.storage, "temporal_depth": depth,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (3 x 67 MB per level), no flush"},
+                   "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kernel_name, "peak_kind": peak_kind,
@@ -392,7 +423,7 @@ def run_ours(args):
     if args.serve > 0:
         with torch.cuda.stream(stream):
             line["serving"] = serving_bench(args.serve, 5, mmfd, stream)
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and args.workload.startswith("tgv2d"):
         timer = OracleTimer(args.workload)
         v, sample = timer.measure(10.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample}

@@ -133,8 +133,10 @@ typedef struct mmfd_solver mmfd_solver;
 int mmfd_desc_init(mmfd_desc* d);
 
 /* Validate the descriptor, resolve the scheme coefficients and EDF constants, run the
- * create-time stability check (LCDE: exact symbol; NCDE: linearised at phi = 0; NSE:
- * linearised at rest), and allocate the level buffers.  *out owns all device memory. */
+ * create-time stability check, and allocate the level buffers.  *out owns all device memory.
+ * The stability check covers the LCDE only (the exact amplification symbol on the grid's wave
+ * numbers, Sec. III); NCDE and NSE problems are nonlinear and are not checked here -- watch
+ * them with mmfd_reduce(..., MMFD_RED_NONFINITE, ...). */
 int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
 
 /* Copy one level into the solver.  level 0 = t_n, level 1 = t_{n-1} (three-level only).

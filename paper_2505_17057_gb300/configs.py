@@ -9,6 +9,9 @@ Workload recipe (seeded, synthetic; the paper uses analytic test problems, no da
                   D(phi) = 0.01 (1 + phi^2), D2Q9 three-level (a_{-1}, a_0, a_1) = (7/8, 0, 1/8),
                   (ahat) = (1/8, 0, -1/8); phi0 = 32 seeded Fourier modes, amplitudes U(0.1, 0.5);
                   dt = 0.4 dx^2 / (2 D(max |phi0|)); 10k steps; FP32.
+  lcde2d_8192     8192x8192 periodic linear CDE on D2Q9 (the scalar bandwidth probe), u and K as in
+                  cde2d_64, two-level, targets (a_0, A10, A11, A21, A22) = (0, -1, -1, 0, 0.5),
+                  phi0 = 1 + 32 seeded Fourier modes (amplitudes U(0.1, 0.5)); FP32.
   tgv2d_4096      4096x4096 periodic He-Luo NSE, D2Q9 two-level, a_0 = abar_0 = 0 (LBGK tau = 1,
                   nu = 1/6), Taylor-Green vortex with u0 = Re nu / N, Re = 100 or 1000; FP32 or BF16.
   cde3d_512       512^3 linear CDE on D3Q7, u = (0.05, 0.03, 0.02), K = diag(0.02, 0.015, 0.01),
@@ -24,7 +27,8 @@ import numpy as np
 
 from . import inputs
 
-CONFIG_INDEX = {"cde2d_64": 0, "ncde2d_1024": 1, "tgv2d_4096": 2, "cde3d_512": 3, "nse3d_512": 3, "serve": 4}
+CONFIG_INDEX = {"cde2d_64": 0, "ncde2d_1024": 1, "lcde2d_8192": 1, "tgv2d_4096": 2, "cde3d_512": 3, "nse3d_512": 3,
+                "serve": 4}
 
 NU_LBGK = 1.0 / 6.0          # -(Abar_22 / Abar_10) dt c_s^2 with a_0 = 0, c_s^2 = 1/3
 THREE_LEVEL_A = (7 / 8, 0.0, 1 / 8)
@@ -51,6 +55,16 @@ def ncde2d_1024(n: int = 1024, storage: str = "fp32"):
                 flux=[[0, 0, 0.5, 0], [0, 0, 0.5, 0]], diff=[0.01, 0, 0.01, 0],
                 a=THREE_LEVEL_A, ahat=THREE_LEVEL_AHAT, storage=storage)
     return desc, [phi0], 10000
+
+
+def lcde2d_8192(n: int = 8192, storage: str = "fp32"):
+    rng = inputs.rng_for(CONFIG_INDEX["lcde2d_8192"])
+    modes = inputs.draw_fourier_modes_2d(rng, 32, 8, 0.1, 0.5)
+    phi0 = 1.0 + inputs.fourier_field_2d(modes, n, n)
+    desc = dict(pde="LCDE", lattice="D2Q9", levels=2, n=[n, n], dt=1.0, dx=[1.0, 1.0],
+                K=[[0.02, 0.005], [0.005, 0.01]], u=[0.1, 0.05], targets=[0, -1, -1, 0, 0.5],
+                storage=storage, ref=[1.0])
+    return desc, [phi0], 1000
 
 
 def tgv2d_4096(n: int = 4096, re: float = 100.0, storage: str = "fp32"):

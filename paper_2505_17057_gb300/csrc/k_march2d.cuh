@@ -58,15 +58,6 @@ __device__ __forceinline__ void stg4(void* p, const typename Storage<ST>::S s[4]
 // own sequence of items (item = global warp id, + total warps, ...) as one stream of input
 // rows; lane 0 keeps NSTAGE rows of that stream in flight through the warp's private ring, so
 // the prefetch runs across item boundaries and warps never wait for one another.
-struct RowCursor {
-    int item;  // current item
-    int row;   // input row index within the item (0 .. nrows - 1)
-};
-
-__device__ __forceinline__ int march_item_rows(int item, int strips, int H, int ny) {
-    const int seg = item / strips;
-    return min(H, ny - seg * H) + 2;
-}
 
 // Even / odd parts E_p, O_p of the pairs a node must push (bit p of MASK set), from the node's
 // basis.  On D2Q9 the two diagonal pairs (1,1) and (-1,1) share omega_p and the diagonal
@@ -148,22 +139,31 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
 
     auto slot = [&](int s, int q) -> unsigned char* { return ring + (size_t)(s * NIN + q) * SLOT; };
 
-    // producer (lane 0): row stream cursor, ring position of the next issue
-    RowCursor pc{wid, 0};
+    // producer (lane 0): row stream cursor with its item's box origin, ring position of the next
+    // issue; the divisions happen once per item, not once per row
+    int p_item = wid, p_row = 0, p_rows = 0, p_xcol = 0, p_prow0 = 0;
+    auto p_load_item = [&]() {
+        if (p_item < nitems) {
+            const int seg = p_item / strips;
+            p_xcol = (p_item - seg * strips) * COLS;     // padded column of the box
+            p_prow0 = seg * H;                            // padded row of input row y0 - 1
+            p_rows = min(H, g.ny - seg * H) + 2;
+        }
+    };
+    p_load_item();
     int ps = 0;                 // stage of the next issue
     long long issued = 0;
     auto issue_next = [&]() {
-        if (pc.item >= nitems) return;
+        if (p_item >= nitems) return;
         mbar_arrive_expect_tx(&full[ps], kTx);
-        const int xcol = (pc.item % strips) * COLS;   // padded column of the box
-        const int prow = (pc.item / strips) * H + pc.row;  // padded row of input row y0 - 1 + row
 #pragma unroll
-        for (int q = 0; q < NIN; ++q) tma_load_2d(slot(ps, q), &maps.m[q], &full[ps], xcol, prow);
+        for (int q = 0; q < NIN; ++q) tma_load_2d(slot(ps, q), &maps.m[q], &full[ps], p_xcol, p_prow0 + p_row);
         ++issued;
         ps = ps + 1 == NSTAGE ? 0 : ps + 1;
-        if (++pc.row == march_item_rows(pc.item, strips, H, g.ny)) {
-            pc.item += wstride;
-            pc.row = 0;
+        if (++p_row == p_rows) {
+            p_item += wstride;
+            p_row = 0;
+            p_load_item();
         }
     };
 
@@ -177,176 +177,186 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     }
     __syncwarp();
 
-    T accP[LN][NF], accC[LN][NF], accN[LN][NF];
+    T acc0[LN][NF], acc1[LN][NF], acc2[LN][NF];
     S* out = static_cast<S*>(outv);
     int cs = 0;              // stage of the next row to consume
     uint32_t cphase = 0;     // its mbarrier phase parity
     long long consumed = 0;
     bool failed = false;
+
+    // One input row: push it into (accP = row r-1, accC = row r, accN = row r+1); row r-1 is then
+    // complete and is stored.
+    auto row_body = [&](int i, int y0, int xb, T (&accP)[LN][NF], T (&accC)[LN][NF], T (&accN)[LN][NF]) -> bool {
+                const int s = cs;
+                const bool ok = mbar_wait_bounded(&full[s], cphase);
+                if (__any_sync(0xffffffffu, !ok)) return false;
+#pragma unroll
+                for (int l = 0; l < LEVELS - 1; ++l) {
+                    // raw fields of the LN + 2 nodes xb-1 .. xb+LN of this input row
+                    T raw[LN + 2][NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const unsigned char* base = slot(s, l * NF + f);
+                        const S* sp = reinterpret_cast<const S*>(base);
+#pragma unroll
+                        for (int k4 = 0; k4 < LN; k4 += 4) {
+                            T v4[4];
+                            lds4<ST>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
+                            raw[1 + k4][f] = v4[0];
+                            raw[2 + k4][f] = v4[1];
+                            raw[3 + k4][f] = v4[2];
+                            raw[4 + k4][f] = v4[3];
+                        }
+                        raw[0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
+                        raw[LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
+                    }
+                    static_for<0, LN + 2>([&](auto cc) {
+                        constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. LN
+                        constexpr bool OWN = C >= 0 && C < LN;
+                        if constexpr (PDE == PDE_LCDE) {
+                            const T phi = raw[C + 1][0];
+                            if constexpr (OWN) accC[C][0] += cf.W0[l] * phi;
+                            static_for<0, NP>([&](auto pcc) {
+                                constexpr int P_ = decltype(pcc)::value;
+                                constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                                constexpr int TP = C - EX, TM = C + EX;
+                                if constexpr (TP >= 0 && TP < LN) {
+                                    if constexpr (EY == 1) accP[TP][0] += cf.Wp[l][P_] * phi;
+                                    else accC[TP][0] += cf.Wp[l][P_] * phi;
+                                }
+                                if constexpr (TM >= 0 && TM < LN) {
+                                    if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P_] * phi;
+                                    else accC[TM][0] += cf.Wm[l][P_] * phi;
+                                }
+                            });
+                        } else {
+                            constexpr int MASK = pushed_pairs<LAT, LN>(C);
+                            const T* f = raw[C + 1];
+                            T A, B[2], m2 = T(0), uxx = T(0), uyy = T(0), uxy = T(0);
+                            if constexpr (PDE == PDE_NSE) {
+                                A = f[0];
+                                B[0] = f[1];
+                                B[1] = f[2];
+                                uxx = f[1] * f[1];
+                                uyy = f[2] * f[2];
+                                uxy = f[1] * f[2];
+                            } else {
+                                const T phi = f[0];
+                                A = phi;
+                                m2 = (((cf.m2[4] * phi + cf.m2[3]) * phi + cf.m2[2]) * phi + cf.m2[1]) * phi + cf.m2[0];
+#pragma unroll
+                                for (int a = 0; a < 2; ++a)
+                                    B[a] = ((cf.flux[a][3] * phi + cf.flux[a][2]) * phi + cf.flux[a][1]) * phi + cf.flux[a][0];
+                            }
+                            if constexpr (OWN) {
+                                T rest;
+                                if constexpr (PDE == PDE_NSE) rest = cf.rC[1] * uyy + (cf.rC[0] * uxx + cf.rA * A);
+                                else rest = cf.rM2 * m2 + cf.rPhi * A;
+                                accC[C][0] += cf.ap[l] * rest + cf.a0[l] * A;
+                                if constexpr (PDE == PDE_NSE) {
+                                    accC[C][1] += cf.ab0[l] * B[0];
+                                    accC[C][2] += cf.ab0[l] * B[1];
+                                }
+                            }
+                            T E[4], O[4];
+                            pair_eo<LAT, PDE, MASK>(cf, A, B, m2, uxx, uyy, uxy, E, O);
+                            static_for<0, NP>([&](auto pcc) {
+                                constexpr int P_ = decltype(pcc)::value;
+                                constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                                constexpr int TP = C - EX, TM = C + EX;
+                                constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
+                                if constexpr (HP || HM) {
+                                    // rho / phi: a+ E +- a- O; momentum: abar+ O +- abar- E (Eq. (2-4-1))
+                                    const T sE = cf.ap[l] * E[P_];
+                                    [[maybe_unused]] T mO = T(0);
+                                    if constexpr (PDE == PDE_NSE) mO = cf.abp[l] * O[P_];
+                                    auto push = [&](T (&acc)[LN][NF], int node, T sv, T mv) {
+                                        acc[node][0] += sv;
+                                        if constexpr (PDE == PDE_NSE) {
+                                            if constexpr (EX != 0) acc[node][1] += (T(EX) * cf.fmom[0]) * mv;
+                                            if constexpr (EY != 0) acc[node][2] += (T(EY) * cf.fmom[1]) * mv;
+                                        }
+                                    };
+                                    if constexpr (HP) {
+                                        const T sv = cf.am[l] * O[P_] + sE;
+                                        T mv = T(0);
+                                        if constexpr (PDE == PDE_NSE) mv = cf.abm[l] * E[P_] + mO;
+                                        if constexpr (EY == 1) push(accP, TP, sv, mv);
+                                        else push(accC, TP, sv, mv);
+                                    }
+                                    if constexpr (HM) {
+                                        const T sv = sE - cf.am[l] * O[P_];
+                                        T mv = T(0);
+                                        if constexpr (PDE == PDE_NSE) mv = mO - cf.abm[l] * E[P_];
+                                        if constexpr (EY == 1) push(accN, TM, sv, mv);
+                                        else push(accC, TM, sv, mv);
+                                    }
+                                }
+                            });
+                        }
+                    });
+                }
+                ++consumed;
+                cs = cs + 1 == NSTAGE ? 0 : cs + 1;
+                if (cs == 0) cphase ^= 1u;
+                __syncwarp();  // every lane is done reading stage s
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    issue_next();
+                }
+                // row y0 - 1 + i - 1 is complete
+                if (i >= 2 && xb < g.nx) {
+                    const int yo = y0 + i - 2;
+                    const long long nb = (long long)yo * g.nx;
+                    const bool interior = xb > 0 && xb + LN - 1 < g.nx - 1 && yo > 0 && yo < g.ny - 1;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        S* fo = out + (size_t)f * g.fs;
+#pragma unroll
+                        for (int k4 = 0; k4 < LN; k4 += 4) {
+                            S sv[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
+                                sv[k] = Tr::pack(accP[k4 + k][f], cf.ref[f], rnd);
+                            }
+                            if (interior) {
+                                stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    if (xb + k4 + k < g.nx) store_with_ghosts<2>(fo, g, xb + k4 + k, yo, 0, sv[k]);
+                            }
+                        }
+                    }
+                }
+        return true;
+    };
+
     for (int item = wid; item < nitems && !failed; item += wstride) {
-        const int x0 = (item % strips) * COLS;
-        const int y0 = (item / strips) * H;
-        const int nrows = march_item_rows(item, strips, H, g.ny);
+        const int seg = item / strips;
+        const int x0 = (item - seg * strips) * COLS;
+        const int y0 = seg * H;
+        const int nrows = min(H, g.ny - y0) + 2;
         const int xb = x0 + lane * LN;
 #pragma unroll
         for (int k = 0; k < LN; ++k)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) accP[k][f] = accC[k][f] = accN[k][f] = T(0);
-
+            for (int f = 0; f < NF; ++f) acc0[k][f] = acc1[k][f] = acc2[k][f] = T(0);
+        // One copy of the row body: unrolling it three times to rotate the accumulator sets by
+        // renaming instead of moves overflowed the instruction cache and ran slower.
         for (int i = 0; i < nrows; ++i) {
-            const int s = cs;
-            const bool ok = mbar_wait_bounded(&full[s], cphase);
-            if (__any_sync(0xffffffffu, !ok)) {
+            if (!row_body(i, y0, xb, acc0, acc1, acc2)) {
                 failed = true;
                 break;
-            }
-#pragma unroll
-            for (int l = 0; l < LEVELS - 1; ++l) {
-                // raw fields of the LN + 2 nodes xb-1 .. xb+LN of this input row
-                T raw[LN + 2][NF];
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const unsigned char* base = slot(s, l * NF + f);
-                    const S* sp = reinterpret_cast<const S*>(base);
-#pragma unroll
-                    for (int k4 = 0; k4 < LN; k4 += 4) {
-                        T v4[4];
-                        lds4<ST>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
-                        raw[1 + k4][f] = v4[0];
-                        raw[2 + k4][f] = v4[1];
-                        raw[3 + k4][f] = v4[2];
-                        raw[4 + k4][f] = v4[3];
-                    }
-                    raw[0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
-                    raw[LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
-                }
-                static_for<0, LN + 2>([&](auto cc) {
-                    constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. LN
-                    constexpr bool OWN = C >= 0 && C < LN;
-                    if constexpr (PDE == PDE_LCDE) {
-                        const T phi = raw[C + 1][0];
-                        if constexpr (OWN) accC[C][0] += cf.W0[l] * phi;
-                        static_for<0, NP>([&](auto pcc) {
-                            constexpr int P_ = decltype(pcc)::value;
-                            constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                            constexpr int TP = C - EX, TM = C + EX;
-                            if constexpr (TP >= 0 && TP < LN) {
-                                if constexpr (EY == 1) accP[TP][0] += cf.Wp[l][P_] * phi;
-                                else accC[TP][0] += cf.Wp[l][P_] * phi;
-                            }
-                            if constexpr (TM >= 0 && TM < LN) {
-                                if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P_] * phi;
-                                else accC[TM][0] += cf.Wm[l][P_] * phi;
-                            }
-                        });
-                    } else {
-                        constexpr int MASK = pushed_pairs<LAT, LN>(C);
-                        const T* f = raw[C + 1];
-                        T A, B[2], m2 = T(0), uxx = T(0), uyy = T(0), uxy = T(0);
-                        if constexpr (PDE == PDE_NSE) {
-                            A = f[0];
-                            B[0] = f[1];
-                            B[1] = f[2];
-                            uxx = f[1] * f[1];
-                            uyy = f[2] * f[2];
-                            uxy = f[1] * f[2];
-                        } else {
-                            const T phi = f[0];
-                            A = phi;
-                            m2 = (((cf.m2[4] * phi + cf.m2[3]) * phi + cf.m2[2]) * phi + cf.m2[1]) * phi + cf.m2[0];
-#pragma unroll
-                            for (int a = 0; a < 2; ++a)
-                                B[a] = ((cf.flux[a][3] * phi + cf.flux[a][2]) * phi + cf.flux[a][1]) * phi + cf.flux[a][0];
-                        }
-                        if constexpr (OWN) {
-                            T rest;
-                            if constexpr (PDE == PDE_NSE) rest = cf.rC[1] * uyy + (cf.rC[0] * uxx + cf.rA * A);
-                            else rest = cf.rM2 * m2 + cf.rPhi * A;
-                            accC[C][0] += cf.ap[l] * rest + cf.a0[l] * A;
-                            if constexpr (PDE == PDE_NSE) {
-                                accC[C][1] += cf.ab0[l] * B[0];
-                                accC[C][2] += cf.ab0[l] * B[1];
-                            }
-                        }
-                        T E[4], O[4];
-                        pair_eo<LAT, PDE, MASK>(cf, A, B, m2, uxx, uyy, uxy, E, O);
-                        static_for<0, NP>([&](auto pcc) {
-                            constexpr int P_ = decltype(pcc)::value;
-                            constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                            constexpr int TP = C - EX, TM = C + EX;
-                            constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
-                            if constexpr (HP || HM) {
-                                // rho / phi: a+ E +- a- O; momentum: abar+ O +- abar- E (Eq. (2-4-1))
-                                const T sE = cf.ap[l] * E[P_];
-                                T mO = T(0);
-                                if constexpr (PDE == PDE_NSE) mO = cf.abp[l] * O[P_];
-                                auto push = [&](T (&acc)[LN][NF], int node, T sv, T mv) {
-                                    acc[node][0] += sv;
-                                    if constexpr (PDE == PDE_NSE) {
-                                        if constexpr (EX != 0) acc[node][1] += (T(EX) * cf.fmom[0]) * mv;
-                                        if constexpr (EY != 0) acc[node][2] += (T(EY) * cf.fmom[1]) * mv;
-                                    }
-                                };
-                                if constexpr (HP) {
-                                    const T sv = cf.am[l] * O[P_] + sE;
-                                    T mv = T(0);
-                                    if constexpr (PDE == PDE_NSE) mv = cf.abm[l] * E[P_] + mO;
-                                    if constexpr (EY == 1) push(accP, TP, sv, mv);
-                                    else push(accC, TP, sv, mv);
-                                }
-                                if constexpr (HM) {
-                                    const T sv = sE - cf.am[l] * O[P_];
-                                    T mv = T(0);
-                                    if constexpr (PDE == PDE_NSE) mv = mO - cf.abm[l] * E[P_];
-                                    if constexpr (EY == 1) push(accN, TM, sv, mv);
-                                    else push(accC, TM, sv, mv);
-                                }
-                            }
-                        });
-                    }
-                });
-            }
-            ++consumed;
-            cs = cs + 1 == NSTAGE ? 0 : cs + 1;
-            if (cs == 0) cphase ^= 1u;
-            __syncwarp();  // every lane is done reading stage s
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue_next();
-            }
-            // row y0 - 1 + i - 1 is complete
-            if (i >= 2 && xb < g.nx) {
-                const int yo = y0 + i - 2;
-                const long long nb = (long long)yo * g.nx;
-                const bool interior = xb > 0 && xb + LN - 1 < g.nx - 1 && yo > 0 && yo < g.ny - 1;
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    S* fo = out + (size_t)f * g.fs;
-#pragma unroll
-                    for (int k4 = 0; k4 < LN; k4 += 4) {
-                        S sv[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
-                            sv[k] = Tr::pack(accP[k4 + k][f], cf.ref[f], rnd);
-                        }
-                        if (interior) {
-                            stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                if (xb + k4 + k < g.nx) store_with_ghosts<2>(fo, g, xb + k4 + k, yo, 0, sv[k]);
-                        }
-                    }
-                }
             }
 #pragma unroll
             for (int k = 0; k < LN; ++k)
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    accP[k][f] = accC[k][f];
-                    accC[k][f] = accN[k][f];
-                    accN[k][f] = T(0);
+                    acc0[k][f] = acc1[k][f];
+                    acc1[k][f] = acc2[k][f];
+                    acc2[k][f] = T(0);
                 }
         }
     }

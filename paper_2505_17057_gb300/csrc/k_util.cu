@@ -18,37 +18,51 @@ __device__ __forceinline__ double load_st(const void* base, long long i, double 
     return (double)Tr::load(static_cast<const typename Tr::S*>(base) + i, (typename Tr::T)ref);
 }
 
+// Layout kernels walk rows (blockIdx.y over y + z ny, grid-stride) and columns (threads), so no
+// per-element division is needed; only edge nodes take the ghost-image path.
 template <int ST>
 __global__ void k_pack(Geom g, const void* __restrict__ src, int src_dtype, void* __restrict__ dst, double ref) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
-    const long long N = (long long)g.nx * g.ny * g.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx);
-        const int y = (int)((i / g.nx) % g.ny);
-        const int z = (int)(i / ((long long)g.nx * g.ny));
-        const double v = src_dtype == 0 ? static_cast<const double*>(src)[i] : (double)static_cast<const float*>(src)[i];
-        const S s = Tr::pack((T)v, (T)ref, 0u);
-        if (g.dim == 3)
-            store_with_ghosts<3>(static_cast<S*>(dst), g, x, y, z, s);
-        else
-            store_with_ghosts<2>(static_cast<S*>(dst), g, x, y, z, s);
+    S* d = static_cast<S*>(dst);
+    const long long rows = (long long)g.ny * g.nz;
+    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const long long base = r * g.nx;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
+            const long long i = base + x;
+            const double v = src_dtype == 0 ? static_cast<const double*>(src)[i] : (double)static_cast<const float*>(src)[i];
+            const S sv = Tr::pack((T)v, (T)ref, 0u);
+            const bool edge = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 ||
+                              (g.dim == 3 && (z == 0 || z == g.nz - 1));
+            if (!edge) {
+                d[g.at(x, y, z)] = sv;
+            } else if (g.dim == 3) {
+                store_with_ghosts<3>(d, g, x, y, z, sv);
+            } else {
+                store_with_ghosts<2>(d, g, x, y, z, sv);
+            }
+        }
     }
 }
 
 template <int ST>
 __global__ void k_unpack(Geom g, const void* __restrict__ src, double ref, void* __restrict__ dst, int dst_dtype) {
-    const long long N = (long long)g.nx * g.ny * g.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx);
-        const int y = (int)((i / g.nx) % g.ny);
-        const int z = (int)(i / ((long long)g.nx * g.ny));
-        const double v = load_st<ST>(src, g.at(x, y, z), ref);
-        if (dst_dtype == 0)
-            static_cast<double*>(dst)[i] = v;
-        else
-            static_cast<float*>(dst)[i] = (float)v;
+    const long long rows = (long long)g.ny * g.nz;
+    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const long long base = r * g.nx;
+        const long long sbase = g.at(0, y, z);
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
+            const double v = load_st<ST>(src, sbase + x, ref);
+            if (dst_dtype == 0)
+                static_cast<double*>(dst)[base + x] = v;
+            else
+                static_cast<float*>(dst)[base + x] = (float)v;
+        }
     }
 }
 
@@ -62,38 +76,44 @@ __device__ __forceinline__ Acc4 combine(int op, Acc4 x, Acc4 y) {
     return {x.a + y.a, 0, 0, 0};
 }
 
-// Fixed-order block reduction: each block covers a fixed strided subset of nodes and
-// reduces through shared memory in a fixed tree, so the result is bitwise reproducible.
+// Fixed-order block reduction: block b covers rows b, b + nblocks, ... (row = y + z ny) and, in
+// each row, columns threadIdx.x, + blockDim.x, ...; it reduces through shared memory in a fixed
+// tree, so the result is bitwise reproducible.
 template <int ST>
 __global__ void __launch_bounds__(kRedThreads) k_reduce_parts(Geom g, const void* __restrict__ lev, double fref,
                                                               int op, const void* __restrict__ ref, int ref_dtype,
                                                               Acc4* __restrict__ parts) {
     __shared__ Acc4 sh[kRedThreads];
-    const long long N = (long long)g.nx * g.ny * g.nz;
+    const long long rows = (long long)g.ny * g.nz;
     Acc4 acc = {0, 0, 0, 0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx);
-        const int y = (int)((i / g.nx) % g.ny);
-        const int z = (int)(i / ((long long)g.nx * g.ny));
-        const double v = load_st<ST>(lev, g.at(x, y, z), fref);
-        Acc4 e;
-        if (op == 0) {
-            e = {v, 0, 0, 0};
-        } else if (op == 1) {
-            e = {fabs(v), 0, 0, 0};
-        } else if (op == 2) {
-            e = {isfinite(v) ? 0.0 : 1.0, 0, 0, 0};
-        } else {
-            const double r = ref_dtype == 0 ? static_cast<const double*>(ref)[i] : (double)static_cast<const float*>(ref)[i];
-            e = {fabs(v - r), fabs(r), fabs(v - r), fabs(r)};
-            if (!isfinite(v)) e = {INFINITY, fabs(r), INFINITY, fabs(r)};
+    const int cop = op == 2 ? 0 : op;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const long long sbase = g.at(0, y, z);
+        const long long dbase = r * g.nx;
+        for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+            const double v = load_st<ST>(lev, sbase + x, fref);
+            Acc4 e;
+            if (op == 0) {
+                e = {v, 0, 0, 0};
+            } else if (op == 1) {
+                e = {fabs(v), 0, 0, 0};
+            } else if (op == 2) {
+                e = {isfinite(v) ? 0.0 : 1.0, 0, 0, 0};
+            } else {
+                const long long i = dbase + x;
+                const double rv = ref_dtype == 0 ? static_cast<const double*>(ref)[i] : (double)static_cast<const float*>(ref)[i];
+                e = {fabs(v - rv), fabs(rv), fabs(v - rv), fabs(rv)};
+                if (!isfinite(v)) e = {INFINITY, fabs(rv), INFINITY, fabs(rv)};
+            }
+            acc = combine(cop, acc, e);
         }
-        acc = combine(op == 2 ? 0 : op, acc, e);
     }
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] = combine(op == 2 ? 0 : op, sh[threadIdx.x], sh[threadIdx.x + s]);
+        if (threadIdx.x < s) sh[threadIdx.x] = combine(cop, sh[threadIdx.x], sh[threadIdx.x + s]);
         __syncthreads();
     }
     if (threadIdx.x == 0) parts[blockIdx.x] = sh[0];
@@ -119,19 +139,18 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const Acc4* __rest
     }
 }
 
-int grid_for(long long n) {
-    long long b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    return (int)b;
+dim3 grid_rows(const Geom& g) {
+    const long long rows = (long long)g.ny * g.nz;
+    const int bx = (g.nx + 255) / 256 < 64 ? (g.nx + 255) / 256 : 64;
+    const long long by = rows < 65535 ? rows : 65535;
+    return dim3(bx, (unsigned)by, 1);
 }
 
 }  // namespace
 
 cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, void* dst_level, int field,
                         double ref, cudaStream_t s) {
-    const long long N = (long long)g.nx * g.ny * g.nz;
-    const int blocks = grid_for(N);
+    const dim3 blocks = grid_rows(g);
     char* dst = static_cast<char*>(dst_level) + (size_t)field * g.fs * g.es;
     if (st == ST_F64) k_pack<ST_F64><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
     else if (st == ST_F32) k_pack<ST_F32><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
@@ -141,8 +160,7 @@ cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, v
 
 cudaError_t launch_unpack(const Geom& g, int st, const void* src_level, int field, double ref, void* dst,
                           int dst_dtype, cudaStream_t s) {
-    const long long N = (long long)g.nx * g.ny * g.nz;
-    const int blocks = grid_for(N);
+    const dim3 blocks = grid_rows(g);
     const char* src = static_cast<const char*>(src_level) + (size_t)field * g.fs * g.es;
     if (st == ST_F64) k_unpack<ST_F64><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype);
     else if (st == ST_F32) k_unpack<ST_F32><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype);

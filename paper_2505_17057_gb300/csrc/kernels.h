@@ -37,6 +37,8 @@ LaunchFn find_direct(int lat, int pde, int levels, int st);
 LaunchFn find_march2d(int lat, int pde, int levels, int st);
 // 3D plane-marching kernels (z march, x-y tile staged in shared memory by TMA).
 LaunchFn find_march3d(int lat, int pde, int levels, int st);
+// Rows of the x-y tile a 3D march CTA stages per plane (the TMA box is 128+halo x rows+2 x 1).
+int march3d_tile_rows(int pde);
 
 // Encode a 2D / 3D tiled TMA descriptor over one field of a ghosted level buffer
 // (box = boxw x 1 [x 1] elements).  Returns 0 on success.

@@ -56,7 +56,14 @@ struct Req {
     double t_submit = 0, t_admit = 0, t_finish = 0;
     int status = MMFD_OK;
     int cls = 0;
+    // large 2D requests run their own TMA march launches instead of joining a batched launch
+    LaunchFn solo = nullptr;
+    CUtensorMap tmaps[3][4];
 };
+
+// A request this large (and at least 128 columns wide) is stepped with the single-solve march
+// kernel (2D or 3D); smaller ones are packed into the batched kernel of their class.
+constexpr long long kSoloNodes = 1ll << 16;
 
 struct ClassTables {
     BatchFn fn = nullptr;
@@ -90,6 +97,7 @@ struct Server {
     unsigned long long next_ticket = 1;
     int parity = 0;
     int sms = 152;
+    int* d_flag = nullptr;  // device error flag for the march kernels' bounded waits
     void* stage = nullptr;
     size_t stage_bytes = 0;
     // graph cache: composition key -> executable graph
@@ -159,6 +167,20 @@ int admit(Server* s, Req* q) {
     }
     q->init.clear();
     q->init.shrink_to_fit();
+    q->solo = nullptr;
+    if (q->g.nx >= 128 && (long long)q->g.nx * q->g.ny * q->g.nz >= kSoloNodes) {
+        LaunchFn fn = q->g.dim == 2 ? find_march2d(q->r->lat, q->r->pde, q->r->levels, q->r->st)
+                                    : find_march3d(q->r->lat, q->r->pde, q->r->levels, q->r->st);
+        bool ok = fn != nullptr;
+        const int boxw = 128 + 2 * (16 / q->g.es);
+        const int boxh = q->g.dim == 2 ? 1 : march3d_tile_rows(q->r->pde) + 2;
+        for (int b = 0; ok && b < nl; ++b)
+            for (int f = 0; ok && f < q->g.nf; ++f) {
+                char* base = static_cast<char*>(q->lev[b]) + (size_t)f * q->g.fs * q->g.es;
+                ok = encode_field_map(&q->tmaps[b][f], base, q->r->st, q->g, boxw, boxh, 1) == 0;
+            }
+        if (ok) q->solo = fn;
+    }
     q->cur = 0;
     q->state = RQ_ACTIVE;
     q->t_admit = now_s();
@@ -212,8 +234,14 @@ int launch_tick(Server* s) {
     // table buffers of this parity were last used two ticks ago: make sure that tick finished
     while (s->inflight.size() >= 2) reap(s, true);
     for (auto& kv : s->classes) kv.second.members.clear();
-    for (Req* q : s->active)
-        if (q->state == RQ_ACTIVE && q->launched < q->nsteps) s->classes[q->cls].members.push_back(q);
+    std::vector<Req*> solos;
+    for (Req* q : s->active) {
+        if (q->state != RQ_ACTIVE || q->launched >= q->nsteps) continue;
+        if (q->solo)
+            solos.push_back(q);
+        else
+            s->classes[q->cls].members.push_back(q);
+    }
     std::string key;
     struct Launch {
         BatchFn fn;
@@ -260,15 +288,54 @@ int launch_tick(Server* s) {
         key += std::to_string(kv.first) + ":" + std::to_string(n) + ":" + std::to_string(tile0) + ":" +
                std::to_string(reinterpret_cast<uintptr_t>(c.d[par])) + ";";
     }
-    if (launches.empty()) return MMFD_OK;
+    for (Req* q : solos) {
+        const long long left = q->nsteps - q->launched;
+        const long long adv = left < S ? left : S;
+        lu += adv * (long long)q->g.nx * q->g.ny * q->g.nz;
+        key += "solo:" + std::to_string(q->ticket) + ":" + std::to_string(q->cur) + ":" + std::to_string(adv) + ";";
+    }
+    if (launches.empty() && solos.empty()) return MMFD_OK;
+    auto solo_step = [&](Req* q, int j) -> cudaError_t {
+        const int nl = q->nlev;
+        const int c = (q->cur + j) % nl;
+        const int prev = nl == 3 ? (c + 2) % 3 : c;
+        const int next = nl == 2 ? 1 - c : (c + 1) % 3;
+        TmapSet maps;
+        for (int f = 0; f < q->g.nf; ++f) {
+            maps.m[f] = q->tmaps[c][f];
+            if (nl == 3) maps.m[q->g.nf + f] = q->tmaps[prev][f];
+        }
+        LaunchArgs a;
+        a.g = q->g;
+        a.in0 = q->lev[c];
+        a.in1 = nl == 3 ? q->lev[prev] : nullptr;
+        a.out = q->lev[next];
+        a.coef = q->r->st == ST_F64 ? static_cast<const void*>(&q->r->cd) : static_cast<const void*>(&q->r->cf);
+        a.ex.seed = q->desc.seed;
+        a.ex.step = q->launched + j + 1;
+        a.ex.sr = (q->r->st == ST_BF16 && (q->desc.flags & MMFD_FLAG_STOCHASTIC_ROUND)) ? 1 : 0;
+        a.stream = s->stream;
+        a.variant = 0;
+        a.maps = &maps;
+        a.H = 0;
+        a.err = s->d_flag;
+        return q->solo(a);
+    };
     auto enqueue = [&]() -> cudaError_t {
-        for (int j = 0; j < S; ++j)
+        for (int j = 0; j < S; ++j) {
             for (const Launch& L : launches) {
                 long long grid = L.total < (long long)s->sms * 8 ? L.total : (long long)s->sms * 8;
                 cudaError_t e = L.fn(L.items, L.n, L.total, j, (int)grid, s->stream);
                 if (e != cudaSuccess) return e;
                 s->st.launches++;
             }
+            for (Req* q : solos) {
+                if (j >= q->nsteps - q->launched) continue;
+                cudaError_t e = solo_step(q, j);
+                if (e != cudaSuccess) return e;
+                s->st.launches++;
+            }
+        }
         return cudaSuccess;
     };
     if (s->d.use_graphs) {
@@ -304,14 +371,16 @@ int launch_tick(Server* s) {
         if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     }
     // advance the bookkeeping of every launched request
+    auto advance = [&](Req* q) {
+        const long long left = q->nsteps - q->launched;
+        const long long adv = left < S ? left : S;
+        q->cur = (int)((q->cur + adv) % q->nlev);
+        q->launched += adv;
+        if (q->launched >= q->nsteps) tick.finishing.push_back(q);
+    };
     for (auto& kv : s->classes)
-        for (Req* q : kv.second.members) {
-            const long long left = q->nsteps - q->launched;
-            const long long adv = left < S ? left : S;
-            q->cur = (int)((q->cur + adv) % q->nlev);
-            q->launched += adv;
-            if (q->launched >= q->nsteps) tick.finishing.push_back(q);
-        }
+        for (Req* q : kv.second.members) advance(q);
+    for (Req* q : solos) advance(q);
     cudaError_t e = cudaEventCreateWithFlags(&tick.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     e = cudaEventRecord(tick.done, s->stream);
@@ -410,6 +479,14 @@ int mmfd_server_create(const mmfd_server_desc* desc, mmfd_server** out) {
     }
     unsigned long long keep = ~0ull;
     cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (srv_alloc(s, 256, reinterpret_cast<void**>(&s->d_flag)) != MMFD_OK ||
+        cudaMemsetAsync(s->d_flag, 0, 256, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaMemPoolDestroy(s->pool);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return set_error(MMFD_ERR_OOM, "server flag allocation failed");
+    }
     *out = reinterpret_cast<mmfd_server*>(s);
     return MMFD_OK;
 }
@@ -519,6 +596,13 @@ int mmfd_result_fields(mmfd_server* h, unsigned long long ticket, void* const* o
     Req* q = it->second;
     if (q->state != RQ_DONE) return set_error(MMFD_ERR_STATE, "request not finished");
     if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    {
+        int flag = 0;
+        cudaError_t fe = cudaMemcpyAsync(&flag, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        if (fe == cudaSuccess) fe = cudaStreamSynchronize(s->stream);
+        if (fe != cudaSuccess) return cuda_fail(fe, "reading the server error flag");
+        if (flag != 0) return set_error(MMFD_ERR_TIMEOUT, "a kernel's bounded wait for its TMA copies ran out");
+    }
     const long long N = (long long)q->g.nx * q->g.ny * q->g.nz;
     const size_t esz = dtype == MMFD_DT_F64 ? 8 : 4;
     if (where == MMFD_HOST) {
@@ -585,6 +669,7 @@ int mmfd_server_destroy(mmfd_server* h) {
         }
     for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
     srv_free(s, s->stage);
+    srv_free(s, s->d_flag);
     cudaStreamSynchronize(s->stream);
     cudaMemPoolDestroy(s->pool);
     if (s->own_stream) cudaStreamDestroy(s->stream);

@@ -268,6 +268,28 @@ int solver_pick_kernels(Solver* s) {
             return MMFD_OK;
         }
     }
+    if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct) {
+        s->fn = find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        if (s->fn) {
+            const int es = s->g.es;
+            const int boxw = 128 + 2 * (16 / es);
+            const int rows = march3d_tile_rows(s->r.pde) + 2;
+            for (int b = 0; b < s->nlev && s->fn; ++b)
+                for (int f = 0; f < s->g.nf; ++f) {
+                    char* base = static_cast<char*>(s->lev[b]) + (size_t)f * s->g.fs * es;
+                    if (encode_field_map(&s->tmaps[b][f], base, s->r.st, s->g, boxw, rows, 1) != 0) {
+                        s->fn = nullptr;
+                        break;
+                    }
+                }
+        }
+        if (s->fn) {
+            s->use_tma = true;
+            s->kernel_name = "k_march3d";
+            s->H = 0;
+            return MMFD_OK;
+        }
+    }
     s->fn = find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
     s->kernel_name = "k_direct";
     if (!s->fn) return set_error(MMFD_ERR_UNSUPPORTED, "no kernel for this lattice/PDE/levels/storage");

@@ -89,11 +89,13 @@ def fourier_field_2d(modes: FourierModes2D, nx: int, ny: int) -> np.ndarray:
     """phi0(x, y) = sum_m A_m cos(k_m . (x, y) + theta_m) on the periodic box [0, 2 pi)^2."""
     x = 2.0 * math.pi * np.arange(nx, dtype=np.float64) / nx
     y = 2.0 * math.pi * np.arange(ny, dtype=np.float64) / ny
-    X, Y = np.meshgrid(x, y, indexing="xy")
-    out = np.zeros((ny, nx))
+    # cos(kx x + ky y + t) = cos(ky y) cos(kx x + t) - sin(ky y) sin(kx x + t): the sum over modes
+    # is one (ny x 2M) @ (2M x nx) product instead of M full-grid cosines
+    cols, rows = [], []
     for a, (kx, ky), t in zip(modes.amps, modes.kvec, modes.phases):
-        out += a * np.cos(kx * X + ky * Y + t)
-    return out
+        cols += [np.cos(ky * y), -np.sin(ky * y)]
+        rows += [a * np.cos(kx * x + t), a * np.sin(kx * x + t)]
+    return np.stack(cols, axis=1) @ np.stack(rows, axis=0)
 
 
 def taylor_green_2d(nx: int, ny: int, u0: float, nu: float, t: float,

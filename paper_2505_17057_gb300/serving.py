@@ -57,13 +57,14 @@ def make_request(rng: inputs.SplitMix64, storage_mix: bool = True, steps_scale: 
             dx = 2 * math.pi / n
             phi = 0.5 * base
             dmax = 0.01 * (1 + float(np.abs(phi).max()) ** 2)
-            dt = 0.4 * dx * dx / (2 * dmax)
+            # diffusive limit of config 2, and a convective one (|B'| dt / dx <= 0.2) for coarse grids
+            dt = min(0.4 * dx * dx / (2 * dmax), 0.2 * dx / max(1e-12, float(np.abs(phi).max())))
             desc = dict(pde="NCDE", lattice="D2Q9", levels=3, n=[n, n], dt=dt, dx=[dx, dx],
                         flux=[[0, 0, 0.5, 0], [0, 0, 0.5, 0]], diff=[0.01, 0, 0.01, 0],
                         a=(7 / 8, 0.0, 1 / 8), ahat=(1 / 8, 0.0, -1 / 8), storage=storage)
             fields = [phi]
         else:
-            u0 = 100 * (1 / 6) / n
+            u0 = min(100 * (1 / 6) / n, 0.05)  # Re 100, capped at Ma ~ 0.09 on coarse grids
             rho, u, v = inputs.taylor_green_2d(n, n, u0, 1 / 6, 0.0)
             desc = dict(pde="NSE", lattice="D2Q9", levels=2, n=[n, n], dt=1.0, dx=[1.0, 1.0],
                         a=(1.0, 0.0, 0.0), abar=(1.0, 0.0, 0.0), storage=storage, ref=[1.0, 0.0, 0.0])
@@ -80,7 +81,7 @@ def make_request(rng: inputs.SplitMix64, storage_mix: bool = True, steps_scale: 
             dx = 2 * math.pi / n
             phi = 0.5 * base
             dmax = 0.01 * (1 + float(np.abs(phi).max()) ** 2)
-            dt = 0.3 * dx * dx / (2 * dmax)
+            dt = min(0.3 * dx * dx / (2 * dmax), 0.15 * dx / max(1e-12, float(np.abs(phi).max())))
             desc = dict(pde="NCDE", lattice="D3Q19", levels=3, n=[n, n, n], dt=dt, dx=[dx, dx, dx],
                         flux=[[0, 0, 0.5, 0]] * 3, diff=[0.01, 0, 0.01, 0],
                         a=(7 / 8, 0.0, 1 / 8), ahat=(1 / 8, 0.0, -1 / 8), storage=storage)

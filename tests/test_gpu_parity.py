@@ -42,7 +42,7 @@ def run_gpu(mm, kw, level0, level1=None, steps=1, **extra):
 
 
 SIZES_2D = [[300, 70], [67, 45]]
-SIZES_3D = [[70, 37, 21]]
+SIZES_3D = [[70, 37, 21], [150, 21, 9]]
 
 
 @pytest.mark.parametrize("lat,pde,levels", G.SUPPORTED)
@@ -63,7 +63,7 @@ def test_parity_fp64(mm, lat, pde, levels):
 @pytest.mark.parametrize("lat,pde,levels", G.SUPPORTED)
 def test_parity_fp32(mm, lat, pde, levels):
     rng = np.random.default_rng(G.RNG_SEED + 1)
-    n = SIZES_2D[0] if G.dims(lat) == 2 else SIZES_3D[0]
+    n = SIZES_2D[0] if G.dims(lat) == 2 else SIZES_3D[1]
     kw, prob = G.case(lat, pde, levels, n, "fp32")
     L0 = G.random_level(prob, rng)
     L1 = G.random_level(prob, rng) if levels == 3 else None
@@ -78,7 +78,7 @@ def test_parity_fp32(mm, lat, pde, levels):
 @pytest.mark.parametrize("sr", [False, True])
 def test_parity_bf16_one_step(mm, lat, pde, levels, sr):
     rng = np.random.default_rng(G.RNG_SEED + 2)
-    n = [260, 33] if G.dims(lat) == 2 else [40, 21, 9]
+    n = [260, 33] if G.dims(lat) == 2 else [140, 13, 7]
     kw, prob = G.case(lat, pde, levels, n, "bf16")
     refs = [1.0 if (pde == "NSE" and f == 0) else 0.0 for f in range(prob.nf)]
     L0 = G.random_level(prob, rng)

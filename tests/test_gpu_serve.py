@@ -30,6 +30,8 @@ MIX = [
     ("D3Q19", "NCDE", 2, [16, 16, 16], "bf16", 14),
     ("D2Q9", "NSE", 2, [300, 90], "fp32", 3),
     ("D2Q9", "NCDE", 2, [70, 70], "fp32", 0),
+    ("D2Q9", "NCDE", 3, [260, 260], "fp32", 7),   # large enough for its own march launches
+    ("D2Q9", "NSE", 2, [512, 160], "bf16", 6),
 ]
 
 
