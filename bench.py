@@ -38,6 +38,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device: str = "cpu") -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(ranks: int, nodes_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank advances its own grid `steps` times in `seconds`
+    (the slowest rank's time), so the job updates ranks x nodes x steps lattice nodes."""
+    return ranks * nodes_per_rank * steps / seconds / 1e6
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -353,19 +370,18 @@ def run_ours(args):
         clocks = sampler.stop()
         total_ms = t_start.elapsed_time(t_end)
         launch_ms = [a.elapsed_time(b) for a, b in ev]
-        if ws > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
         steps_done = args.steps * depth
         ms_per_step = total_ms / steps_done
-        value = ws * nodes * steps_done / (total_ms / 1e3) / 1e6
+        value = job_mlups(ws, nodes, steps_done, total_ms / 1e3)
 
         # roofline of the dominant (only) kernel: compulsory bytes per launch / launch time
         peak, peak_kind = measured_peaks()
         avg_launch_s = statistics.mean(launch_ms) / 1e3
-        alg_bytes = bytes_per_lu * nodes * depth
+        # a launch reads and writes the stored level once, whatever its temporal depth
+        alg_bytes = bytes_per_lu * nodes
         achieved = alg_bytes / avg_launch_s / 1e9
+        effective = bytes_per_lu * nodes * depth / avg_launch_s / 1e9
         kernel_name = info.kernel.decode()
         traffic = traffic_from_profile(kernel_name, args.workload)
 
@@ -389,11 +405,8 @@ def run_ours(args):
             s.reduce(mmfd.MMFD_RED_SUM)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e_value = ws * nodes * e2e_steps / e2e_s / 1e6
+        e2e_s = max_over_ranks(e2e_s, "cuda")
+        e2e_value = job_mlups(ws, nodes, e2e_steps, e2e_s)
         s.close()
 
     if rank != 0:
@@ -414,7 +427,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kernel_name, "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3},
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                     "effective_gbs": effective},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},

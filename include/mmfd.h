@@ -77,7 +77,16 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        NSE momentum set.
  *  storage, ref[4]       storage type; BF16 offsets per field (default ref = {rho0 or 0, 0, ..}).
  *  flags                 MMFD_FLAG_*.
- *  temporal_depth        steps fused per kernel launch: 0 = autotuned, 1 = none, T >= 2.
+ *  temporal_depth        time steps fused per kernel launch (temporal blocking): 1 = none;
+ *                        T >= 2 asks for T; 0 asks for the deepest available.  Blocking is
+ *                        available for 2D two-level LCDE / NCDE grids with nx >= 128 and
+ *                        ny >= 2T, up to T = 2 (FP64), 4 (FP32), 5 (BF16) -- the x ghost
+ *                        columns of the padded layout hold that many levels.  Larger requests
+ *                        are clamped, other configurations run unblocked; mmfd_get_info reports
+ *                        the depth in use.  mmfd_step(n) runs n / T blocked launches and the
+ *                        remaining n % T steps unblocked.  With BF16 storage a blocked solver
+ *                        rounds the state to BF16 once per T steps (the intermediate levels
+ *                        stay in FP32).
  *  seed                  BF16 stochastic-rounding seed.
  *  stream                cudaStream_t (NULL = legacy default stream).
  *  alloc/free_fn/ctx     device allocator for the level buffers (NULL = cudaMalloc/cudaFree).

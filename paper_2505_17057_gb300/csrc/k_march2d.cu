@@ -5,17 +5,23 @@ namespace mmfd {
 
 namespace {
 
-// Ring depth per warp: about 8 KB of stages, between 3 and 12 rows in flight.
+// Rows per stage: the scalar PDEs stage two input rows per TMA box, which halves the per-row
+// waits, copy issues and accumulator rotations of their short stencils; the NSE's register
+// budget keeps one.
+constexpr int rows_per_stage(int pde) { return pde == PDE_NSE ? 1 : 2; }
+
+// Ring depth per warp: about 8 KB of stages, between 3 and 12 stages in flight.
 template <int LAT, int PDE, int LEVELS, int ST, int LN>
 constexpr int march2d_stages() {
-    constexpr size_t per = (march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 1, 1, LN>() - 256);
+    constexpr size_t per = (march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 1, 1, LN, rows_per_stage(PDE)>() - 256);
     constexpr size_t n = 8192 / per;
     return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
 }
 
 template <int LAT, int PDE, int LEVELS, int ST, int LN>
 cudaError_t launch_variant(const LaunchArgs& a) {
-    return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST, LN>(), LN>(a);
+    return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST, LN>(), LN,
+                            rows_per_stage(PDE)>(a);
 }
 
 // 4 nodes per lane (128-column items: the TMA box of 128 + 2 x 16 bytes stays within the
@@ -45,6 +51,8 @@ LaunchFn pick_ls(int levels, int st) {
 }
 
 }  // namespace
+
+int march2d_rows_per_stage(int pde) { return rows_per_stage(pde); }
 
 LaunchFn find_march2d(int lat, int pde, int levels, int st) {
     if (lat == LAT_D2Q5) return pde == PDE_LCDE ? pick_ls<LAT_D2Q5, PDE_LCDE>(levels, st) : nullptr;

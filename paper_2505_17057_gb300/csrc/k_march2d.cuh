@@ -54,6 +54,50 @@ __device__ __forceinline__ void stg4(void* p, const typename Storage<ST>::S s[4]
     }
 }
 
+// Store four consecutive nodes xb .. xb+3 (xb a multiple of 4) of row y, plane z, together with
+// their periodic ghost images: the x ghosts within g.gx of either x edge, the ghost row of
+// y = 0 / ny - 1 and, in 3D, the ghost plane of z = 0 / nz - 1 (with all combinations).  Nodes
+// outside [0, nx) are skipped.  Straight-line predicated stores, no local arrays: the warps that
+// own edge strips and rows must not fall behind the others.
+template <int DIM, int ST>
+__device__ __noinline__ void store4_ghosted(typename Storage<ST>::S* f, const Geom g, int xb, int y, int z,
+                                               const typename Storage<ST>::S (&sv)[4]) {
+    using S = typename Storage<ST>::S;
+    const bool full = xb >= 0 && xb + 3 < g.nx;
+    const bool xedge = xb < g.gx || xb + 3 >= g.nx - g.gx;
+    auto put_row = [&](int yy, int zz) {
+        S* row = f + g.at(0, yy, zz);
+        if (full) {
+            stg4<ST>(row + xb, sv);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (xb + k >= 0 && xb + k < g.nx) row[xb + k] = sv[k];
+        }
+        if (xedge) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = xb + k;
+                if (x >= 0 && x < g.nx) {
+                    if (x < g.gx) row[x + g.nx] = sv[k];
+                    if (x >= g.nx - g.gx) row[x - g.nx] = sv[k];
+                }
+            }
+        }
+    };
+    const bool ylo = y == 0, yhi = y == g.ny - 1;
+    auto put_plane = [&](int zz) {
+        put_row(y, zz);
+        if (ylo) put_row(g.ny, zz);
+        if (yhi) put_row(-1, zz);
+    };
+    put_plane(z);
+    if constexpr (DIM == 3) {
+        if (z == 0) put_plane(g.nz);
+        if (z == g.nz - 1) put_plane(-1);
+    }
+}
+
 // Work decomposition: an item is (128-column warp strip, H-row segment).  Every warp walks its
 // own sequence of items (item = global warp id, + total warps, ...) as one stream of input
 // rows; lane 0 keeps NSTAGE rows of that stream in flight through the warp's private ring, so
@@ -105,7 +149,7 @@ __host__ __device__ constexpr int pushed_pairs(int C) {
     return m;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS>
 __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ TmapSet maps, Geom g,
                                                      void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                      StepExtra ex, int H, int nitems, int* __restrict__ err) {
@@ -116,11 +160,12 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     constexpr int ALIGN = 16 / ES;
     constexpr int COLS = 32 * LN;                         // columns per warp item
     constexpr int BOXW = COLS + 2 * ALIGN;                // TMA box width (elements)
-    constexpr int SLOT = ((BOXW * ES + 127) / 128) * 128; // bytes per (stage, field) slot
+    constexpr int ROWB = BOXW * ES;                       // bytes per staged row
+    constexpr int SLOT = ((RPS * ROWB + 127) / 128) * 128; // bytes per (stage, field) slot: RPS rows
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr int NIN = NF * (LEVELS - 1);
     constexpr int NP = lat_npair(LAT);
-    constexpr uint32_t kTx = (uint32_t)(NIN * BOXW * ES);
+    constexpr uint32_t kTx = (uint32_t)(NIN * RPS * ROWB);
     constexpr size_t kRingBytes = (size_t)NSTAGE * NIN * SLOT;
     static_assert(BOXW <= 256, "TMA box too wide");
 
@@ -147,7 +192,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
             const int seg = p_item / strips;
             p_xcol = (p_item - seg * strips) * COLS;     // padded column of the box
             p_prow0 = seg * H;                            // padded row of input row y0 - 1
-            p_rows = min(H, g.ny - seg * H) + 2;
+            p_rows = (min(H, g.ny - seg * H) + 2 + RPS - 1) / RPS * RPS;
         }
     };
     p_load_item();
@@ -160,7 +205,8 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
         for (int q = 0; q < NIN; ++q) tma_load_2d(slot(ps, q), &maps.m[q], &full[ps], p_xcol, p_prow0 + p_row);
         ++issued;
         ps = ps + 1 == NSTAGE ? 0 : ps + 1;
-        if (++p_row == p_rows) {
+        p_row += RPS;
+        if (p_row == p_rows) {
             p_item += wstride;
             p_row = 0;
             p_load_item();
@@ -177,186 +223,196 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     }
     __syncwarp();
 
-    T acc0[LN][NF], acc1[LN][NF], acc2[LN][NF];
+    // Accumulators of the output rows around the staged input rows: with RPS = 1, acc0/1/2 are
+    // rows r-1, r, r+1 of input row r; with RPS = 2 (two input rows r, r+1 per stage), acc0..3
+    // are rows r-1 .. r+2.
+    T acc0[LN][NF], acc1[LN][NF], acc2[LN][NF], acc3[LN][NF];
     S* out = static_cast<S*>(outv);
-    int cs = 0;              // stage of the next row to consume
+    int cs = 0;              // stage of the next rows to consume
     uint32_t cphase = 0;     // its mbarrier phase parity
     long long consumed = 0;
     bool failed = false;
 
-    // One input row: push it into (accP = row r-1, accC = row r, accN = row r+1); row r-1 is then
-    // complete and is stored.
-    auto row_body = [&](int i, int y0, int xb, T (&accP)[LN][NF], T (&accC)[LN][NF], T (&accN)[LN][NF]) -> bool {
-                const int s = cs;
-                const bool ok = mbar_wait_bounded(&full[s], cphase);
-                if (__any_sync(0xffffffffu, !ok)) return false;
+    // Push input row j of stage s into (accP = row r-1, accC = row r, accN = row r+1).
+    auto push_row = [&](int s, int j, T (&accP)[LN][NF], T (&accC)[LN][NF], T (&accN)[LN][NF]) {
 #pragma unroll
-                for (int l = 0; l < LEVELS - 1; ++l) {
-                    // raw fields of the LN + 2 nodes xb-1 .. xb+LN of this input row
-                    T raw[LN + 2][NF];
+        for (int l = 0; l < LEVELS - 1; ++l) {
+            // raw fields of the LN + 2 nodes xb-1 .. xb+LN of this input row
+            T raw[LN + 2][NF];
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        const unsigned char* base = slot(s, l * NF + f);
-                        const S* sp = reinterpret_cast<const S*>(base);
+            for (int f = 0; f < NF; ++f) {
+                const unsigned char* base = slot(s, l * NF + f) + j * ROWB;
+                const S* sp = reinterpret_cast<const S*>(base);
 #pragma unroll
-                        for (int k4 = 0; k4 < LN; k4 += 4) {
-                            T v4[4];
-                            lds4<ST>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
-                            raw[1 + k4][f] = v4[0];
-                            raw[2 + k4][f] = v4[1];
-                            raw[3 + k4][f] = v4[2];
-                            raw[4 + k4][f] = v4[3];
+                for (int k4 = 0; k4 < LN; k4 += 4) {
+                    T v4[4];
+                    lds4<ST>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
+                    raw[1 + k4][f] = v4[0];
+                    raw[2 + k4][f] = v4[1];
+                    raw[3 + k4][f] = v4[2];
+                    raw[4 + k4][f] = v4[3];
+                }
+                raw[0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
+                raw[LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
+            }
+            static_for<0, LN + 2>([&](auto cc) {
+                constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. LN
+                constexpr bool OWN = C >= 0 && C < LN;
+                if constexpr (PDE == PDE_LCDE) {
+                    const T phi = raw[C + 1][0];
+                    if constexpr (OWN) accC[C][0] += cf.W0[l] * phi;
+                    static_for<0, NP>([&](auto pcc) {
+                        constexpr int P_ = decltype(pcc)::value;
+                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                        constexpr int TP = C - EX, TM = C + EX;
+                        if constexpr (TP >= 0 && TP < LN) {
+                            if constexpr (EY == 1) accP[TP][0] += cf.Wp[l][P_] * phi;
+                            else accC[TP][0] += cf.Wp[l][P_] * phi;
                         }
-                        raw[0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
-                        raw[LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
-                    }
-                    static_for<0, LN + 2>([&](auto cc) {
-                        constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. LN
-                        constexpr bool OWN = C >= 0 && C < LN;
-                        if constexpr (PDE == PDE_LCDE) {
-                            const T phi = raw[C + 1][0];
-                            if constexpr (OWN) accC[C][0] += cf.W0[l] * phi;
-                            static_for<0, NP>([&](auto pcc) {
-                                constexpr int P_ = decltype(pcc)::value;
-                                constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                                constexpr int TP = C - EX, TM = C + EX;
-                                if constexpr (TP >= 0 && TP < LN) {
-                                    if constexpr (EY == 1) accP[TP][0] += cf.Wp[l][P_] * phi;
-                                    else accC[TP][0] += cf.Wp[l][P_] * phi;
-                                }
-                                if constexpr (TM >= 0 && TM < LN) {
-                                    if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P_] * phi;
-                                    else accC[TM][0] += cf.Wm[l][P_] * phi;
-                                }
-                            });
-                        } else {
-                            constexpr int MASK = pushed_pairs<LAT, LN>(C);
-                            const T* f = raw[C + 1];
-                            T A, B[2], m2 = T(0), uxx = T(0), uyy = T(0), uxy = T(0);
-                            if constexpr (PDE == PDE_NSE) {
-                                A = f[0];
-                                B[0] = f[1];
-                                B[1] = f[2];
-                                uxx = f[1] * f[1];
-                                uyy = f[2] * f[2];
-                                uxy = f[1] * f[2];
-                            } else {
-                                const T phi = f[0];
-                                A = phi;
-                                m2 = (((cf.m2[4] * phi + cf.m2[3]) * phi + cf.m2[2]) * phi + cf.m2[1]) * phi + cf.m2[0];
+                        if constexpr (TM >= 0 && TM < LN) {
+                            if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P_] * phi;
+                            else accC[TM][0] += cf.Wm[l][P_] * phi;
+                        }
+                    });
+                } else {
+                    constexpr int MASK = pushed_pairs<LAT, LN>(C);
+                    const T* f = raw[C + 1];
+                    T A, B[2], m2 = T(0), uxx = T(0), uyy = T(0), uxy = T(0);
+                    if constexpr (PDE == PDE_NSE) {
+                        A = f[0];
+                        B[0] = f[1];
+                        B[1] = f[2];
+                        uxx = f[1] * f[1];
+                        uyy = f[2] * f[2];
+                        uxy = f[1] * f[2];
+                    } else {
+                        const T phi = f[0];
+                        A = phi;
+                        m2 = (((cf.m2[4] * phi + cf.m2[3]) * phi + cf.m2[2]) * phi + cf.m2[1]) * phi + cf.m2[0];
 #pragma unroll
-                                for (int a = 0; a < 2; ++a)
-                                    B[a] = ((cf.flux[a][3] * phi + cf.flux[a][2]) * phi + cf.flux[a][1]) * phi + cf.flux[a][0];
-                            }
-                            if constexpr (OWN) {
-                                T rest;
-                                if constexpr (PDE == PDE_NSE) rest = cf.rC[1] * uyy + (cf.rC[0] * uxx + cf.rA * A);
-                                else rest = cf.rM2 * m2 + cf.rPhi * A;
-                                accC[C][0] += cf.ap[l] * rest + cf.a0[l] * A;
+                        for (int a = 0; a < 2; ++a)
+                            B[a] = ((cf.flux[a][3] * phi + cf.flux[a][2]) * phi + cf.flux[a][1]) * phi + cf.flux[a][0];
+                    }
+                    if constexpr (OWN) {
+                        T rest;
+                        if constexpr (PDE == PDE_NSE) rest = cf.rC[1] * uyy + (cf.rC[0] * uxx + cf.rA * A);
+                        else rest = cf.rM2 * m2 + cf.rPhi * A;
+                        accC[C][0] += cf.ap[l] * rest + cf.a0[l] * A;
+                        if constexpr (PDE == PDE_NSE) {
+                            accC[C][1] += cf.ab0[l] * B[0];
+                            accC[C][2] += cf.ab0[l] * B[1];
+                        }
+                    }
+                    T E[4], O[4];
+                    pair_eo<LAT, PDE, MASK>(cf, A, B, m2, uxx, uyy, uxy, E, O);
+                    static_for<0, NP>([&](auto pcc) {
+                        constexpr int P_ = decltype(pcc)::value;
+                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                        constexpr int TP = C - EX, TM = C + EX;
+                        constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
+                        if constexpr (HP || HM) {
+                            // rho / phi: a+ E +- a- O; momentum: abar+ O +- abar- E (Eq. (2-4-1))
+                            const T sE = cf.ap[l] * E[P_];
+                            [[maybe_unused]] T mO = T(0);
+                            if constexpr (PDE == PDE_NSE) mO = cf.abp[l] * O[P_];
+                            auto push = [&](T (&acc)[LN][NF], int node, T sv, T mv) {
+                                acc[node][0] += sv;
                                 if constexpr (PDE == PDE_NSE) {
-                                    accC[C][1] += cf.ab0[l] * B[0];
-                                    accC[C][2] += cf.ab0[l] * B[1];
+                                    if constexpr (EX != 0) acc[node][1] += (T(EX) * cf.fmom[0]) * mv;
+                                    if constexpr (EY != 0) acc[node][2] += (T(EY) * cf.fmom[1]) * mv;
                                 }
+                            };
+                            if constexpr (HP) {
+                                const T sv = cf.am[l] * O[P_] + sE;
+                                T mv = T(0);
+                                if constexpr (PDE == PDE_NSE) mv = cf.abm[l] * E[P_] + mO;
+                                if constexpr (EY == 1) push(accP, TP, sv, mv);
+                                else push(accC, TP, sv, mv);
                             }
-                            T E[4], O[4];
-                            pair_eo<LAT, PDE, MASK>(cf, A, B, m2, uxx, uyy, uxy, E, O);
-                            static_for<0, NP>([&](auto pcc) {
-                                constexpr int P_ = decltype(pcc)::value;
-                                constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                                constexpr int TP = C - EX, TM = C + EX;
-                                constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
-                                if constexpr (HP || HM) {
-                                    // rho / phi: a+ E +- a- O; momentum: abar+ O +- abar- E (Eq. (2-4-1))
-                                    const T sE = cf.ap[l] * E[P_];
-                                    [[maybe_unused]] T mO = T(0);
-                                    if constexpr (PDE == PDE_NSE) mO = cf.abp[l] * O[P_];
-                                    auto push = [&](T (&acc)[LN][NF], int node, T sv, T mv) {
-                                        acc[node][0] += sv;
-                                        if constexpr (PDE == PDE_NSE) {
-                                            if constexpr (EX != 0) acc[node][1] += (T(EX) * cf.fmom[0]) * mv;
-                                            if constexpr (EY != 0) acc[node][2] += (T(EY) * cf.fmom[1]) * mv;
-                                        }
-                                    };
-                                    if constexpr (HP) {
-                                        const T sv = cf.am[l] * O[P_] + sE;
-                                        T mv = T(0);
-                                        if constexpr (PDE == PDE_NSE) mv = cf.abm[l] * E[P_] + mO;
-                                        if constexpr (EY == 1) push(accP, TP, sv, mv);
-                                        else push(accC, TP, sv, mv);
-                                    }
-                                    if constexpr (HM) {
-                                        const T sv = sE - cf.am[l] * O[P_];
-                                        T mv = T(0);
-                                        if constexpr (PDE == PDE_NSE) mv = mO - cf.abm[l] * E[P_];
-                                        if constexpr (EY == 1) push(accN, TM, sv, mv);
-                                        else push(accC, TM, sv, mv);
-                                    }
-                                }
-                            });
+                            if constexpr (HM) {
+                                const T sv = sE - cf.am[l] * O[P_];
+                                T mv = T(0);
+                                if constexpr (PDE == PDE_NSE) mv = mO - cf.abm[l] * E[P_];
+                                if constexpr (EY == 1) push(accN, TM, sv, mv);
+                                else push(accC, TM, sv, mv);
+                            }
                         }
                     });
                 }
-                ++consumed;
-                cs = cs + 1 == NSTAGE ? 0 : cs + 1;
-                if (cs == 0) cphase ^= 1u;
-                __syncwarp();  // every lane is done reading stage s
-                if (lane == 0) {
-                    fence_proxy_async_smem();
-                    issue_next();
+            });
+        }
+    };
+
+    // store the completed output row yo from acc
+    auto store_row = [&](int yo, int xb, const T (&acc)[LN][NF]) {
+        const long long nb = (long long)yo * g.nx;
+        const bool interior = xb >= g.gx && xb + LN - 1 < g.nx - g.gx && yo > 0 && yo < g.ny - 1;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            S* fo = out + (size_t)f * g.fs;
+#pragma unroll
+            for (int k4 = 0; k4 < LN; k4 += 4) {
+                S sv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
+                    sv[k] = Tr::pack(acc[k4 + k][f], cf.ref[f], rnd);
                 }
-                // row y0 - 1 + i - 1 is complete
-                if (i >= 2 && xb < g.nx) {
-                    const int yo = y0 + i - 2;
-                    const long long nb = (long long)yo * g.nx;
-                    const bool interior = xb > 0 && xb + LN - 1 < g.nx - 1 && yo > 0 && yo < g.ny - 1;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        S* fo = out + (size_t)f * g.fs;
-#pragma unroll
-                        for (int k4 = 0; k4 < LN; k4 += 4) {
-                            S sv[4];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
-                                sv[k] = Tr::pack(accP[k4 + k][f], cf.ref[f], rnd);
-                            }
-                            if (interior) {
-                                stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    if (xb + k4 + k < g.nx) store_with_ghosts<2>(fo, g, xb + k4 + k, yo, 0, sv[k]);
-                            }
-                        }
-                    }
-                }
-        return true;
+                if (interior) stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
+                else store4_ghosted<2, ST>(fo, g, xb + k4, yo, 0, sv);
+            }
+        }
     };
 
     for (int item = wid; item < nitems && !failed; item += wstride) {
         const int seg = item / strips;
         const int x0 = (item - seg * strips) * COLS;
         const int y0 = seg * H;
-        const int nrows = min(H, g.ny - y0) + 2;
+        const int hrows = min(H, g.ny - y0);                       // output rows of the item
+        const int nrows = (hrows + 2 + RPS - 1) / RPS * RPS;       // staged input rows
         const int xb = x0 + lane * LN;
 #pragma unroll
         for (int k = 0; k < LN; ++k)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc0[k][f] = acc1[k][f] = acc2[k][f] = T(0);
-        // One copy of the row body: unrolling it three times to rotate the accumulator sets by
-        // renaming instead of moves overflowed the instruction cache and ran slower.
-        for (int i = 0; i < nrows; ++i) {
-            if (!row_body(i, y0, xb, acc0, acc1, acc2)) {
+            for (int f = 0; f < NF; ++f) acc0[k][f] = acc1[k][f] = acc2[k][f] = acc3[k][f] = T(0);
+        for (int i = 0; i < nrows; i += RPS) {
+            const int s = cs;
+            const bool ok = mbar_wait_bounded(&full[s], cphase);
+            if (__any_sync(0xffffffffu, !ok)) {
                 failed = true;
                 break;
+            }
+            push_row(s, 0, acc0, acc1, acc2);
+            if constexpr (RPS == 2) push_row(s, 1, acc1, acc2, acc3);
+            ++consumed;
+            cs = cs + 1 == NSTAGE ? 0 : cs + 1;
+            if (cs == 0) cphase ^= 1u;
+            __syncwarp();  // every lane is done reading stage s
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue_next();
+            }
+            // input row i (y0 - 1 + i) completes output row y0 + i - 2
+            if (xb < g.nx) {
+                if (i >= 2) store_row(y0 + i - 2, xb, acc0);
+                if constexpr (RPS == 2) {
+                    if (i >= 1 && i - 1 < hrows) store_row(y0 + i - 1, xb, acc1);
+                }
             }
 #pragma unroll
             for (int k = 0; k < LN; ++k)
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    acc0[k][f] = acc1[k][f];
-                    acc1[k][f] = acc2[k][f];
-                    acc2[k][f] = T(0);
+                    if constexpr (RPS == 1) {
+                        acc0[k][f] = acc1[k][f];
+                        acc1[k][f] = acc2[k][f];
+                        acc2[k][f] = T(0);
+                    } else {
+                        acc0[k][f] = acc2[k][f];
+                        acc1[k][f] = acc3[k][f];
+                        acc2[k][f] = T(0);
+                        acc3[k][f] = T(0);
+                    }
                 }
         }
     }
@@ -369,19 +425,19 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     __syncwarp();
 }
 
-template <int ST, int LEVELS, int NF, int NW, int NSTAGE, int LN>
+template <int ST, int LEVELS, int NF, int NW, int NSTAGE, int LN, int RPS>
 constexpr size_t march2d_smem() {
     constexpr int ES = (int)sizeof(typename Storage<ST>::S);
-    constexpr int SLOT = (((32 * LN + 2 * (16 / ES)) * ES + 127) / 128) * 128;
+    constexpr int SLOT = ((RPS * (32 * LN + 2 * (16 / ES)) * ES + 127) / 128) * 128;
     return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * NF * (LEVELS - 1) * SLOT;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS>
 cudaError_t launch_march2d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
-    constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE, LN>();
-    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN>;
+    constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE, LN, RPS>();
+    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

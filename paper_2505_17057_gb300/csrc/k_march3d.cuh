@@ -236,7 +236,7 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
             if (i >= 2 && xb < g.nx && y < g.ny) {
                 const int zo = z0 + i - 2;
                 const long long nb = ((long long)zo * g.ny + y) * g.nx;
-                const bool interior = xb > 0 && xb + LN - 1 < g.nx - 1 && y > 0 && y < g.ny - 1 && zo > 0 &&
+                const bool interior = xb >= g.gx && xb + LN - 1 < g.nx - g.gx && y > 0 && y < g.ny - 1 && zo > 0 &&
                                       zo < g.nz - 1;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -247,13 +247,8 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
                         sv[n] = Tr::pack(accP[n][f], cf.ref[f], rnd);
                     }
                     S* fo = out + (size_t)f * g.fs;
-                    if (interior) {
-                        stg4<ST>(fo + g.at(xb, y, zo), sv);
-                    } else {
-#pragma unroll
-                        for (int n = 0; n < 4; ++n)
-                            if (xb + n < g.nx) store_with_ghosts<3>(fo, g, xb + n, y, zo, sv[n]);
-                    }
+                    if (interior) stg4<ST>(fo + g.at(xb, y, zo), sv);
+                    else store4_ghosted<3, ST>(fo, g, xb, y, zo, sv);
                 }
             }
 #pragma unroll

@@ -35,7 +35,7 @@ __global__ void k_pack(Geom g, const void* __restrict__ src, int src_dtype, void
             const long long i = base + x;
             const double v = src_dtype == 0 ? static_cast<const double*>(src)[i] : (double)static_cast<const float*>(src)[i];
             const S sv = Tr::pack((T)v, (T)ref, 0u);
-            const bool edge = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 ||
+            const bool edge = x < g.gx || x >= g.nx - g.gx || y == 0 || y == g.ny - 1 ||
                               (g.dim == 3 && (z == 0 || z == g.nz - 1));
             if (!edge) {
                 d[g.at(x, y, z)] = sv;

@@ -35,8 +35,16 @@ using LaunchFn = cudaError_t (*)(const LaunchArgs&);
 LaunchFn find_direct(int lat, int pde, int levels, int st);
 // Row-marching 2D kernels fed by a TMA (cp.async.bulk.tensor) shared-memory ring.
 LaunchFn find_march2d(int lat, int pde, int levels, int st);
+// Input rows per TMA box (stage) of the 2D marching kernel for this PDE; its tensor maps use
+// boxes of 128 + 2 x 16 bytes by this many rows.
+int march2d_rows_per_stage(int pde);
 // 3D plane-marching kernels (z march, x-y tile staged in shared memory by TMA).
 LaunchFn find_march3d(int lat, int pde, int levels, int st);
+// Temporally blocked 2D kernel advancing `depth` levels per launch (two-level LCDE / NCDE;
+// nullptr where unsupported) and the largest depth its ghost columns allow for storage st.
+// It reads the level through the same 2-row-box tensor maps as k_march2d.
+LaunchFn find_march2d_tb(int lat, int pde, int levels, int st, int depth);
+int march2d_tb_max_depth(int st);
 // Rows of the x-y tile a 3D march CTA stages per plane (the TMA box is 128+halo x rows+2 x 1).
 int march3d_tile_rows(int pde);
 

@@ -173,7 +173,7 @@ int admit(Server* s, Req* q) {
                                     : find_march3d(q->r->lat, q->r->pde, q->r->levels, q->r->st);
         bool ok = fn != nullptr;
         const int boxw = 128 + 2 * (16 / q->g.es);
-        const int boxh = q->g.dim == 2 ? 1 : march3d_tile_rows(q->r->pde) + 2;
+        const int boxh = q->g.dim == 2 ? march2d_rows_per_stage(q->r->pde) : march3d_tile_rows(q->r->pde) + 2;
         for (int b = 0; ok && b < nl; ++b)
             for (int f = 0; ok && f < q->g.nf; ++f) {
                 char* base = static_cast<char*>(q->lev[b]) + (size_t)f * q->g.fs * q->g.es;

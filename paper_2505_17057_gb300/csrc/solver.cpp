@@ -140,9 +140,9 @@ int solver_step(Solver* s, long long nsteps) {
             a.maps = &s->launch_maps;
         }
         if (blocked) {
-            // the blocked kernel writes level t + depth dt into next(); for three-level
-            // solvers it also leaves level t + (depth - 1) dt in the buffer that becomes prev.
+            // the blocked kernel (two-level solvers) writes level t + depth dt into next()
             a.out = s->lev[s->next()];
+            a.ex.step = s->steps_done + s->depth;
             cudaError_t e = s->fn_block(a);
             if (e != cudaSuccess) return cuda_fail(e, "blocked step kernel");
             s->cur = s->next();
@@ -255,7 +255,8 @@ int solver_pick_kernels(Solver* s) {
             for (int b = 0; b < s->nlev; ++b)
                 for (int f = 0; f < s->g.nf; ++f) {
                     char* base = static_cast<char*>(s->lev[b]) + (size_t)f * s->g.fs * es;
-                    if (encode_field_map(&s->tmaps[b][f], base, s->r.st, s->g, boxw, 1, 1) != 0) {
+                    if (encode_field_map(&s->tmaps[b][f], base, s->r.st, s->g, boxw,
+                                         march2d_rows_per_stage(s->r.pde), 1) != 0) {
                         s->fn = nullptr;
                         break;
                     }
@@ -265,6 +266,19 @@ int solver_pick_kernels(Solver* s) {
             s->use_tma = true;
             s->kernel_name = "k_march2d";
             s->H = 0;  // chosen by the launcher from the kernel's occupancy
+            // temporal blocking: 0 asks for the deepest blocking the storage allows
+            const int maxd = march2d_tb_max_depth(s->r.st);
+            int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
+            if (want > maxd) want = maxd;
+            // (the blocked kernel stages two rows per box, as the solver's maps for these PDEs do)
+            if (want >= 2 && s->g.ny >= 2 * want && march2d_rows_per_stage(s->r.pde) == 2) {
+                s->fn_block = find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, want);
+                if (s->fn_block) {
+                    s->depth = want;
+                    s->g.gx = want;   // every writer keeps the x ghost columns to this depth
+                    s->kernel_name = "k_march2d_tb";
+                }
+            }
             return MMFD_OK;
         }
     }

@@ -125,14 +125,15 @@ struct Basis<LAT, PDE_NSE, T> {
 
 // ------------------------------------------------------------------ ghost write-through
 // Write value v of node (x, y, z) to its interior slot and to every periodic ghost image
-// (x == 0 also lands at x = nx, x == nx - 1 also at x = -1; likewise y, z; all combinations).
+// (x < gx also lands at x + nx, x >= nx - gx also at x - nx, with gx the ghost depth in x;
+// y == 0 also at y = ny, y == ny - 1 at y = -1; likewise z; all combinations).
 template <int DIM, typename S>
 __device__ __forceinline__ void store_with_ghosts(S* f, const Geom& g, int x, int y, int z, S v) {
     int xs[3], ys[3], zs[3];
     int nxs = 0, nys = 0, nzs = 0;
     xs[nxs++] = x;
-    if (x == 0) xs[nxs++] = g.nx;
-    if (x == g.nx - 1) xs[nxs++] = -1;
+    if (x < g.gx) xs[nxs++] = x + g.nx;
+    if (x >= g.nx - g.gx) xs[nxs++] = x - g.nx;
     ys[nys++] = y;
     if (y == 0) ys[nys++] = g.ny;
     if (y == g.ny - 1) ys[nys++] = -1;
