@@ -339,6 +339,12 @@ def run_ours(args):
         d = mmfd.make_desc(**desc_kw, temporal_depth=args.depth)
         s = mmfd.Solver(d, stream=stream)
         s.set_fields(fields)
+        tuned = None
+        if args.tune:
+            # outside the timed region: trial launches write only the spare buffer
+            t = s.autotune(None)
+            tuned = {"temporal_depth": t.temporal_depth, "rows_per_item": t.rows_per_item,
+                     "candidates": t.candidates, "ms_per_step": t.ms_per_step}
         info = s.get_info()
         depth = max(1, info.temporal_depth)
         nodes = n ** dim
@@ -422,6 +428,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "grid": [n] * dim, "lattice": desc_kw["lattice"],
                    "pde": {"NSE": "NSE (He-Luo)"}.get(desc_kw["pde"], desc_kw["pde"]),
                    "levels": desc_kw["levels"], "storage": args.storage, "temporal_depth": depth,
+                   "autotuned": tuned,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -455,7 +462,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv2d_4096")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
-    ap.add_argument("--depth", type=int, default=1, help="temporal blocking depth (1 = plain step)")
+    ap.add_argument("--depth", type=int, default=1,
+                    help="temporal blocking depth (1 = plain step, 0 = chosen by the autotuner)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the autotuner (work-item height from the launcher's heuristic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=200, help="requests in the serving run (0 = skip)")
     args = ap.parse_args()

@@ -202,6 +202,30 @@ int mmfd_destroy(mmfd_solver* s);
 /* Host-only helpers (no GPU needed). */
 /* Eq. (X): (a_0, A_10, A_11, A_21, A_22) -> a = (a_{-1}, a_0, a_1), ahat likewise. */
 int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3]);
+/* ---- autotuner --------------------------------------------------------------------------
+ * Not from the paper: a build choice.  The step kernels take two tuning parameters, the temporal
+ * depth (time steps per launch, where blocking is available) and the work-item height (rows in
+ * 2D, planes in 3D, streamed per warp or CTA item; 0 = the launcher's occupancy-based choice).
+ * mmfd_autotune times candidate pairs on this solver's own grid -- depths 1 .. the deepest the
+ * solver allows when it was created with temporal_depth = 0, else the depth in use; heights 0,
+ * 16, 32, 64, 128 (2D) or 0, 8, 16, 32, 64 (3D marching kernels) -- and keeps the fastest for
+ * later mmfd_step calls.  Trial launches read the current level(s) and write only the spare
+ * buffer, so the solver's fields and step count are unchanged; the call synchronises the
+ * solver's stream.  Any solver can be tuned, before or after its fields are set.
+ * cache_path (NULL = no cache): a text file of earlier choices, one line per key
+ * (device name, SM count, lattice, PDE, levels, storage, flags, grid, depth mode).  A hit applies
+ * the stored choice without timing; a miss times the candidates and appends the choice.  A
+ * cache that cannot be read or written is ignored (the tuning result still applies). */
+typedef struct {
+    int temporal_depth;     /* depth now in use */
+    int rows_per_item;      /* work-item height now in use (0 = launcher's choice) */
+    double ms_per_step;     /* measured time per time step of that choice (cached value on a hit) */
+    int candidates;         /* configurations timed (0 on a cache hit) */
+    int from_cache;         /* 1 if the choice came from cache_path */
+} mmfd_tune_info;
+
+int mmfd_autotune(mmfd_solver* s, const char* cache_path, mmfd_tune_info* out);
+
 /* Resolve a descriptor's constants without touching the GPU (info filled as by create). */
 int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out);
 

@@ -98,6 +98,71 @@ __device__ __noinline__ void store4_ghosted(typename Storage<ST>::S* f, const Ge
     }
 }
 
+// The edge store of the marching kernels.  The common edge cases are inline and cheap -- a row
+// on a y edge adds one vector store into the ghost row; a lane whose nodes lie within g.gx of an
+// x edge writes their ghost images as whole vectors, filling the 16-byte ghost block at that
+// edge completely -- because a single lane on a slow path holds back its whole warp on every
+// row it stores, and because ghost blocks left partly written made the next step's loads of
+// the edge strips slow (the warps owning them then finished long after the rest).  Rare cases
+// (z edge planes, ny == 1, vectors that straddle x = nx) take store4_ghosted.  Lanes with no
+// node in [0, nx) store nothing.
+template <int DIM, int ST>
+__device__ __forceinline__ void store4_edge(typename Storage<ST>::S* f, const Geom& g, int xb, int y, int z,
+                                            const typename Storage<ST>::S (&sv)[4]) {
+    using S = typename Storage<ST>::S;
+    if (xb + 3 < 0 || xb >= g.nx) return;
+    const bool ylo = y == 0, yhi = y == g.ny - 1;
+    const bool rare = (DIM == 3 && (z == 0 || z == g.nz - 1)) || (ylo && yhi) || xb < 0 || xb + 3 >= g.nx;
+    if (rare) {
+        store4_ghosted<DIM, ST>(f, g, xb, y, z, sv);
+        return;
+    }
+    S* p = f + g.at(xb, y, z);
+    const long long dy = ylo ? (long long)g.ny * g.py : (yhi ? -(long long)g.ny * g.py : 0);
+    stg4<ST>(p, sv);
+    if (dy != 0) stg4<ST>(p + dy, sv);
+    if (xb < g.gx || xb + 3 >= g.nx - g.gx) {
+        constexpr int OX = 16 / (int)sizeof(S);   // ghost block width (elements)
+        bool lo = false, hi = false;              // ghost images already written as vectors
+        if constexpr (OX >= 4) {
+            // FP32 / BF16: the lane's four nodes are one 16- or 8-byte piece of the block; the
+            // image at x -+ nx is vector-aligned only when nx is a multiple of 4
+            const bool al = (g.nx & 3) == 0;
+            if (al && xb + 3 < OX) {
+                stg4<ST>(p + g.nx, sv);
+                if (dy != 0) stg4<ST>(p + g.nx + dy, sv);
+                lo = true;
+            }
+            if (al && xb >= g.nx - OX) {
+                stg4<ST>(p - g.nx, sv);
+                if (dy != 0) stg4<ST>(p - g.nx + dy, sv);
+                hi = true;
+            }
+        } else {
+            // FP64: the block is two doubles, the first or last half of the lane
+            if (xb == 0 && (g.nx & 1) == 0) {
+                *reinterpret_cast<double2*>(p + g.nx) = make_double2(sv[0], sv[1]);
+                if (dy != 0) *reinterpret_cast<double2*>(p + g.nx + dy) = make_double2(sv[0], sv[1]);
+                lo = true;
+            }
+            if (xb + 4 == g.nx) {
+                *reinterpret_cast<double2*>(p + 2 - g.nx) = make_double2(sv[2], sv[3]);
+                if (dy != 0) *reinterpret_cast<double2*>(p + 2 - g.nx + dy) = make_double2(sv[2], sv[3]);
+                hi = true;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = xb + k;
+            const int dx = (!lo && x < g.gx) ? g.nx : ((!hi && x >= g.nx - g.gx) ? -g.nx : 0);
+            if (dx != 0) {
+                p[k + dx] = sv[k];
+                if (dy != 0) p[k + dx + dy] = sv[k];
+            }
+        }
+    }
+}
+
 // Work decomposition: an item is (128-column warp strip, H-row segment).  Every warp walks its
 // own sequence of items (item = global warp id, + total warps, ...) as one stream of input
 // rows; lane 0 keeps NSTAGE rows of that stream in flight through the warp's private ring, so
@@ -359,7 +424,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                     sv[k] = Tr::pack(acc[k4 + k][f], cf.ref[f], rnd);
                 }
                 if (interior) stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
-                else store4_ghosted<2, ST>(fo, g, xb + k4, yo, 0, sv);
+                else store4_edge<2, ST>(fo, g, xb + k4, yo, 0, sv);
             }
         }
     };

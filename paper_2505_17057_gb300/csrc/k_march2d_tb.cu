@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
             if (xb >= g.gx && xb + LN - 1 < g.nx - g.gx && yo > 0 && yo < g.ny - 1)
                 stg4<ST>(out + g.at(xb, yo, 0), sv);
             else
-                store4_ghosted<2, ST>(out, g, xb, yo, 0, sv);
+                store4_edge<2, ST>(out, g, xb, yo, 0, sv);
         }
     };
 

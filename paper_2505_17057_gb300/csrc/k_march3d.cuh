@@ -248,7 +248,7 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
                     }
                     S* fo = out + (size_t)f * g.fs;
                     if (interior) stg4<ST>(fo + g.at(xb, y, zo), sv);
-                    else store4_ghosted<3, ST>(fo, g, xb, y, zo, sv);
+                    else store4_edge<3, ST>(fo, g, xb, y, zo, sv);
                 }
             }
 #pragma unroll

@@ -39,7 +39,7 @@ Geom make_geom(const Resolved& r) {
     const int align = 16 / g.es;            // elements per 16 bytes
     g.ox = align;                            // interior column 0 on a 16-byte boundary
     g.gz = r.dim == 3 ? 1 : 0;
-    g.gx = 1;                                // raised by temporally blocked solvers
+    g.gx = g.ox;                             // every ghost column is kept current
     long long py = g.ox + g.nx + align;      // right ghost plus slack for vector/TMA tails
     py = (py + 2 * align - 1) / (2 * align) * (2 * align);  // 32-byte rows
     g.py = py;

@@ -55,7 +55,7 @@ __host__ __device__ constexpr int pde_nf(int pde, int lat) { return pde == PDE_N
 struct Geom {
     int dim, nx, ny, nz;
     int ox, gz;
-    int gx;                // depth of the x ghost columns kept up to date (1 .. ox)
+    int gx;                // depth of the x ghost columns kept up to date (= ox)
     long long py, pz, fs;  // row pitch, plane pitch, field stride (elements)
     int nf, es;
     __host__ __device__ long long at(int x, int y, int z) const {

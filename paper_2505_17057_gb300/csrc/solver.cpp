@@ -112,6 +112,30 @@ int solver_set_fields(Solver* s, int level, const void* const* fields, int where
     return MMFD_OK;
 }
 
+void solver_launch_args(Solver* s, LaunchArgs& a) {
+    a.g = s->g;
+    a.in0 = s->lev[s->cur];
+    a.in1 = s->nlev == 3 ? s->lev[s->prev()] : nullptr;
+    a.out = s->lev[s->next()];
+    a.coef = s->coef();
+    a.ex.seed = s->desc.seed;
+    a.ex.step = s->steps_done + 1;
+    a.ex.sr = (s->r.st == ST_BF16 && (s->desc.flags & MMFD_FLAG_STOCHASTIC_ROUND)) ? 1 : 0;
+    a.stream = s->stream;
+    a.variant = s->variant;
+    a.H = s->H;
+    a.err = s->d_flag;
+    a.maps = nullptr;
+    if (s->use_tma) {
+        const int nf = s->g.nf;
+        for (int f = 0; f < nf; ++f) {
+            s->launch_maps.m[f] = s->tmaps[s->cur][f];
+            if (s->nlev == 3) s->launch_maps.m[nf + f] = s->tmaps[s->prev()][f];
+        }
+        a.maps = &s->launch_maps;
+    }
+}
+
 int solver_step(Solver* s, long long nsteps) {
     if (!s->fields_set) return set_error(MMFD_ERR_STATE, "set the fields before stepping");
     long long done = 0;
@@ -119,29 +143,9 @@ int solver_step(Solver* s, long long nsteps) {
         const long long left = nsteps - done;
         const bool blocked = s->fn_block && s->depth > 1 && left >= s->depth;
         LaunchArgs a;
-        a.g = s->g;
-        a.in0 = s->lev[s->cur];
-        a.in1 = s->nlev == 3 ? s->lev[s->prev()] : nullptr;
-        a.coef = s->coef();
-        a.ex.seed = s->desc.seed;
-        a.ex.step = s->steps_done + 1;
-        a.ex.sr = (s->r.st == ST_BF16 && (s->desc.flags & MMFD_FLAG_STOCHASTIC_ROUND)) ? 1 : 0;
-        a.stream = s->stream;
-        a.variant = s->variant;
-        a.H = s->H;
-        a.err = s->d_flag;
-        a.maps = nullptr;
-        if (s->use_tma) {
-            const int nf = s->g.nf;
-            for (int f = 0; f < nf; ++f) {
-                s->launch_maps.m[f] = s->tmaps[s->cur][f];
-                if (s->nlev == 3) s->launch_maps.m[nf + f] = s->tmaps[s->prev()][f];
-            }
-            a.maps = &s->launch_maps;
-        }
+        solver_launch_args(s, a);
         if (blocked) {
             // the blocked kernel (two-level solvers) writes level t + depth dt into next()
-            a.out = s->lev[s->next()];
             a.ex.step = s->steps_done + s->depth;
             cudaError_t e = s->fn_block(a);
             if (e != cudaSuccess) return cuda_fail(e, "blocked step kernel");
@@ -149,7 +153,6 @@ int solver_step(Solver* s, long long nsteps) {
             s->steps_done += s->depth;
             done += s->depth;
         } else {
-            a.out = s->lev[s->next()];
             cudaError_t e = s->fn(a);
             if (e != cudaSuccess) return cuda_fail(e, "step kernel");
             s->cur = s->next();
@@ -239,9 +242,23 @@ int solver_error_norms(Solver* s, int field, const void* ref, int where, int dty
     return MMFD_OK;
 }
 
+void solver_use_depth(Solver* s, int depth) {
+    LaunchFn fb = depth >= 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth) : nullptr;
+    if (fb) {
+        s->fn_block = fb;
+        s->depth = depth;
+        s->kernel_name = "k_march2d_tb";
+    } else {
+        s->fn_block = nullptr;
+        s->depth = 1;
+        s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
+    }
+}
+
 int solver_pick_kernels(Solver* s) {
     s->fn_block = nullptr;
     s->depth = 1;
+    s->max_depth = 1;
     s->variant = 0;
     s->use_tma = false;
     s->fn = nullptr;
@@ -266,18 +283,18 @@ int solver_pick_kernels(Solver* s) {
             s->use_tma = true;
             s->kernel_name = "k_march2d";
             s->H = 0;  // chosen by the launcher from the kernel's occupancy
-            // temporal blocking: 0 asks for the deepest blocking the storage allows
-            const int maxd = march2d_tb_max_depth(s->r.st);
-            int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
-            if (want > maxd) want = maxd;
-            // (the blocked kernel stages two rows per box, as the solver's maps for these PDEs do)
-            if (want >= 2 && s->g.ny >= 2 * want && march2d_rows_per_stage(s->r.pde) == 2) {
-                s->fn_block = find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, want);
-                if (s->fn_block) {
-                    s->depth = want;
-                    s->g.gx = want;   // every writer keeps the x ghost columns to this depth
-                    s->kernel_name = "k_march2d_tb";
-                }
+            // temporal blocking: 0 asks for the deepest blocking the storage allows (the
+            // autotuner may then pick a shallower one); the x ghost columns, kept current to
+            // their full depth ox by every writer, bound the depth.
+            // (The blocked kernel stages two rows per box, as the solver's maps for these PDEs do.)
+            int maxd = march2d_tb_max_depth(s->r.st);
+            while (maxd >= 2 && s->g.ny < 2 * maxd) --maxd;
+            if (s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
+                find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
+                s->max_depth = maxd;
+                int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
+                if (want > maxd) want = maxd;
+                solver_use_depth(s, want);
             }
             return MMFD_OK;
         }

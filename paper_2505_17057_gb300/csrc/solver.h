@@ -28,6 +28,7 @@ struct Solver {
     double* d_red = nullptr;                     // reduction partials and results
     long long steps_done = 0;
     int depth = 1;                               // steps fused per launch
+    int max_depth = 1;                           // deepest blocking this solver's ghosts allow
     LaunchFn fn = nullptr;                       // single-step kernel
     LaunchFn fn_block = nullptr;                 // temporally blocked kernel (depth > 1)
     int variant = 0;
@@ -61,5 +62,11 @@ int solver_error_norms(Solver* s, int field, const void* ref, int where, int dty
 int solver_pick_kernels(Solver* s);
 // Read (and clear) the device error flag; MMFD_ERR_TIMEOUT if a kernel gave up a wait.
 int solver_check_flag(Solver* s);
+// Launch arguments of the next step: inputs the current level(s), output the spare buffer.
+void solver_launch_args(Solver* s, LaunchArgs& a);
+// Switch to temporal depth `depth` (1 = unblocked; must not exceed max_depth).
+void solver_use_depth(Solver* s, int depth);
+// Time the candidate configurations and keep the fastest (mmfd_autotune).
+int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out);
 
 }  // namespace mmfd

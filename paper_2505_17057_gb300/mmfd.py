@@ -77,6 +77,11 @@ class mmfd_info_t(C.Structure):
     ]
 
 
+class mmfd_tune_info(C.Structure):
+    _fields_ = [("temporal_depth", C.c_int), ("rows_per_item", C.c_int), ("ms_per_step", C.c_double),
+                ("candidates", C.c_int), ("from_cache", C.c_int)]
+
+
 class mmfd_server_desc(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("steps_per_tick", C.c_int),
                 ("use_graphs", C.c_int), ("stream", C.c_void_p)]
@@ -107,6 +112,7 @@ SIGNATURES = {
     "mmfd_error_norms": (C.c_int, [_VP, C.c_int, _VP, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mmfd_reduce_static": (C.c_int, [_VP, C.c_int, C.c_longlong, C.c_int, _VP, _VP]),
     "mmfd_get_info": (C.c_int, [_VP, C.POINTER(mmfd_info_t)]),
+    "mmfd_autotune": (C.c_int, [_VP, C.c_char_p, C.POINTER(mmfd_tune_info)]),
     "mmfd_set_stream": (C.c_int, [_VP, _VP]),
     "mmfd_destroy": (C.c_int, [_VP]),
     "mmfd_solve_three_level": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -231,6 +237,13 @@ def mmfd_reduce_static(field_ptr: int, dtype: int, count: int, what: int, out_pt
 def mmfd_get_info(h: int) -> mmfd_info_t:
     info = mmfd_info_t()
     check(lib.mmfd_get_info(h, C.byref(info)), "mmfd_get_info")
+    return info
+
+
+def mmfd_autotune(h: int, cache_path: Optional[str] = None) -> mmfd_tune_info:
+    info = mmfd_tune_info()
+    path = cache_path.encode() if cache_path else None
+    check(lib.mmfd_autotune(h, path, C.byref(info)), "mmfd_autotune")
     return info
 
 
@@ -418,6 +431,9 @@ class Solver:
 
     def get_info(self) -> mmfd_info_t:
         return mmfd_get_info(self.h)
+
+    def autotune(self, cache_path: Optional[str] = None) -> mmfd_tune_info:
+        return mmfd_autotune(self.h, cache_path)
 
 
 def info_dict(info: mmfd_info_t) -> dict:

@@ -103,9 +103,14 @@ def test_depth_selection(mm):
     s = mm.Solver(mm.make_desc(**kw64, temporal_depth=0))
     assert s.get_info().temporal_depth == 2
     s.close()
+    # the depth is clamped to what the rows allow (ny >= 2 T)
+    kw7, _ = G.case("D2Q9", "LCDE", 2, [300, 7], "fp32")
+    s = mm.Solver(mm.make_desc(**kw7, temporal_depth=4))
+    assert s.get_info().temporal_depth == 3
+    s.close()
     # unsupported: three-level, NSE, too few rows, narrow grids -> unblocked
     for args, depth in [(("D2Q9", "LCDE", 3, [300, 70]), 4), (("D2Q9", "NSE", 2, [300, 70]), 4),
-                        (("D2Q9", "LCDE", 2, [300, 7]), 4), (("D2Q9", "LCDE", 2, [100, 70]), 4)]:
+                        (("D2Q9", "LCDE", 2, [300, 3]), 4), (("D2Q9", "LCDE", 2, [100, 70]), 4)]:
         kwu, _ = G.case(*args, "fp32")
         s = mm.Solver(mm.make_desc(**kwu, temporal_depth=depth))
         assert s.get_info().temporal_depth == 1, args

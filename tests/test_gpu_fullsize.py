@@ -1,0 +1,96 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times (same
+descriptors, same kernels, the launcher's own tile choice): one step of the full grid on the
+GPU, compared with the FP64 oracle on sampled nodes -- random interior nodes plus every
+corner and samples of every edge row/column (and face) -- and, for the temporally blocked
+path, with the unblocked GPU path on the whole grid (a property that holds at any size).
+
+Tolerance: FP32 storage, 1e-5 relative to the field's max |value| (one step from the
+FP32-rounded initial state, which is what the oracle is given).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from oracle import params as P
+from paper_2505_17057_gb300 import configs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_17057_gb300 import mmfd
+    return mmfd
+
+
+def oracle_problem(kw):
+    lat, n, dt, dx = kw["lattice"], kw["n"], kw["dt"], kw["dx"]
+    if kw["pde"] == "NSE":
+        return P.problem_nse(lat, 2, n, dt, dx, kw["a"], kw["abar"])
+    a = P.two_level_from_a0(kw["targets"][0])
+    return P.problem_lcde(lat, 2, n, dt, dx, np.asarray(kw["K"], dtype=float), kw["u"], a)
+
+
+def sample_nodes(shape, rng, count=20000):
+    """Flat indices (C order over `shape`, x fastest) of random nodes, all corners and
+    samples of every boundary line / face."""
+    shape = tuple(shape)
+    idx = [rng.integers(0, int(np.prod(shape)), count)]
+    dims = len(shape)
+    for corner in np.ndindex(*([2] * dims)):
+        c = tuple((s - 1) * b for s, b in zip(shape, corner))
+        idx.append(np.array([np.ravel_multi_index(c, shape)]))
+    for ax in range(dims):
+        for side in (0, shape[ax] - 1):
+            coords = [rng.integers(0, s, 500) for s in shape]
+            coords[ax] = np.full(500, side)
+            idx.append(np.ravel_multi_index(coords, shape))
+    return np.unique(np.concatenate(idx))
+
+
+def solve_one(mm, kw, fields, steps, depth):
+    s = mm.Solver(mm.make_desc(**kw, temporal_depth=depth))
+    try:
+        info = s.get_info()
+        s.set_fields(fields)
+        stored = s.fields(0)
+        s.step(steps)
+        out = s.fields(0)
+    finally:
+        s.close()
+    return info, stored, out
+
+
+FULL = [("tgv2d", configs.tgv2d_4096, 4096, "k_march2d"),
+        ("lcde2d", configs.lcde2d_8192, 8192, "k_march2d"),
+        ("cde3d", configs.cde3d_512, 512, "k_march3d"),
+        ("nse3d", configs.nse3d_512, 512, "k_march3d")]
+
+
+@pytest.mark.parametrize("name,maker,n,kernel", FULL, ids=[f[0] for f in FULL])
+def test_full_size_one_step_matches_oracle_on_samples(mm, name, maker, n, kernel):
+    kw, fields, _ = maker(n=n, storage="fp32")
+    info, stored, out = solve_one(mm, kw, fields, 1, 1)
+    assert info.kernel.decode() == kernel
+    prob = oracle_problem(kw)
+    rng = np.random.default_rng(1234)
+    nodes = sample_nodes(stored[0].shape, rng)
+    ref = orc.step_nodes(prob, stored, None, nodes)
+    for f in range(len(out)):
+        got = out[f].reshape(-1)[nodes]
+        scale = max(np.abs(ref[:, f]).max(), np.abs(out[f]).max())
+        err = np.abs(got - ref[:, f]).max() / scale
+        assert err < 1e-5, (name, f, err)
+    assert all(np.isfinite(o).all() for o in out)
+
+
+def test_full_size_blocked_matches_unblocked(mm):
+    kw, fields, _ = configs.lcde2d_8192(n=8192, storage="fp32")
+    info, _, blocked = solve_one(mm, kw, fields, 4, 4)
+    assert info.kernel.decode() == "k_march2d_tb" and info.temporal_depth == 4
+    _, _, plain = solve_one(mm, kw, fields, 4, 1)
+    err = np.abs(blocked[0] - plain[0]).max() / np.abs(plain[0]).max()
+    assert err < 1e-6, err
