@@ -59,10 +59,14 @@ __device__ __forceinline__ void stg4(void* p, const typename Storage<ST>::S s[4]
 // y = 0 / ny - 1 and, in 3D, the ghost plane of z = 0 / nz - 1 (with all combinations).  Nodes
 // outside [0, nx) are skipped.  Straight-line predicated stores, no local arrays: the warps that
 // own edge strips and rows must not fall behind the others.
+// (The four values come as scalars: an array passed by address to an out-of-line function would
+// have to live in local memory in the caller, on every row, for every lane.)
 template <int DIM, int ST>
 __device__ __noinline__ void store4_ghosted(typename Storage<ST>::S* f, const Geom g, int xb, int y, int z,
-                                               const typename Storage<ST>::S (&sv)[4]) {
+                                            typename Storage<ST>::S s0, typename Storage<ST>::S s1,
+                                            typename Storage<ST>::S s2, typename Storage<ST>::S s3) {
     using S = typename Storage<ST>::S;
+    const S sv[4] = {s0, s1, s2, s3};
     const bool full = xb >= 0 && xb + 3 < g.nx;
     const bool xedge = xb < g.gx || xb + 3 >= g.nx - g.gx;
     auto put_row = [&](int yy, int zz) {
@@ -98,70 +102,73 @@ __device__ __noinline__ void store4_ghosted(typename Storage<ST>::S* f, const Ge
     }
 }
 
-// The edge store of the marching kernels.  The common edge cases are inline and cheap -- a row
-// on a y edge adds one vector store into the ghost row; a lane whose nodes lie within g.gx of an
-// x edge writes their ghost images as whole vectors, filling the 16-byte ghost block at that
-// edge completely -- because a single lane on a slow path holds back its whole warp on every
-// row it stores, and because ghost blocks left partly written made the next step's loads of
-// the edge strips slow (the warps owning them then finished long after the rest).  Rare cases
-// (z edge planes, ny == 1, vectors that straddle x = nx) take store4_ghosted.  Lanes with no
-// node in [0, nx) store nothing.
+// The output store of the marching kernels.  A lane writes its four nodes xb .. xb+3 (xb a
+// multiple of 4) and their periodic ghost images -- the ghost row of y = 0 / ny - 1 and the
+// whole-vector x ghost blocks -- with predicated stores only, all 32 lanes following the same
+// control flow: a lane that branched off alone onto an edge path made its whole warp run about
+// three times slower on every row (measured per warp with %globaltimer), and the warps owning
+// the edge strips then set the length of the launch.  What depends only on the lane's columns
+// is worked out once per work item (init); the cases vectors cannot cover (z edge planes,
+// ny == 1, vectors straddling x = nx, x ghosts when nx is not a multiple of 4) take
+// store4_ghosted under a warp-uniform branch.
 template <int DIM, int ST>
-__device__ __forceinline__ void store4_edge(typename Storage<ST>::S* f, const Geom& g, int xb, int y, int z,
-                                            const typename Storage<ST>::S (&sv)[4]) {
+struct EdgeStore {
     using S = typename Storage<ST>::S;
-    if (xb + 3 < 0 || xb >= g.nx) return;
-    const bool ylo = y == 0, yhi = y == g.ny - 1;
-    const bool rare = (DIM == 3 && (z == 0 || z == g.nz - 1)) || (ylo && yhi) || xb < 0 || xb + 3 >= g.nx;
-    if (rare) {
-        store4_ghosted<DIM, ST>(f, g, xb, y, z, sv);
-        return;
-    }
-    S* p = f + g.at(xb, y, z);
-    const long long dy = ylo ? (long long)g.ny * g.py : (yhi ? -(long long)g.ny * g.py : 0);
-    stg4<ST>(p, sv);
-    if (dy != 0) stg4<ST>(p + dy, sv);
-    if (xb < g.gx || xb + 3 >= g.nx - g.gx) {
-        constexpr int OX = 16 / (int)sizeof(S);   // ghost block width (elements)
-        bool lo = false, hi = false;              // ghost images already written as vectors
+    static constexpr int OX = 16 / (int)sizeof(S);   // ghost block width (elements)
+    bool in = false;      // the lane's four nodes are output nodes inside [0, nx)
+    bool lo = false;      // writes the x ghost block at x + nx as a vector
+    bool hi = false;      // writes the x ghost block at x - nx as a vector
+    bool xrare = false;   // needs the general path (partial vector, scalar x ghosts)
+    bool wrare = false;   // some lane of the warp does (warp-uniform)
+
+    // all 32 lanes, once per item
+    __device__ __forceinline__ void init(const Geom& g, int xb, bool valid) {
+        in = valid && xb >= 0 && xb + 3 < g.nx;
+        const bool part = valid && !in && xb < g.nx && xb + 3 >= 0;
+        bool xdone;
         if constexpr (OX >= 4) {
-            // FP32 / BF16: the lane's four nodes are one 16- or 8-byte piece of the block; the
-            // image at x -+ nx is vector-aligned only when nx is a multiple of 4
+            // FP32 / BF16: the lane's nodes are one 16- or 8-byte piece of the block; the image at
+            // x -+ nx is vector-aligned only when nx is a multiple of 4
             const bool al = (g.nx & 3) == 0;
-            if (al && xb + 3 < OX) {
-                stg4<ST>(p + g.nx, sv);
-                if (dy != 0) stg4<ST>(p + g.nx + dy, sv);
-                lo = true;
-            }
-            if (al && xb >= g.nx - OX) {
-                stg4<ST>(p - g.nx, sv);
-                if (dy != 0) stg4<ST>(p - g.nx + dy, sv);
-                hi = true;
-            }
+            lo = in && al && xb + 3 < OX;
+            hi = in && al && xb >= g.nx - OX;
+            xdone = !(in && (xb < g.gx || xb + 3 >= g.nx - g.gx)) || lo || hi;
         } else {
             // FP64: the block is two doubles, the first or last half of the lane
-            if (xb == 0 && (g.nx & 1) == 0) {
-                *reinterpret_cast<double2*>(p + g.nx) = make_double2(sv[0], sv[1]);
-                if (dy != 0) *reinterpret_cast<double2*>(p + g.nx + dy) = make_double2(sv[0], sv[1]);
-                lo = true;
-            }
-            if (xb + 4 == g.nx) {
-                *reinterpret_cast<double2*>(p + 2 - g.nx) = make_double2(sv[2], sv[3]);
-                if (dy != 0) *reinterpret_cast<double2*>(p + 2 - g.nx + dy) = make_double2(sv[2], sv[3]);
-                hi = true;
+            lo = in && xb == 0 && (g.nx & 1) == 0;
+            hi = in && xb + 4 == g.nx;
+            xdone = (!(in && xb < g.gx) || lo) && (!(in && xb + 3 >= g.nx - g.gx) || hi);
+        }
+        xrare = part || !xdone;
+        wrare = __any_sync(0xffffffffu, xrare);
+    }
+
+    // all 32 lanes (warp-uniform y, z)
+    __device__ __forceinline__ void put(S* f, const Geom& g, int xb, int y, int z, const S (&sv)[4]) const {
+        S* p = f + g.at(xb, y, z);
+        if (in) stg4<ST>(p, sv);
+        const bool ydup = g.ny > 1 && (y == 0 || y == g.ny - 1);
+        if (ydup || lo || hi) {
+            const long long dy = y == 0 ? (long long)g.ny * g.py : -(long long)g.ny * g.py;
+            if (in && ydup) stg4<ST>(p + dy, sv);
+            if constexpr (OX >= 4) {
+                if (lo) stg4<ST>(p + g.nx, sv);
+                if (lo && ydup) stg4<ST>(p + g.nx + dy, sv);
+                if (hi) stg4<ST>(p - g.nx, sv);
+                if (hi && ydup) stg4<ST>(p - g.nx + dy, sv);
+            } else {
+                if (lo) *reinterpret_cast<double2*>(p + g.nx) = make_double2(sv[0], sv[1]);
+                if (lo && ydup) *reinterpret_cast<double2*>(p + g.nx + dy) = make_double2(sv[0], sv[1]);
+                if (hi) *reinterpret_cast<double2*>(p + 2 - g.nx) = make_double2(sv[2], sv[3]);
+                if (hi && ydup) *reinterpret_cast<double2*>(p + 2 - g.nx + dy) = make_double2(sv[2], sv[3]);
             }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int x = xb + k;
-            const int dx = (!lo && x < g.gx) ? g.nx : ((!hi && x >= g.nx - g.gx) ? -g.nx : 0);
-            if (dx != 0) {
-                p[k + dx] = sv[k];
-                if (dy != 0) p[k + dx + dy] = sv[k];
-            }
+        const bool plane_rare = g.ny == 1 || (DIM == 3 && (z == 0 || z == g.nz - 1));
+        if (wrare || plane_rare) {
+            if (xrare || (plane_rare && (in || xrare))) store4_ghosted<DIM, ST>(f, g, xb, y, z, sv[0], sv[1], sv[2], sv[3]);
         }
     }
-}
+};
 
 // Work decomposition: an item is (128-column warp strip, H-row segment).  Every warp walks its
 // own sequence of items (item = global warp id, + total warps, ...) as one stream of input
@@ -409,9 +416,9 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     };
 
     // store the completed output row yo from acc
+    EdgeStore<2, ST> es;
     auto store_row = [&](int yo, int xb, const T (&acc)[LN][NF]) {
         const long long nb = (long long)yo * g.nx;
-        const bool interior = xb >= g.gx && xb + LN - 1 < g.nx - g.gx && yo > 0 && yo < g.ny - 1;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             S* fo = out + (size_t)f * g.fs;
@@ -423,8 +430,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                     const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
                     sv[k] = Tr::pack(acc[k4 + k][f], cf.ref[f], rnd);
                 }
-                if (interior) stg4<ST>(fo + g.at(xb + k4, yo, 0), sv);
-                else store4_edge<2, ST>(fo, g, xb + k4, yo, 0, sv);
+                es.put(fo, g, xb + k4, yo, 0, sv);
             }
         }
     };
@@ -436,6 +442,8 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
         const int hrows = min(H, g.ny - y0);                       // output rows of the item
         const int nrows = (hrows + 2 + RPS - 1) / RPS * RPS;       // staged input rows
         const int xb = x0 + lane * LN;
+        static_assert(LN == 4, "the edge store covers four nodes per lane");
+        es.init(g, xb, true);
 #pragma unroll
         for (int k = 0; k < LN; ++k)
 #pragma unroll
@@ -457,12 +465,11 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                 fence_proxy_async_smem();
                 issue_next();
             }
-            // input row i (y0 - 1 + i) completes output row y0 + i - 2
-            if (xb < g.nx) {
-                if (i >= 2) store_row(y0 + i - 2, xb, acc0);
-                if constexpr (RPS == 2) {
-                    if (i >= 1 && i - 1 < hrows) store_row(y0 + i - 1, xb, acc1);
-                }
+            // input row i (y0 - 1 + i) completes output row y0 + i - 2 (all lanes take part in
+            // the store; lanes beyond nx write nothing)
+            if (i >= 2) store_row(y0 + i - 2, xb, acc0);
+            if constexpr (RPS == 2) {
+                if (i >= 1 && i - 1 < hrows) store_row(y0 + i - 1, xb, acc1);
             }
 #pragma unroll
             for (int k = 0; k < LN; ++k)

@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
 
     // input row i of the item at (xb, y0): push it through the TT levels and store the completed
     // level-TT row y0 - 2 TT + i if it is one of the item's output rows
+    EdgeStore<2, ST> es;
     auto cascade = [&](T (&raw)[LN + 2], int i, int xb, int y0, int hrows) {
 #pragma unroll
         for (int t = 0; t < TT; ++t) {
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
             }
         }
         const int yo = y0 - 2 * TT + i;
-        if (i >= 2 * TT && i < hrows + 2 * TT && store_lane) {
+        if (i >= 2 * TT && i < hrows + 2 * TT) {   // warp-uniform; lanes 0 and 31 hold no output
             const long long nb = (long long)yo * g.nx;
             S sv[4];
 #pragma unroll
@@ -195,10 +196,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
                 const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k, 0) : 0u;
                 sv[k] = Tr::pack(raw[1 + k], cf.ref[0], rnd);
             }
-            if (xb >= g.gx && xb + LN - 1 < g.nx - g.gx && yo > 0 && yo < g.ny - 1)
-                stg4<ST>(out + g.at(xb, yo, 0), sv);
-            else
-                store4_edge<2, ST>(out, g, xb, yo, 0, sv);
+            es.put(out, g, xb, yo, 0, sv);
         }
     };
 
@@ -221,6 +219,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
         const int hrows = min(H, g.ny - y0);
         const int nrows = (hrows + 2 * TT + RPS - 1) / RPS * RPS;
         const int xb = x0 + lane * LN;
+        es.init(g, xb, store_lane);
 #pragma unroll
         for (int t = 0; t < TT; ++t)
 #pragma unroll

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
 
     // -------------------------------------------------------------------- consumer warps
     T accP[LN][NF], accC[LN][NF], accN[LN][NF];
+    EdgeStore<3, ST> es;
     S* out = static_cast<S*>(outv);
     long long k = 0;
     bool failed = false;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
         const int z0 = (item / (xs * ys)) * H;
         const int np = item_planes(item);
         const int xb = x0 + lane * LN;
+        es.init(g, xb, true);
         const int y = y0 + warp;
 #pragma unroll
         for (int n = 0; n < LN; ++n)
@@ -233,11 +235,9 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             // plane z0 - 1 + i - 1 is complete
-            if (i >= 2 && xb < g.nx && y < g.ny) {
+            if (i >= 2 && y < g.ny) {
                 const int zo = z0 + i - 2;
                 const long long nb = ((long long)zo * g.ny + y) * g.nx;
-                const bool interior = xb >= g.gx && xb + LN - 1 < g.nx - g.gx && y > 0 && y < g.ny - 1 && zo > 0 &&
-                                      zo < g.nz - 1;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     S sv[4];
@@ -247,8 +247,7 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
                         sv[n] = Tr::pack(accP[n][f], cf.ref[f], rnd);
                     }
                     S* fo = out + (size_t)f * g.fs;
-                    if (interior) stg4<ST>(fo + g.at(xb, y, zo), sv);
-                    else store4_edge<3, ST>(fo, g, xb, y, zo, sv);
+                    es.put(fo, g, xb, y, zo, sv);
                 }
             }
 #pragma unroll

@@ -86,32 +86,35 @@ template <int LAT, typename T>
 struct Basis<LAT, PDE_NSE, T> {
     static constexpr int D = lat_dim(LAT);
     T rho, u[3];
+    T uu[6];   // u_a u_b: (xx, yy, zz, xy, xz, yz), formed once per node and shared by all pairs
     __device__ __forceinline__ void init(const T* f, const Coef<T>&) {
         rho = f[0];
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = f[1 + a];
+#pragma unroll
+        for (int a = 0; a < D; ++a) uu[a] = u[a] * u[a];
+        uu[3] = u[0] * u[1];
+        if constexpr (D == 3) {
+            uu[4] = u[0] * u[2];
+            uu[5] = u[1] * u[2];
+        }
     }
     __device__ __forceinline__ T A() const { return rho; }
-    __device__ __forceinline__ T cc(int k) const {
-        // (xx, yy, zz, xy, xz, yz)
-        return k == 0 ? u[0] * u[0] : k == 1 ? u[1] * u[1] : k == 2 ? u[2] * u[2]
-             : k == 3 ? u[0] * u[1] : k == 4 ? u[0] * u[2] : u[1] * u[2];
-    }
     __device__ __forceinline__ T rest(const Coef<T>& c) const {
         T r = c.rA * rho;
 #pragma unroll
-        for (int a = 0; a < D; ++a) r += c.rC[a] * u[a] * u[a];
+        for (int a = 0; a < D; ++a) r += c.rC[a] * uu[a];
         return r;
     }
     template <int P>
     __device__ __forceinline__ void eo(const Coef<T>& c, T& E, T& O) const {
         T e = c.eA[P] * rho;
 #pragma unroll
-        for (int a = 0; a < D; ++a) e += c.eC[P][a] * u[a] * u[a];
-        if (pair_e(LAT, P, 0) * pair_e(LAT, P, 1) != 0) e += c.eC[P][3] * u[0] * u[1];
+        for (int a = 0; a < D; ++a) e += c.eC[P][a] * uu[a];
+        if (pair_e(LAT, P, 0) * pair_e(LAT, P, 1) != 0) e += c.eC[P][3] * uu[3];
         if (D == 3) {
-            if (pair_e(LAT, P, 0) * pair_e(LAT, P, 2) != 0) e += c.eC[P][4] * u[0] * u[2];
-            if (pair_e(LAT, P, 1) * pair_e(LAT, P, 2) != 0) e += c.eC[P][5] * u[1] * u[2];
+            if (pair_e(LAT, P, 0) * pair_e(LAT, P, 2) != 0) e += c.eC[P][4] * uu[4];
+            if (pair_e(LAT, P, 1) * pair_e(LAT, P, 2) != 0) e += c.eC[P][5] * uu[5];
         }
         T o = T(0);
 #pragma unroll

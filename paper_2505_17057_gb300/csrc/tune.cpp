@@ -2,6 +2,7 @@
 // step kernel on its own grid and keeps the fastest; optional text cache of earlier choices.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <fstream>
 #include <sstream>
@@ -99,7 +100,17 @@ int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out) {
     double best = -1.0;
     int best_d = keep_depth, best_h = keep_h;
     int rc = MMFD_OK;
-    constexpr int kReps = 3;
+    // one sample = `reps` back-to-back launches; reps is sized from a probe so that a sample
+    // lasts about a millisecond, and the median of three samples is kept (single short samples
+    // picked different heights from run to run)
+    auto sample = [&](LaunchFn fn, const LaunchArgs& a, int reps, float* ms) -> cudaError_t {
+        cudaError_t e2 = cudaEventRecord(e0, s->stream);
+        for (int r = 0; r < reps && e2 == cudaSuccess; ++r) e2 = fn(a);
+        if (e2 == cudaSuccess) e2 = cudaEventRecord(e1, s->stream);
+        if (e2 == cudaSuccess) e2 = cudaEventSynchronize(e1);
+        if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(ms, e0, e1);
+        return e2;
+    };
     for (int d : depths) {
         solver_use_depth(s, d);
         LaunchFn fn = d >= 2 ? s->fn_block : s->fn;
@@ -108,19 +119,21 @@ int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out) {
             LaunchArgs a;
             solver_launch_args(s, a);   // reads the current level(s), writes the spare buffer only
             a.H = h;
-            e = fn(a);                  // warm-up (first launch also sets the kernel's attributes)
-            if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);
-            for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = fn(a);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            float probe = 0.f;
+            e = fn(a);                  // warm-up (the first launch also sets the kernel's attributes)
+            if (e == cudaSuccess) e = fn(a);
+            if (e == cudaSuccess) e = sample(fn, a, 1, &probe);
+            int reps = probe > 0.f ? (int)(1.0f / probe) + 1 : 1;
+            if (reps > 50) reps = 50;
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = sample(fn, a, reps, &t[k]);
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "autotune trial launch");
                 break;
             }
             ++info.candidates;
-            const double per_step = (double)ms / (kReps * d);
+            const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+            const double per_step = (double)med / ((double)reps * d);
             if (best < 0 || per_step < best) {
                 best = per_step;
                 best_d = d;
