@@ -56,8 +56,11 @@ struct Req {
     double t_submit = 0, t_admit = 0, t_finish = 0;
     int status = MMFD_OK;
     int cls = 0;
-    // large 2D requests run their own TMA march launches instead of joining a batched launch
+    // large requests run their own TMA march launches instead of joining a batched launch;
+    // two-level 2D ones advance solo_depth steps per launch with the blocked kernel
     LaunchFn solo = nullptr;
+    LaunchFn solo_tb = nullptr;
+    int solo_depth = 1;
     CUtensorMap tmaps[3][4];
 };
 
@@ -103,6 +106,13 @@ struct Server {
     // graph cache: composition key -> executable graph
     std::map<std::string, cudaGraphExec_t> graphs;
     std::deque<std::string> graph_lru;
+    // side streams: a tick forks its solo requests across them so that their launches overlap
+    // on the GPU (each request stays on one stream within the tick; the join at the end of a
+    // tick orders it before the next tick's fork)
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kSide] = {};
 };
 
 namespace {
@@ -180,6 +190,16 @@ int admit(Server* s, Req* q) {
                 ok = encode_field_map(&q->tmaps[b][f], base, q->r->st, q->g, boxw, boxh, 1) == 0;
             }
         if (ok) q->solo = fn;
+        // temporal blocking for two-level 2D solos (the blocked kernel reads the same 2-row maps)
+        if (ok && q->g.dim == 2 && nl == 2 && march2d_rows_per_stage(q->r->pde) == 2) {
+            int depth = march2d_tb_max_depth(q->r->st);
+            const int S = s->d.steps_per_tick > 0 ? s->d.steps_per_tick : 1;
+            while (depth >= 2 && (q->g.ny < 2 * depth || depth > S)) --depth;
+            if (depth >= 2) {
+                q->solo_tb = find_march2d_tb(q->r->lat, q->r->pde, 2, q->r->st, depth);
+                q->solo_depth = q->solo_tb ? depth : 1;
+            }
+        }
     }
     q->cur = 0;
     q->state = RQ_ACTIVE;
@@ -295,9 +315,10 @@ int launch_tick(Server* s) {
         key += "solo:" + std::to_string(q->ticket) + ":" + std::to_string(q->cur) + ":" + std::to_string(adv) + ";";
     }
     if (launches.empty() && solos.empty()) return MMFD_OK;
-    auto solo_step = [&](Req* q, int j) -> cudaError_t {
+    // one solo launch of request q: reads buffer c (and its predecessor for three-level), writes
+    // the next buffer, advancing `steps` time levels from step index step0
+    auto solo_launch = [&](Req* q, LaunchFn fn, int c, long long step0, int steps, cudaStream_t st) -> cudaError_t {
         const int nl = q->nlev;
-        const int c = (q->cur + j) % nl;
         const int prev = nl == 3 ? (c + 2) % 3 : c;
         const int next = nl == 2 ? 1 - c : (c + 1) % 3;
         TmapSet maps;
@@ -312,16 +333,41 @@ int launch_tick(Server* s) {
         a.out = q->lev[next];
         a.coef = q->r->st == ST_F64 ? static_cast<const void*>(&q->r->cd) : static_cast<const void*>(&q->r->cf);
         a.ex.seed = q->desc.seed;
-        a.ex.step = q->launched + j + 1;
+        a.ex.step = step0 + steps;
         a.ex.sr = (q->r->st == ST_BF16 && (q->desc.flags & MMFD_FLAG_STOCHASTIC_ROUND)) ? 1 : 0;
-        a.stream = s->stream;
+        a.stream = st;
         a.variant = 0;
         a.maps = &maps;
         a.H = 0;
         a.err = s->d_flag;
-        return q->solo(a);
+        return fn(a);
+    };
+    // the tick's launches of solo request q: blocked launches while a full block of steps is
+    // left, then single steps; returns the buffer index after them through *cur_after
+    auto solo_tick = [&](Req* q, cudaStream_t st, int* cur_after) -> cudaError_t {
+        const long long left = q->nsteps - q->launched;
+        const long long adv = left < S ? left : S;
+        int c = q->cur;
+        long long done = 0;
+        while (done < adv) {
+            const bool blocked = q->solo_tb && adv - done >= q->solo_depth;
+            const int steps = blocked ? q->solo_depth : 1;
+            cudaError_t e = solo_launch(q, blocked ? q->solo_tb : q->solo, c, q->launched + done, steps, st);
+            if (e != cudaSuccess) return e;
+            s->st.launches++;
+            c = q->nlev == 2 ? 1 - c : (c + 1) % 3;
+            done += steps;
+        }
+        *cur_after = c;
+        return cudaSuccess;
     };
     auto enqueue = [&]() -> cudaError_t {
+        const int nside = solos.empty() ? 0 : (int)std::min<size_t>(solos.size(), Server::kSide);
+        if (nside > 0) {
+            cudaError_t e = cudaEventRecord(s->fork_ev, s->stream);
+            for (int k = 0; k < nside && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s->side[k], s->fork_ev, 0);
+            if (e != cudaSuccess) return e;
+        }
         for (int j = 0; j < S; ++j) {
             for (const Launch& L : launches) {
                 long long grid = L.total < (long long)s->sms * 8 ? L.total : (long long)s->sms * 8;
@@ -329,12 +375,16 @@ int launch_tick(Server* s) {
                 if (e != cudaSuccess) return e;
                 s->st.launches++;
             }
-            for (Req* q : solos) {
-                if (j >= q->nsteps - q->launched) continue;
-                cudaError_t e = solo_step(q, j);
-                if (e != cudaSuccess) return e;
-                s->st.launches++;
-            }
+        }
+        for (size_t i = 0; i < solos.size(); ++i) {
+            int cur_after = 0;
+            cudaError_t e = solo_tick(solos[i], s->side[i % Server::kSide], &cur_after);
+            if (e != cudaSuccess) return e;
+        }
+        for (int k = 0; k < nside; ++k) {
+            cudaError_t e = cudaEventRecord(s->join_ev[k], s->side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->join_ev[k], 0);
+            if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
@@ -380,7 +430,15 @@ int launch_tick(Server* s) {
     };
     for (auto& kv : s->classes)
         for (Req* q : kv.second.members) advance(q);
-    for (Req* q : solos) advance(q);
+    for (Req* q : solos) {
+        // one buffer flip per launch: blocked launches while a full block is left, then singles
+        const long long left = q->nsteps - q->launched;
+        const long long adv = left < S ? left : S;
+        const long long flips = q->solo_tb ? adv / q->solo_depth + adv % q->solo_depth : adv;
+        q->cur = (int)((q->cur + flips) % q->nlev);
+        q->launched += adv;
+        if (q->launched >= q->nsteps) tick.finishing.push_back(q);
+    }
     cudaError_t e = cudaEventCreateWithFlags(&tick.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     e = cudaEventRecord(tick.done, s->stream);
@@ -486,6 +544,16 @@ int mmfd_server_create(const mmfd_server_desc* desc, mmfd_server** out) {
         if (s->own_stream) cudaStreamDestroy(s->stream);
         delete s;
         return set_error(MMFD_ERR_OOM, "server flag allocation failed");
+    }
+    e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < Server::kSide && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join_ev[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mmfd_server_destroy(reinterpret_cast<mmfd_server*>(s));
+        return cuda_fail(e, "side streams");
     }
     *out = reinterpret_cast<mmfd_server*>(s);
     return MMFD_OK;
@@ -671,6 +739,14 @@ int mmfd_server_destroy(mmfd_server* h) {
     srv_free(s, s->stage);
     srv_free(s, s->d_flag);
     cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < Server::kSide; ++k) {
+        if (s->side[k]) {
+            cudaStreamSynchronize(s->side[k]);
+            cudaStreamDestroy(s->side[k]);
+        }
+        if (s->join_ev[k]) cudaEventDestroy(s->join_ev[k]);
+    }
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
     cudaMemPoolDestroy(s->pool);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;

@@ -2,8 +2,10 @@
 
 Each request: PDE uniform over {CDE, NCDE, NSE}; 2D with p = 0.7 (side log-uniform in
 [32, 1024]) else 3D (side log-uniform in [32, 128]); steps log-uniform in [100, 5000];
-storage FP32 or BF16 with p = 1/2; parameters as the single-solve workloads; initial fields
-from seeded Fourier series.  Arrivals: Poisson at a given rate.
+storage FP32 or BF16 with p = 1/2 (BF16 requests use stochastic rounding: with
+round-to-nearest, the small per-step changes of the slow three-level NCDE solves stall in
+BF16); parameters as the single-solve workloads; initial fields from seeded Fourier series.
+Arrivals: Poisson at a given rate.
 """
 from __future__ import annotations
 
@@ -14,6 +16,8 @@ from typing import List
 import numpy as np
 
 from . import inputs
+
+STOCHASTIC_ROUND = 0x4   # MMFD_FLAG_STOCHASTIC_ROUND of the C ABI
 
 
 @dataclass
@@ -93,6 +97,8 @@ def make_request(rng: inputs.SplitMix64, storage_mix: bool = True, steps_scale: 
                         a=(1.0, 0.0, 0.0), abar=(1.0, 0.0, 0.0), storage=storage, ref=[1.0, 0.0, 0.0, 0.0])
             fields = [rho, 0.03 * base, 0.03 * g, 0.03 * np.transpose(base, (1, 2, 0))]
         nodes = n * n * n
+    if storage == "bf16":
+        desc["flags"] = STOCHASTIC_ROUND
     return Request(desc, fields, steps, nodes)
 
 
