@@ -64,10 +64,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+# Sources that determine each step kernel's code and launch shape -- the kernel, its launcher,
+# the autotuner that picks the work-item height and the tensor-map boxes (the traffic figure of
+# a committed profile is used only while these files are unchanged).
+KERNEL_SOURCES = {
+    "k_march2d": ["k_march2d.cuh", "k_march2d.cu", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
+                  "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+    "k_march2d_tb": ["k_march2d_tb.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
+                     "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+    "k_march3d": ["k_march3d.cuh", "k_march3d.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
+                  "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_17057_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(KERNEL_SOURCES.get(kernel, os.listdir(csrc))):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -81,7 +94,7 @@ def traffic_from_profile(kernel: str, workload: str):
     with open(p) as fh:
         d = json.load(fh)
     e = d.get(f"{workload}:{kernel}")
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

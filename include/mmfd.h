@@ -151,7 +151,9 @@ int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
 /* Copy one level into the solver.  level 0 = t_n, level 1 = t_{n-1} (three-level only).
  * fields: nf pointers, each to nx*ny*nz values of element type dtype (MMFD_DT_*), on the
  * host (where = MMFD_HOST, pageable or pinned) or device (MMFD_DEVICE).  The data is copied;
- * pointers are not retained.  Setting level 0 of a three-level solver also sets level 1
+ * pointers are not retained.  Copies are asynchronous on the solver's stream: device and
+ * page-locked host buffers (the latter are read directly by the packing kernel) must stay
+ * unchanged until the stream has passed this call; pageable host buffers are staged first.  Setting level 0 of a three-level solver also sets level 1
  * to the same values (the equilibrium start) unless level 1 is set afterwards. */
 int mmfd_set_fields(mmfd_solver* s, int level, const void* const* fields, int where, int dtype);
 

@@ -2,6 +2,8 @@
 // FP64 reductions (sum, max |v|, non-finite count, GRE of Sec. IV and max-norm).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "stencil.cuh"
 
@@ -16,6 +18,79 @@ template <int ST>
 __device__ __forceinline__ double load_st(const void* base, long long i, double ref) {
     using Tr = Storage<ST>;
     return (double)Tr::load(static_cast<const typename Tr::S*>(base) + i, (typename Tr::T)ref);
+}
+
+// Four consecutive values of a dense FP64 / FP32 source row, 16-byte aligned.
+__device__ __forceinline__ void ld4_src(const void* src, int dtype, long long i, double v[4]) {
+    if (dtype == 0) {
+        const double2 a = *reinterpret_cast<const double2*>(static_cast<const double*>(src) + i);
+        const double2 b = *reinterpret_cast<const double2*>(static_cast<const double*>(src) + i + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+        const float4 a = *reinterpret_cast<const float4*>(static_cast<const float*>(src) + i);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+}
+
+// Four consecutive stored values starting at a 16-byte aligned slot.
+template <int ST>
+__device__ __forceinline__ void ld4_st(const void* base, long long i, double ref, double v[4]) {
+    using Tr = Storage<ST>;
+    using S = typename Tr::S;
+    const S* p = static_cast<const S*>(base) + i;
+    if constexpr (ST == ST_F32) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (ST == ST_F64) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (double)Tr::load(p + k, (typename Tr::T)ref);
+    }
+}
+
+// Vector pack: rows as in k_pack, four consecutive columns per thread (nx a multiple of 4 and a
+// 16-byte aligned source); the source may be device memory or page-locked host memory read
+// directly over the host link.
+template <int ST>
+__global__ void k_pack4(Geom g, const void* __restrict__ src, int src_dtype, void* __restrict__ dst, double ref) {
+    using Tr = Storage<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    S* d = static_cast<S*>(dst);
+    const long long rows = (long long)g.ny * g.nz;
+    const int nq = g.nx >> 2;
+    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const bool yedge = y == 0 || y == g.ny - 1 || (g.dim == 3 && (z == 0 || z == g.nz - 1));
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+            const int x = q << 2;
+            double v[4];
+            ld4_src(src, src_dtype, r * g.nx + x, v);
+            S sv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sv[k] = Tr::pack((T)v[k], (T)ref, 0u);
+            const bool edge = yedge || x < g.gx || x + 3 >= g.nx - g.gx;
+            if (!edge) {
+                S* p = d + g.at(x, y, z);
+                if constexpr (ST == ST_F32) {
+                    *reinterpret_cast<float4*>(p) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) p[k] = sv[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (g.dim == 3) store_with_ghosts<3>(d, g, x + k, y, z, sv[k]);
+                    else store_with_ghosts<2>(d, g, x + k, y, z, sv[k]);
+                }
+            }
+        }
+    }
 }
 
 // Layout kernels walk rows (blockIdx.y over y + z ny, grid-stride) and columns (threads), so no
@@ -79,19 +154,37 @@ __device__ __forceinline__ Acc4 combine(int op, Acc4 x, Acc4 y) {
 // Fixed-order block reduction: block b covers rows b, b + nblocks, ... (row = y + z ny) and, in
 // each row, columns threadIdx.x, + blockDim.x, ...; it reduces through shared memory in a fixed
 // tree, so the result is bitwise reproducible.
-template <int ST>
+// The operation is a template parameter (0 sum, 1 max |v|, 2 non-finite count, 3 error norms):
+// with a run-time switch in the element loop every element paid for all four accumulators.
+template <int ST, int OPT>
 __global__ void __launch_bounds__(kRedThreads) k_reduce_parts(Geom g, const void* __restrict__ lev, double fref,
-                                                              int op, const void* __restrict__ ref, int ref_dtype,
+                                                              const void* __restrict__ ref, int ref_dtype,
                                                               Acc4* __restrict__ parts) {
+    constexpr int op = OPT;
     __shared__ Acc4 sh[kRedThreads];
     const long long rows = (long long)g.ny * g.nz;
     Acc4 acc = {0, 0, 0, 0};
-    const int cop = op == 2 ? 0 : op;
+    constexpr int cop = op == 2 ? 0 : op;
+    const bool vec = OPT != 3 && (g.nx & 3) == 0;
     for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
         const int y = (int)(r % g.ny);
         const int z = (int)(r / g.ny);
         const long long sbase = g.at(0, y, z);
         const long long dbase = r * g.nx;
+        if (vec) {
+            // four columns per thread per pass (the row starts on a 16-byte boundary)
+            for (int x = threadIdx.x << 2; x < g.nx; x += blockDim.x << 2) {
+                double v[4];
+                ld4_st<ST>(lev, sbase + x, fref, v);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if constexpr (OPT == 0) acc.a += v[k];
+                    else if constexpr (OPT == 1) acc.a = fmax(acc.a, fabs(v[k]));
+                    else if constexpr (OPT == 2) acc.a += isfinite(v[k]) ? 0.0 : 1.0;
+                }
+            }
+            continue;
+        }
         for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
             const double v = load_st<ST>(lev, sbase + x, fref);
             Acc4 e;
@@ -152,6 +245,13 @@ cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, v
                         double ref, cudaStream_t s) {
     const dim3 blocks = grid_rows(g);
     char* dst = static_cast<char*>(dst_level) + (size_t)field * g.fs * g.es;
+    if ((g.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && g.nx >= 8) {
+        const dim3 b4((unsigned)((g.nx / 4 + 255) / 256 < 64 ? (g.nx / 4 + 255) / 256 : 64), blocks.y, 1);
+        if (st == ST_F64) k_pack4<ST_F64><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref);
+        else if (st == ST_F32) k_pack4<ST_F32><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref);
+        else k_pack4<ST_BF16><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref);
+        return cudaGetLastError();
+    }
     if (st == ST_F64) k_pack<ST_F64><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
     else if (st == ST_F32) k_pack<ST_F32><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
     else k_pack<ST_BF16><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
@@ -176,9 +276,18 @@ cudaError_t launch_reduce(const Geom& g, int st, const void* level, int field, d
     (void)nparts;
     const char* lev = static_cast<const char*>(level) + (size_t)field * g.fs * g.es;
     Acc4* parts = reinterpret_cast<Acc4*>(d_partials);
-    if (st == ST_F64) k_reduce_parts<ST_F64><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, op, ref, ref_dtype, parts);
-    else if (st == ST_F32) k_reduce_parts<ST_F32><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, op, ref, ref_dtype, parts);
-    else k_reduce_parts<ST_BF16><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, op, ref, ref_dtype, parts);
+    auto parts_kernel = [&](auto stc) -> void {
+        constexpr int SC = decltype(stc)::value;
+        switch (op) {
+            case 0: k_reduce_parts<SC, 0><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, ref, ref_dtype, parts); break;
+            case 1: k_reduce_parts<SC, 1><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, ref, ref_dtype, parts); break;
+            case 2: k_reduce_parts<SC, 2><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, ref, ref_dtype, parts); break;
+            default: k_reduce_parts<SC, 3><<<kRedBlocks, kRedThreads, 0, s>>>(g, lev, fref, ref, ref_dtype, parts); break;
+        }
+    };
+    if (st == ST_F64) parts_kernel(std::integral_constant<int, ST_F64>{});
+    else if (st == ST_F32) parts_kernel(std::integral_constant<int, ST_F32>{});
+    else parts_kernel(std::integral_constant<int, ST_BF16>{});
     k_reduce_final<<<1, kRedThreads, 0, s>>>(parts, kRedBlocks, op, d_out);
     return cudaGetLastError();
 }

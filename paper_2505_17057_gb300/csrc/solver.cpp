@@ -96,9 +96,18 @@ int solver_set_fields(Solver* s, int level, const void* const* fields, int where
         if (!fields[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
         const void* src = fields[f];
         if (where == MMFD_HOST) {
-            cudaError_t e = cudaMemcpyAsync(s->stage, src, bytes, cudaMemcpyHostToDevice, s->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
-            src = s->stage;
+            // page-locked host memory is read by the pack kernel itself, over the host link (one
+            // pass instead of a copy into the staging buffer plus a second pass over it)
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, src) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                pa.devicePointer) {
+                src = pa.devicePointer;
+            } else {
+                cudaGetLastError();
+                cudaError_t e = cudaMemcpyAsync(s->stage, src, bytes, cudaMemcpyHostToDevice, s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+                src = s->stage;
+            }
         }
         cudaError_t e = launch_pack(s->g, s->r.st, src, dtype, s->lev[idx], f, s->r.ref[f], s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
