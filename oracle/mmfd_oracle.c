@@ -17,6 +17,12 @@
  *   form 2: direct MMFD, Eq. (2-2) / (2-4) / (3layerMMFD-1);
  *   form 3: central MMFD, Eq. (2-2-1) / (2-4-1) with the even/odd split Eq. (2-5)
  *           and the central differences Eq. (CentralFD).
+ * Multiple-parameter-set scheme (two_sets = 1), Eq. (2-2-1b): the zeroth-order term keeps
+ * {a}, the second-difference (even) term takes its own set and the first-difference (odd)
+ * term another; the momentum equation likewise (the paper: "similarly" for Eq. (2-4-1)).
+ *   form 3 evaluates Eq. (2-2-1b) (and its momentum analogue) directly;
+ *   form 4: the TRT MesoFD scheme Eq. (2-1b): f_j = sum_k (abar_k f_j^eq,+ + ahat_k f_j^eq,-)
+ *           at x + k c_j, then the moments -- equal to form 3 when {a} is the even set.
  * EDFs: general quadratic form Eq. (3-3)/(3-4) with direction-dependent
  * c_s,alpha^2 = d_0alpha c_alpha^2 (App. A); linear CDE Eq. (TforMMFD-0);
  * NCDE Eq. (NCDEfeq); incompressible NSE He-Luo form of Remark 4.
@@ -35,7 +41,7 @@
 
 enum { OR_D2Q5 = 0, OR_D2Q9 = 1, OR_D3Q7 = 2, OR_D3Q19 = 3 };
 enum { OR_LCDE = 0, OR_NCDE = 1, OR_NSE = 2 };
-enum { OR_FORM_MESOFD = 1, OR_FORM_MMFD = 2, OR_FORM_CENTRAL = 3 };
+enum { OR_FORM_MESOFD = 1, OR_FORM_MMFD = 2, OR_FORM_CENTRAL = 3, OR_FORM_MESOFD_TRT = 4 };
 enum { OR_OK = 0, OR_EARG = -1 };
 
 #define OR_QMAX 19
@@ -57,6 +63,14 @@ typedef struct {
     double flux[12];    /* NCDE: B_alpha(phi) = sum_{p=0}^{3} flux[4 alpha + p] phi^p */
     double m2[5];       /* NCDE: isotropic second moment M2(phi) = sum_{p=0}^{4} m2[p] phi^p */
     double rho0;        /* NSE: He-Luo reference density (Remark 4) */
+    /* Eq. (2-2-1b), used when two_sets = 1 (index k + 1 as above):
+     *   d2[l]: set of the second-difference term on f^eq,+ of the phi / rho moment,
+     *   d1[l]: set of the first-difference term on f^eq,-,
+     *   bar_d2[l]: momentum, second-difference term on f^eq,-,
+     *   bar_d1[l]: momentum, first-difference term on f^eq,+,
+     * for level l = 0 (t) and l = 1 (t - dt). */
+    int two_sets;
+    double d2[2][3], d1[2][3], bar_d2[2][3], bar_d1[2][3];
 } or_problem;
 
 /* Lattice tables of App. A, with the scalings of Eq. (3-4) folded in once. */
@@ -309,10 +323,15 @@ static void node_central(const or_problem* P, const or_lat* L, const double* lev
         const double* lev = levs[l];
         const double* a = coef(P, l);
         const double* ab = coefbar(P, l);
+        /* Eq. (2-2-1b): with two_sets the difference terms take their own sets */
+        const double* e2 = P->two_sets ? P->d2[l] : a;
+        const double* o1 = P->two_sets ? P->d1[l] : a;
+        const double* be2 = P->two_sets ? P->bar_d2[l] : ab;
+        const double* bo1 = P->two_sets ? P->bar_d1[l] : ab;
         double A0 = a[0] + a[1] + a[2];
         double Ab0 = ab[0] + ab[1] + ab[2];
-        double ap = a[2] + a[0], am = a[2] - a[0];
-        double abp = ab[2] + ab[0], abm = ab[2] - ab[0];
+        double ap = e2[2] + e2[0], am = o1[2] - o1[0];
+        double abp = be2[2] + be2[0], abm = bo1[2] - bo1[0];
         double M0 = 0.0, M1[3] = {0, 0, 0};
         for (int j = 0; j < L->b; ++j) {
             double fe = feq_at(P, L, lev, N, idx, j);
@@ -339,6 +358,38 @@ static void node_central(const or_problem* P, const or_lat* L, const double* lev
     for (int d = 1; d < nf; ++d) out[d] = acc[d] / P->rho0;
 }
 
+/* One node, form 4: the TRT version of the MesoFD scheme, Eq. (2-1b), m_q = 1:
+ *   f_j(x) = sum_q sum_k [ abar_kq f_j^eq,+ + ahat_kq f_j^eq,- ](x + k c_j, t + q dt)
+ * followed by phi = sum_j f_j.  The even set is d2 and the odd set d1; for the NSE the
+ * momentum distribution takes bar_d1 on the even parts and bar_d2 on the odd parts and
+ * (rho u) = sum_j c_j fbar_j.  Expanding the shifts with Eq. (2-5) turns this into
+ * Eq. (2-2-1b) with the zeroth-order set equal to the even set (momentum: to bar_d2). */
+static void node_mesofd_trt(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
+                            long long idx, double* out) {
+    int nf = nfields(P, L);
+    double fj[OR_QMAX], fbarj[OR_QMAX];
+    for (int j = 0; j < L->b; ++j) {
+        double s = 0.0, sb = 0.0;
+        for (int l = 0; l < P->levels - 1; ++l) {
+            for (int k = -1; k <= 1; ++k) {
+                long long ik = shifted(P, L, idx, j, k);
+                double fe = feq_even(P, L, levs[l], N, ik, j), fo = feq_odd(P, L, levs[l], N, ik, j);
+                s += P->d2[l][k + 1] * fe + P->d1[l][k + 1] * fo;
+                sb += P->bar_d1[l][k + 1] * fe + P->bar_d2[l][k + 1] * fo;
+            }
+        }
+        fj[j] = s;
+        fbarj[j] = sb;
+    }
+    double phi = 0.0, m[3] = {0, 0, 0};
+    for (int j = 0; j < L->b; ++j) {
+        phi += fj[j];
+        for (int d = 0; d < L->dim; ++d) m[d] += L->cj[j][d] * fbarj[j];
+    }
+    out[0] = phi;
+    for (int d = 1; d < nf; ++d) out[d] = m[d - 1] / P->rho0;
+}
+
 typedef void (*node_fn)(const or_problem*, const or_lat*, const double* [2], long long, long long,
                         double*);
 
@@ -347,6 +398,7 @@ static node_fn pick(int form) {
     case OR_FORM_MESOFD: return node_mesofd;
     case OR_FORM_MMFD: return node_mmfd;
     case OR_FORM_CENTRAL: return node_central;
+    case OR_FORM_MESOFD_TRT: return node_mesofd_trt;
     default: return 0;
     }
 }

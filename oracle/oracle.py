@@ -26,7 +26,7 @@ SRC = os.path.join(HERE, "mmfd_oracle.c")
 
 LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q19": 3}
 PDES = {"LCDE": 0, "NCDE": 1, "NSE": 2}
-FORMS = {"mesofd": 1, "mmfd": 2, "central": 3}
+FORMS = {"mesofd": 1, "mmfd": 2, "central": 3, "mesofd_trt": 4}
 LATTICE_DIM = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q19": 3}
 
 _lock = threading.Lock()
@@ -54,6 +54,9 @@ class _Problem(C.Structure):
         ("abar", C.c_double * 3), ("abarhat", C.c_double * 3),
         ("u", C.c_double * 3), ("Cmat", C.c_double * 9),
         ("flux", C.c_double * 12), ("m2", C.c_double * 5), ("rho0", C.c_double),
+        ("two_sets", C.c_int),
+        ("d2", (C.c_double * 3) * 2), ("d1", (C.c_double * 3) * 2),
+        ("bar_d2", (C.c_double * 3) * 2), ("bar_d1", (C.c_double * 3) * 2),
     ]
 
 
@@ -94,6 +97,11 @@ class Problem:
     """A problem in the paper's notation (all scheme and EDF parameters explicit).
 
     a, ahat, abar, abarhat: coefficient triples (a_{-1}, a_0, a_1).
+    sets: None for the one-set scheme, or the multiple-parameter-set scheme of Eq. (2-2-1b) as
+    a dict of triples per level ((level t, level t - dt)): "d2" (second-difference term on
+    f^eq,+ of the phi / rho moment), "d1" (first-difference term on f^eq,-), and for the NSE
+    momentum "bar_d2" (second difference on f^eq,-) and "bar_d1" (first difference on f^eq,+).
+    a / ahat (abar / abarhat) keep the zeroth-order term.
     """
     lattice: str
     pde: str
@@ -110,6 +118,7 @@ class Problem:
     flux: Sequence[float] = field(default_factory=lambda: [0.0] * 12)
     m2: Sequence[float] = field(default_factory=lambda: [0.0] * 5)
     rho0: float = 1.0
+    sets: Optional[dict] = None
 
     @property
     def dim(self) -> int:
@@ -139,6 +148,13 @@ class Problem:
         p.flux = (C.c_double * 12)(*_arr3(np.asarray(self.flux, dtype=float).ravel(), 12))
         p.m2 = (C.c_double * 5)(*_arr3(self.m2, 5))
         p.rho0 = float(self.rho0)
+        if self.sets:
+            p.two_sets = 1
+            for name in ("d2", "d1", "bar_d2", "bar_d1"):
+                lv = self.sets.get(name, ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)))
+                arr = getattr(p, name)
+                for l in range(2):
+                    arr[l] = (C.c_double * 3)(*_arr3(lv[l]))
         return p
 
 
