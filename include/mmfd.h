@@ -49,6 +49,7 @@ enum { MMFD_COEF_EXPLICIT = 0, MMFD_COEF_TARGETS = 1 };
 #define MMFD_FLAG_ALLOW_UNSTABLE 0x1u   /* skip the create-time stability rejection */
 #define MMFD_FLAG_DROP_OFFDIAG 0x2u     /* axis lattices: drop K_xy (solve with diag(K)) */
 #define MMFD_FLAG_STOCHASTIC_ROUND 0x4u /* BF16 storage: stochastic instead of nearest rounding */
+#define MMFD_FLAG_TWO_SETS 0x8u         /* multiple-parameter-set scheme, Eq. (2-2-1b): see mmfd_desc */
 
 typedef int (*mmfd_alloc_fn)(size_t bytes, void** ptr, void* ctx);
 typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
@@ -75,6 +76,15 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        Eq. (X) (three-level) or a_{-1} = 1 - a_0/2, a_1 = -a_0/2 (two-level,
  *                        Eq. (LMMFD-2-2); only targets[0] used); targets_bar likewise for the
  *                        NSE momentum set.
+ *  d2, d1, bar_d2, bar_d1  with MMFD_FLAG_TWO_SETS: the multiple-parameter-set scheme of
+ *                        Eq. (2-2-1b).  a / ahat (abar / abarhat) then give only the zeroth-order
+ *                        term sum_k a_k phi(x); the second-difference term on the even parts
+ *                        f^eq,+ takes d2, the first-difference term on the odd parts f^eq,- takes
+ *                        d1.  The NSE momentum, likewise: bar_d2 on the second difference of
+ *                        f^eq,-, bar_d1 on the first difference of f^eq,+.  Index [0] is level t,
+ *                        [1] level t - dt (three-level), each (a_{-1}, a_0, a_1).  With a = d2 and
+ *                        abar = bar_d2 this is the TRT MesoFD scheme of Eq. (2-1b) (even set d2,
+ *                        odd set d1; momentum: even set bar_d1, odd set bar_d2).
  *  storage, ref[4]       storage type; BF16 offsets per field (default ref = {rho0 or 0, 0, ..}).
  *  flags                 MMFD_FLAG_*.
  *  temporal_depth        time steps fused per kernel launch (temporal blocking): 1 = none;
@@ -106,6 +116,7 @@ typedef struct {
     int coef_mode;
     double a[3], ahat[3], abar[3], abarhat[3];
     double targets[5], targets_bar[5];
+    double d2[2][3], d1[2][3], bar_d2[2][3], bar_d1[2][3];
     int storage;
     unsigned flags;
     double ref[4];

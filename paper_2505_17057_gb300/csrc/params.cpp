@@ -178,6 +178,12 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
     // A_00 = 1 (Eq. (4-2-0)); a scheme violating it does not conserve mass.
     const double A00 = r.a[0] + r.a[1] + r.a[2] + (d.levels == 3 ? r.ahat[0] + r.ahat[1] + r.ahat[2] : 0.0);
     if (std::fabs(A00 - 1.0) > 1e-12) return fail(msg, MMFD_ERR_ARG, "coefficients violate A_00 = 1");
+    if (d.flags & MMFD_FLAG_TWO_SETS) {
+        for (int l = 0; l < 2; ++l)
+            for (int k = 0; k < 3; ++k)
+                if (!finite(d.d2[l][k]) || !finite(d.d1[l][k]) || !finite(d.bar_d2[l][k]) || !finite(d.bar_d1[l][k]))
+                    return fail(msg, MMFD_ERR_ARG, "non-finite coefficient in the parameter sets");
+    }
     if (d.pde == PDE_NSE) {
         const double Ab00 = r.abar[0] + r.abar[1] + r.abar[2] +
                             (d.levels == 3 ? r.abarhat[0] + r.abarhat[1] + r.abarhat[2] : 0.0);
@@ -292,13 +298,24 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
 
     const double* sets[2] = {r.a, r.ahat};
     const double* bsets[2] = {r.abar, r.abarhat};
+    const bool two = (d.flags & MMFD_FLAG_TWO_SETS) != 0;
     for (int l = 0; l < 2; ++l) {
-        c.a0[l] = sets[l][1];
-        c.ap[l] = sets[l][2] + sets[l][0];
-        c.am[l] = sets[l][2] - sets[l][0];
-        c.ab0[l] = bsets[l][1];
-        c.abp[l] = bsets[l][2] + bsets[l][0];
-        c.abm[l] = bsets[l][2] - bsets[l][0];
+        // pair form of one level: a0 A(x) + ap f_0^eq(x) + sum_p [ap (E_p(+) + E_p(-)) + am (O_p(+) - O_p(-))].
+        // One set (Eq. (2-2-1)): ap = a_1 + a_{-1}, am = a_1 - a_{-1}, a0 = a_0.  Several sets
+        // (Eq. (2-2-1b)): the zeroth-order term sum_k a_k A(x) plus the second difference of the
+        // even parts with d2 and the first difference of the odd parts with d1, which expands
+        // to ap = d2^+, am = d1^-, a0 = sum_k a_k - d2^+.  The momentum likewise, with bar_d2 on
+        // the odd parts' second difference (abp) and bar_d1 on the even parts' first (abm).
+        const double* e2 = two ? d.d2[l] : sets[l];
+        const double* o1 = two ? d.d1[l] : sets[l];
+        const double* be2 = two ? d.bar_d2[l] : bsets[l];
+        const double* bo1 = two ? d.bar_d1[l] : bsets[l];
+        c.ap[l] = e2[2] + e2[0];
+        c.am[l] = o1[2] - o1[0];
+        c.a0[l] = two ? sets[l][0] + sets[l][1] + sets[l][2] - c.ap[l] : sets[l][1];
+        c.abp[l] = be2[2] + be2[0];
+        c.abm[l] = bo1[2] - bo1[0];
+        c.ab0[l] = two ? bsets[l][0] + bsets[l][1] + bsets[l][2] - c.abp[l] : bsets[l][1];
     }
     for (int a = 0; a < dim; ++a) c.fmom[a] = r.c[a] / rho0;
 

@@ -40,6 +40,7 @@ MMFD_COEF_EXPLICIT, MMFD_COEF_TARGETS = 0, 1
 MMFD_FLAG_ALLOW_UNSTABLE = 0x1
 MMFD_FLAG_DROP_OFFDIAG = 0x2
 MMFD_FLAG_STOCHASTIC_ROUND = 0x4
+MMFD_FLAG_TWO_SETS = 0x8
 MMFD_RED_SUM, MMFD_RED_MAXABS, MMFD_RED_NONFINITE = 0, 1, 2
 
 PDE = {"LCDE": MMFD_LCDE, "NCDE": MMFD_NCDE, "NSE": MMFD_NSE}
@@ -59,6 +60,8 @@ class mmfd_desc(C.Structure):
         ("coef_mode", C.c_int),
         ("a", C.c_double * 3), ("ahat", C.c_double * 3), ("abar", C.c_double * 3), ("abarhat", C.c_double * 3),
         ("targets", C.c_double * 5), ("targets_bar", C.c_double * 5),
+        ("d2", (C.c_double * 3) * 2), ("d1", (C.c_double * 3) * 2),
+        ("bar_d2", (C.c_double * 3) * 2), ("bar_d1", (C.c_double * 3) * 2),
         ("storage", C.c_int), ("flags", C.c_uint), ("ref", C.c_double * 4), ("temporal_depth", C.c_int),
         ("seed", C.c_ulonglong), ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p),
@@ -266,8 +269,12 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
               storage: str = "fp32", K=None, u=None, lambda_bar: float = 1.0, flux=None, diff=None,
               rho0: float = 1.0, a=None, ahat=None, abar=None, abarhat=None, targets=None, targets_bar=None,
               d0=None, flags: int = 0, ref=None, temporal_depth: int = 1, seed: Optional[int] = None,
-              stream: Optional[int] = None) -> mmfd_desc:
-    """Fill an mmfd_desc (plain field assignment; every derived constant is computed by the library)."""
+              stream: Optional[int] = None, sets: Optional[dict] = None) -> mmfd_desc:
+    """Fill an mmfd_desc (plain field assignment; every derived constant is computed by the library).
+
+    sets: the multiple-parameter-set scheme (MMFD_FLAG_TWO_SETS): a dict with "d2", "d1" and,
+    for the NSE momentum, "bar_d2", "bar_d1", each a pair of triples (level t, level t - dt).
+    """
     d = mmfd_desc_init()
     d.pde = PDE[pde]
     d.lattice = LATTICE[lattice]
@@ -317,6 +324,14 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
                 d.targets_bar[i] = float(v)
     d.storage = STORAGE[storage]
     d.flags = int(flags)
+    if sets:
+        d.flags |= MMFD_FLAG_TWO_SETS
+        for name in ("d2", "d1", "bar_d2", "bar_d1"):
+            lv = sets.get(name, ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)))
+            arr = getattr(d, name)
+            for l in range(2):
+                for k in range(3):
+                    arr[l][k] = float(lv[l][k])
     if ref is not None:
         for i, v in enumerate(ref):
             d.ref[i] = float(v)

@@ -20,8 +20,11 @@ def shape_of(n, lat):
     return (n[1], n[0]) if dims(lat) == 2 else (n[2], n[1], n[0])
 
 
-def case(lat, pde, levels, n, storage="fp64", generic=True):
-    """(desc kwargs, oracle Problem) for a generic stable problem on the given grid."""
+def case(lat, pde, levels, n, storage="fp64", generic=True, coeffs=None):
+    """(desc kwargs, oracle Problem) for a generic stable problem on the given grid.
+
+    coeffs: optional dict overriding "a", "ahat" (and, for the NSE, "abar", "abarhat"); the
+    oracle problem is then built from them (its EDF parameters follow the scheme's moments)."""
     dim = dims(lat)
     n = list(n) + [1] * (3 - len(n))
     dt = 0.8
@@ -30,6 +33,9 @@ def case(lat, pde, levels, n, storage="fp64", generic=True):
     a3, ah3 = THREE_A, THREE_AHAT
     a = a2 if levels == 2 else a3
     ah = (0.0, 0.0, 0.0) if levels == 2 else ah3
+    coeffs = coeffs or {}
+    a = tuple(coeffs.get("a", a))
+    ah = tuple(coeffs.get("ahat", ah))
     kw = dict(pde=pde, lattice=lat, levels=levels, n=n[:dim] if dim == 3 else n[:2], dt=dt, dx=dx, storage=storage)
     if dim == 3:
         kw["n"] = n
@@ -50,6 +56,8 @@ def case(lat, pde, levels, n, storage="fp64", generic=True):
     else:
         ab = (0.9, 0.2, -0.1) if levels == 2 else (0.8, 0.0, 0.2)
         abh = (0.0, 0.0, 0.0) if levels == 2 else (0.1, 0.0, -0.1)
+        ab = tuple(coeffs.get("abar", ab))
+        abh = tuple(coeffs.get("abarhat", abh))
         kw.update(a=a, ahat=ah, abar=ab, abarhat=abh)
         prob = P.problem_nse(lat, levels, n, dt, dx, a, ab, ah, abh)
     return kw, prob
