@@ -19,7 +19,7 @@
  *           and the central differences Eq. (CentralFD).
  * Multiple-parameter-set scheme (two_sets = 1), Eq. (2-2-1b): the zeroth-order term keeps
  * {a}, the second-difference (even) term takes its own set and the first-difference (odd)
- * term another; the momentum equation likewise (the paper: "similarly" for Eq. (2-4-1)).
+ * term another; the momentum equation likewise (its analogue of Eq. (2-4-1)).
  *   form 3 evaluates Eq. (2-2-1b) (and its momentum analogue) directly;
  *   form 4: the TRT MesoFD scheme Eq. (2-1b): f_j = sum_k (abar_k f_j^eq,+ + ahat_k f_j^eq,-)
  *           at x + k c_j, then the moments -- equal to form 3 when {a} is the even set.
@@ -27,6 +27,8 @@
  * c_s,alpha^2 = d_0alpha c_alpha^2 (App. A); linear CDE Eq. (TforMMFD-0);
  * NCDE Eq. (NCDEfeq); incompressible NSE He-Luo form of Remark 4.
  * Lattices: rD2Q5I, rD2Q9, rD3Q7, rD3Q19 of App. A.
+ * Independent checks on explicit populations: SRT LB with tau = 1 and TRT LB with
+ * s+ + s- = 2 (the special cases (1) and (2) of Sec. III.C), collide then stream.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no SIMD
  * intrinsics; summation order fixed: levels t then t - dt, k ascending,
@@ -552,6 +554,60 @@ int or_lbgk_tau1_run(const or_problem* P, long long nsteps, double* fields) {
             for (int j = 0; j < L.b; ++j) g[j * N + x] = geq_j(&L, j, A, B, C);
         }
         /* stream: population j moves from x to x + e_j */
+        for (long long x = 0; x < N; ++x)
+            for (int j = 0; j < L.b; ++j) f[j * N + shifted(P, &L, x, j, 1)] = g[j * N + x];
+    }
+    for (long long x = 0; x < N; ++x) {
+        double m0 = 0.0, m1[3] = {0, 0, 0};
+        for (int j = 0; j < L.b; ++j) {
+            m0 += f[j * N + x];
+            for (int d = 0; d < L.dim; ++d) m1[d] += L.cj[j][d] * f[j * N + x];
+        }
+        fields[x] = m0;
+        for (int d = 1; d < nf; ++d) fields[d * N + x] = m1[d - 1] / P->rho0;
+    }
+    free(f);
+    free(g);
+    return OR_OK;
+}
+
+/* Independent two-relaxation-time LB code (Sec. III.C, special case (2), TRT with
+ * s+ + s- = 2), collide-then-stream on explicit populations:
+ *   f_j* = f_j - s+ (f_j^+ - f_j^eq,+) - s- (f_j^- - f_j^eq,-),   f_j(x + c_j, t + dt) = f_j*(x, t),
+ * with the even / odd parts of Eq. (2-5) taken over j and its opposite jbar, s+ = 2 - s-, and
+ * f^eq built from the moments of f.  Starts from equilibrium populations of `fields`; the a's
+ * of P are not used.  Fields (moments) in place after nsteps. */
+int or_trt_run(const or_problem* P, double s_minus, long long nsteps, double* fields) {
+    or_lat L;
+    if (check(P, &L) != OR_OK) return OR_EARG;
+    const double s_plus = 2.0 - s_minus;
+    const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
+    const int nf = nfields(P, &L);
+    double* f = (double*)malloc(sizeof(double) * (size_t)(L.b * N));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(L.b * N));
+    if (!f || !g) { free(f); free(g); return OR_EARG; }
+    for (long long x = 0; x < N; ++x)
+        for (int j = 0; j < L.b; ++j) f[j * N + x] = feq_at(P, &L, fields, N, x, j);
+    for (long long s = 0; s < nsteps; ++s) {
+        for (long long x = 0; x < N; ++x) {
+            double m0 = 0.0, m1[3] = {0, 0, 0};
+            for (int j = 0; j < L.b; ++j) {
+                m0 += f[j * N + x];
+                for (int d = 0; d < L.dim; ++d) m1[d] += L.cj[j][d] * f[j * N + x];
+            }
+            double loc[4];
+            loc[0] = m0;
+            for (int d = 0; d < L.dim; ++d) loc[1 + d] = m1[d] / P->rho0;
+            double A, B[3], C[9], eq[OR_QMAX];
+            edf_args(P, &L, loc, &A, B, C);
+            for (int j = 0; j < L.b; ++j) eq[j] = geq_j(&L, j, A, B, C);
+            for (int j = 0; j < L.b; ++j) {
+                const int jb = L.opp[j];
+                const double fp = 0.5 * (f[j * N + x] + f[jb * N + x]), fm = 0.5 * (f[j * N + x] - f[jb * N + x]);
+                const double ep = 0.5 * (eq[j] + eq[jb]), em = 0.5 * (eq[j] - eq[jb]);
+                g[j * N + x] = f[j * N + x] - s_plus * (fp - ep) - s_minus * (fm - em);
+            }
+        }
         for (long long x = 0; x < N; ++x)
             for (int j = 0; j < L.b; ++j) f[j * N + shifted(P, &L, x, j, 1)] = g[j * N + x];
     }

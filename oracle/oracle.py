@@ -77,6 +77,7 @@ def lib():
             L.or_step_nodes.argtypes = [pp, C.c_int, dp, dp, C.POINTER(C.c_longlong), C.c_longlong, dp]
             L.or_run.argtypes = [pp, C.c_int, C.c_longlong, dp, dp]
             L.or_lbgk_tau1_run.argtypes = [pp, C.c_longlong, dp]
+            L.or_trt_run.argtypes = [pp, C.c_double, C.c_longlong, dp]
             _lib = L
         return _lib
 
@@ -268,6 +269,17 @@ def lbgk_tau1_run(prob: Problem, level_n, nsteps: int) -> List[np.ndarray]:
     if lib().or_lbgk_tau1_run(C.byref(p), int(nsteps), _dp(b)) != 0:
         raise ValueError("oracle rejected the problem")
     return _unpack(b)
+
+
+def trt_run(prob: Problem, level_n, s_minus: float, nsteps: int) -> List[np.ndarray]:
+    """Independent TRT lattice-Boltzmann run (s+ = 2 - s-), from equilibrium populations of
+    level_n; returns the moments after nsteps."""
+    buf = _pack(level_n, prob.nf, prob.shape)
+    p = prob.to_c()
+    rc = lib().or_trt_run(C.byref(p), float(s_minus), int(nsteps), _dp(buf))
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    return _unpack(buf)
 
 
 class NodeSampler:
