@@ -215,6 +215,15 @@ int mmfd_destroy(mmfd_solver* s);
 /* Host-only helpers (no GPU needed). */
 /* Eq. (X): (a_0, A_10, A_11, A_21, A_22) -> a = (a_{-1}, a_0, a_1), ahat likewise. */
 int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3]);
+/* Sec. III.C, special case (2): the TRT lattice-Boltzmann model with s+ + s- = 2 as a
+ * three-level MMFD scheme.  s_minus (the odd-moment rate, 0 < s_minus < 2) gives, with
+ * w = 1 - s_minus, the scalar / density sets a = (1, 0, w), ahat = (0, -w, 0) and the NSE
+ * momentum sets abar = (1, 0, -w), abarhat = (0, w, 0) (the momentum pair follows from the same
+ * collide-and-stream elimination; it gives the viscosity c_s^2 (1/s+ - 1/2) dt, the scalar pair
+ * the diffusivity c_s^2 (1/s- - 1/2) dt).  The scheme reproduces the LB moments from the second
+ * step on when level t - dt holds the initial moments and level t one LBGK tau = 1 step of them
+ * (a = (1, 0, 0)).  Any output pointer may be NULL.  MMFD_ERR_ARG if s_minus is outside (0, 2). */
+int mmfd_trt_coefficients(double s_minus, double a[3], double ahat[3], double abar[3], double abarhat[3]);
 /* ---- autotuner --------------------------------------------------------------------------
  * Not from the paper: a build choice.  The step kernels take two tuning parameters, the temporal
  * depth (time steps per launch, where blocking is available) and the work-item height (rows in

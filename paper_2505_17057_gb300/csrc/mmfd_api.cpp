@@ -110,6 +110,17 @@ int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3])
     return solve_three_level_targets(targets, a, ahat);
 }
 
+int mmfd_trt_coefficients(double s_minus, double a[3], double ahat[3], double abar[3], double abarhat[3]) {
+    if (!(s_minus > 0.0 && s_minus < 2.0)) return set_error(MMFD_ERR_ARG, "s_minus outside (0, 2)");
+    const double w = 1.0 - s_minus;
+    const double sets[4][3] = {{1.0, 0.0, w}, {0.0, -w, 0.0}, {1.0, 0.0, -w}, {0.0, w, 0.0}};
+    double* out[4] = {a, ahat, abar, abarhat};
+    for (int i = 0; i < 4; ++i)
+        if (out[i])
+            for (int k = 0; k < 3; ++k) out[i][k] = sets[i][k];
+    return MMFD_OK;
+}
+
 static void fill_info(const Resolved& r, mmfd_info_t* o) {
     std::memset(o, 0, sizeof(*o));
     o->nf = r.nf;

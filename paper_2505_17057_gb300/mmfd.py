@@ -119,6 +119,7 @@ SIGNATURES = {
     "mmfd_set_stream": (C.c_int, [_VP, _VP]),
     "mmfd_destroy": (C.c_int, [_VP]),
     "mmfd_solve_three_level": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mmfd_trt_coefficients": (C.c_int, [C.c_double] + [C.POINTER(C.c_double)] * 4),
     "mmfd_describe": (C.c_int, [C.POINTER(mmfd_desc), C.POINTER(mmfd_info_t)]),
     "mmfd_selftest_wait_timeout": (C.c_int, [_VP, C.c_longlong]),
     "mmfd_strerror": (C.c_char_p, [C.c_int]),
@@ -193,6 +194,13 @@ def mmfd_solve_three_level(targets: Sequence[float]):
     ah = (C.c_double * 3)()
     check(lib.mmfd_solve_three_level(t, a, ah), "mmfd_solve_three_level")
     return tuple(a), tuple(ah)
+
+
+def mmfd_trt_coefficients(s_minus: float) -> dict:
+    """Keyword arguments a, ahat, abar, abarhat of make_desc for the TRT special case."""
+    out = [(C.c_double * 3)() for _ in range(4)]
+    check(lib.mmfd_trt_coefficients(float(s_minus), *out), "mmfd_trt_coefficients")
+    return dict(zip(("a", "ahat", "abar", "abarhat"), (tuple(o) for o in out)))
 
 
 def mmfd_create(d: mmfd_desc) -> int:

@@ -145,3 +145,58 @@ def test_stability_check_matches_oracle_symbol(mm):
                              targets=[a0, -1, -1, 0, 0.5], flags=mm.MMFD_FLAG_ALLOW_UNSTABLE)
             prob = P.problem_lcde(lat, 2, [24, 20], 1.0, [1, 1], K, u, P.two_level_from_a0(a0))
             assert abs(info.max_lambda - F.max_amplification(prob)) < 1e-12
+
+
+def _corollary1_q(prob, shape):
+    """max over wave numbers (theta = 0 excluded) of A^2 + B^2, Corollary 1's A and B."""
+    up, um, E = F.ubar_split(prob)
+    th = F.thetas(shape)
+    dim = len(shape)
+    A = np.zeros(shape)
+    B = np.zeros(shape)
+    for j in range(E.shape[0]):
+        xi = sum(th[i] * E[j][dim - 1 - i] for i in range(dim))
+        A += up[j] * np.cos(xi)
+        B += um[j] * np.sin(xi)
+    q = A * A + B * B
+    q.flat[0] = 0.0
+    return float(q.max())
+
+
+def test_trt_coefficients(mm):
+    for s in (0.3, 1.0, 1.7):
+        w = 1.0 - s
+        c = mm.mmfd_trt_coefficients(s)
+        assert c == {"a": (1.0, 0.0, w), "ahat": (0.0, -w, 0.0), "abar": (1.0, 0.0, -w), "abarhat": (0.0, w, 0.0)}
+    for bad in (0.0, 2.0, -0.5, float("nan")):
+        with pytest.raises(mm.MMFDError) as e:
+            mm.mmfd_trt_coefficients(bad)
+        assert e.value.code == mm.MMFD_ERR_ARG
+
+
+def test_stability_check_trt_is_corollary1(mm):
+    # the library's create-time check with the TRT sets: its max |lambda| equals the oracle's
+    # three-level roots, and it flags instability exactly where Corollary 1 (A^2 + B^2 > 1) does
+    rng = np.random.default_rng(77)
+    verdicts = []
+    for _ in range(40):
+        lat = ("D2Q5", "D2Q9")[rng.integers(2)]
+        s = rng.uniform(0.2, 1.9)
+        coef = mm.mmfd_trt_coefficients(s)
+        # K in units of the TRT's natural diffusivity (1/s- - 1/2) dt: the derived c_s^2 is then
+        # k0 + u_alpha^2 on D2Q5, below the App. A bound d_0x + d_0y < 1
+        K = np.diag(rng.uniform(0.005, 0.2, 2)) * (1.0 / s - 0.5)
+        ang = rng.uniform(0, 2 * np.pi)
+        mag = rng.uniform(0.1, 0.7)
+        u = [mag * np.cos(ang), mag * np.sin(ang)]
+        info = _describe(mm, pde="LCDE", lattice=lat, levels=3, n=[20, 18], dt=1.0, dx=[1, 1], K=K, u=u,
+                         a=coef["a"], ahat=coef["ahat"], flags=mm.MMFD_FLAG_ALLOW_UNSTABLE)
+        prob = P.problem_lcde(lat, 3, [20, 18], 1.0, [1, 1], K, u, coef["a"], coef["ahat"])
+        assert abs(info.max_lambda - F.max_amplification(prob)) < 1e-12
+        q = _corollary1_q(prob, prob.shape)
+        if abs(q - 1) < 1e-9:
+            continue
+        # the library's maximum includes theta = 0 (root exactly 1, the conserved mass)
+        assert (info.max_lambda > 1 + 1e-12) == (q > 1), (lat, s, mag, q, info.max_lambda)
+        verdicts.append(q > 1)
+    assert len(verdicts) > 30 and 3 <= sum(verdicts) <= len(verdicts) - 3
