@@ -27,6 +27,8 @@
  * c_s,alpha^2 = d_0alpha c_alpha^2 (App. A); linear CDE Eq. (TforMMFD-0);
  * NCDE Eq. (NCDEfeq); incompressible NSE He-Luo form of Remark 4.
  * Lattices: rD2Q5I, rD2Q9, rD3Q7, rD3Q19 of App. A.
+ * Source terms (scalar PDEs): the b_kq F_j terms of Eq. (2-1) / (3layer-1) with
+ * F_j = g_j^eq(S, M_1F, 0), Eq. (SourceF); forms 1-3 (form 3 per Eq. (3layerMMFD-2)).
  * Independent checks on explicit populations: SRT LB with tau = 1 and TRT LB with
  * s+ + s- = 2 (the special cases (1) and (2) of Sec. III.C), collide then stream.
  *
@@ -73,7 +75,18 @@ typedef struct {
      * for level l = 0 (t) and l = 1 (t - dt). */
     int two_sets;
     double d2[2][3], d1[2][3], bar_d2[2][3], bar_d1[2][3];
+    /* Source terms of Eq. (2-1): dt sum_{k,q} b_kq F_j(x + k c_j dt, t + q dt), with the source
+     * distribution F_j = g_j^eq(S, M_1F, 0) of Eq. (SourceF) (scalar PDEs only).
+     *   src_mode OR_SRC_S:  M_1F = 0;
+     *            OR_SRC_SU: M_1F = S u with the LCDE's u (the F_j of Example 1);
+     *            OR_SRC_SM: S and M_1F given as fields (1 + dim per source level).
+     * b[k + 1] on level t (two-level: the only level), bhat[k + 1] on level t - dt. */
+    double dt;
+    int src_mode;
+    double b[3], bhat[3];
 } or_problem;
+
+enum { OR_SRC_NONE = 0, OR_SRC_S = 1, OR_SRC_SU = 2, OR_SRC_SM = 3 };
 
 /* Lattice tables of App. A, with the scalings of Eq. (3-4) folded in once. */
 typedef struct {
@@ -245,25 +258,43 @@ static long long shifted(const or_problem* P, const or_lat* L, long long idx, in
     return (z * ny + y) * nx + x;
 }
 
+/* Number of source fields per level. */
+static int nsrc(const or_problem* P, const or_lat* L) {
+    return P->src_mode == OR_SRC_SM ? 1 + L->dim : (P->src_mode ? 1 : 0);
+}
+
+/* F_j = g_j^eq(S, M_1F, 0) (Eq. (SourceF)) at node idx of one source level (SoA, N per field). */
+static double F_at(const or_problem* P, const or_lat* L, const double* src, long long N, long long idx, int j) {
+    double S = src[idx], M[3] = {0, 0, 0}, C[9] = {0};
+    for (int d = 0; d < L->dim; ++d)
+        M[d] = P->src_mode == OR_SRC_SU ? S * P->u[d] : (P->src_mode == OR_SRC_SM ? src[(1 + d) * N + idx] : 0.0);
+    return geq_j(L, j, S, M, C);
+}
+
+static const double* bcoef(const or_problem* P, int l) { return l == 0 ? P->b : P->bhat; }
+
 /* Coefficients of level index l (0: t, 1: t - dt) for the scalar / rho moment and for the
  * momentum moment. */
 static const double* coef(const or_problem* P, int l) { return l == 0 ? P->a : P->ahat; }
 static const double* coefbar(const or_problem* P, int l) { return l == 0 ? P->abar : P->abarhat; }
 
 /* One node, form 2 (direct MMFD): Eq. (2-2) / (2-4) / (3layerMMFD-1). */
-static void node_mmfd(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
-                      long long idx, double* out) {
+static void node_mmfd(const or_problem* P, const or_lat* L, const double* levs[2], const double* srcs[2],
+                      long long N, long long idx, double* out) {
     int nf = nfields(P, L);
     double acc[4] = {0, 0, 0, 0};
     for (int l = 0; l < P->levels - 1; ++l) {
         const double* a = coef(P, l);
         const double* ab = coefbar(P, l);
+        const double* bb = bcoef(P, l);
         for (int k = -1; k <= 1; ++k) {
             for (int j = 0; j < L->b; ++j) {
-                double fe = feq_at(P, L, levs[l], N, shifted(P, L, idx, j, k), j);
+                long long ik = shifted(P, L, idx, j, k);
+                double fe = feq_at(P, L, levs[l], N, ik, j);
                 acc[0] += a[k + 1] * fe;
                 if (P->pde == OR_NSE)
                     for (int d = 0; d < L->dim; ++d) acc[1 + d] += ab[k + 1] * L->cj[j][d] * fe;
+                if (P->src_mode) acc[0] += P->dt * bb[k + 1] * F_at(P, L, srcs[l], N, ik, j);
             }
         }
     }
@@ -273,8 +304,8 @@ static void node_mmfd(const or_problem* P, const or_lat* L, const double* levs[2
 
 /* One node, form 1 (MesoFD): Eq. (2-1) gives f_j(x) per direction, then Eq. (2-1-1)
  * (and, for the NSE, the double-distribution moments Eq. (2-4)). */
-static void node_mesofd(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
-                        long long idx, double* out) {
+static void node_mesofd(const or_problem* P, const or_lat* L, const double* levs[2], const double* srcs[2],
+                        long long N, long long idx, double* out) {
     int nf = nfields(P, L);
     double fj[OR_QMAX], fbarj[OR_QMAX];
     for (int j = 0; j < L->b; ++j) {
@@ -282,10 +313,13 @@ static void node_mesofd(const or_problem* P, const or_lat* L, const double* levs
         for (int l = 0; l < P->levels - 1; ++l) {
             const double* a = coef(P, l);
             const double* ab = coefbar(P, l);
+            const double* bb = bcoef(P, l);
             for (int k = -1; k <= 1; ++k) {
-                double fe = feq_at(P, L, levs[l], N, shifted(P, L, idx, j, k), j);
+                long long ik = shifted(P, L, idx, j, k);
+                double fe = feq_at(P, L, levs[l], N, ik, j);
                 s += a[k + 1] * fe;
                 sb += ab[k + 1] * fe;
+                if (P->src_mode) s += P->dt * bb[k + 1] * F_at(P, L, srcs[l], N, ik, j);
             }
         }
         fj[j] = s;
@@ -317,8 +351,8 @@ static double feq_odd(const or_problem* P, const or_lat* L, const double* lev, l
  * with a+_1 = a_1 + a_{-1}, a-_1 = a_1 - a_{-1} (Eq. (2-1-FD1-0)) and the central
  * differences of Eq. (CentralFD).  phi(x) and (rho u)(x) are the zeroth and first
  * moments of f^eq at x (Eq. (3-5)). */
-static void node_central(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
-                         long long idx, double* out) {
+static void node_central(const or_problem* P, const or_lat* L, const double* levs[2], const double* srcs[2],
+                         long long N, long long idx, double* out) {
     int nf = nfields(P, L);
     double acc[4] = {0, 0, 0, 0};
     for (int l = 0; l < P->levels - 1; ++l) {
@@ -355,6 +389,27 @@ static void node_central(const or_problem* P, const or_lat* L, const double* lev
                 for (int d = 0; d < L->dim; ++d)
                     acc[1 + d] += 0.5 * L->cj[j][d] * (abp * d2o + abm * d1e);
         }
+        if (P->src_mode) {
+            /* Eq. (3layerMMFD-2): dt [ B_0 S(x) + 1/2 sum_j ( b+_1 D2_j F_j^+ + b-_1 D1_j F_j^- ) ],
+             * B_0 = b_0 + b_1 + b_{-1}, b+-_1 = b_1 +- b_{-1}, S(x) = sum_j F_j(x) */
+            const double* bb = bcoef(P, l);
+            const double* src = srcs[l];
+            double B0 = bb[0] + bb[1] + bb[2], bp = bb[2] + bb[0], bm = bb[2] - bb[0];
+            double S0 = 0.0, t = 0.0;
+            for (int j = 0; j < L->b; ++j) S0 += F_at(P, L, src, N, idx, j);
+            for (int j = 0; j < L->b; ++j) {
+                const int jb = L->opp[j];
+                long long at[3] = {shifted(P, L, idx, j, 1), idx, shifted(P, L, idx, j, -1)};
+                double Fp[3], Fm[3];   /* even / odd parts at x + c_j, x, x - c_j */
+                for (int i = 0; i < 3; ++i) {
+                    double fj = F_at(P, L, src, N, at[i], j), fjb = F_at(P, L, src, N, at[i], jb);
+                    Fp[i] = 0.5 * (fj + fjb);
+                    Fm[i] = 0.5 * (fj - fjb);
+                }
+                t += 0.5 * (bp * (Fp[0] - 2.0 * Fp[1] + Fp[2]) + bm * (Fm[0] - Fm[2]));
+            }
+            acc[0] += P->dt * (B0 * S0 + t);
+        }
     }
     out[0] = acc[0];
     for (int d = 1; d < nf; ++d) out[d] = acc[d] / P->rho0;
@@ -366,8 +421,9 @@ static void node_central(const or_problem* P, const or_lat* L, const double* lev
  * momentum distribution takes bar_d1 on the even parts and bar_d2 on the odd parts and
  * (rho u) = sum_j c_j fbar_j.  Expanding the shifts with Eq. (2-5) turns this into
  * Eq. (2-2-1b) with the zeroth-order set equal to the even set (momentum: to bar_d2). */
-static void node_mesofd_trt(const or_problem* P, const or_lat* L, const double* levs[2], long long N,
-                            long long idx, double* out) {
+static void node_mesofd_trt(const or_problem* P, const or_lat* L, const double* levs[2], const double* srcs[2],
+                            long long N, long long idx, double* out) {
+    (void)srcs;  /* no source terms in this form */
     int nf = nfields(P, L);
     double fj[OR_QMAX], fbarj[OR_QMAX];
     for (int j = 0; j < L->b; ++j) {
@@ -392,8 +448,8 @@ static void node_mesofd_trt(const or_problem* P, const or_lat* L, const double* 
     for (int d = 1; d < nf; ++d) out[d] = m[d - 1] / P->rho0;
 }
 
-typedef void (*node_fn)(const or_problem*, const or_lat*, const double* [2], long long, long long,
-                        double*);
+typedef void (*node_fn)(const or_problem*, const or_lat*, const double* [2], const double* [2], long long,
+                        long long, double*);
 
 static node_fn pick(int form) {
     switch (form) {
@@ -413,6 +469,17 @@ static int check(const or_problem* P, or_lat* L) {
     for (int a = 0; a < 3; ++a) if (P->n[a] < 1) return OR_EARG;
     if (L->dim == 2 && P->n[2] != 1) return OR_EARG;
     if (P->pde == OR_NSE && P->rho0 == 0.0) return OR_EARG;
+    if (P->src_mode < OR_SRC_NONE || P->src_mode > OR_SRC_SM) return OR_EARG;
+    if (P->src_mode && (P->pde == OR_NSE || !(P->dt > 0.0))) return OR_EARG;
+    if (P->src_mode == OR_SRC_SU && P->pde != OR_LCDE) return OR_EARG;
+    return OR_OK;
+}
+
+/* Sources needed by a step: level t always, level t - dt for three-level problems. */
+static int check_src(const or_problem* P, int form, const double* src_n, const double* src_nm1) {
+    if (!P->src_mode) return OR_OK;
+    if (form == OR_FORM_MESOFD_TRT || !src_n) return OR_EARG;
+    if (P->levels == 3 && !src_nm1) return OR_EARG;
     return OR_OK;
 }
 
@@ -461,46 +528,62 @@ int or_set_threads(int n) {
 #endif
 }
 
-/* One step: out (nf x N, SoA) from lev_n (level t) and lev_nm1 (level t - dt; ignored when
- * levels == 2). */
-int or_step(const or_problem* P, int form, const double* lev_n, const double* lev_nm1, double* out) {
+/* One step with source terms: out (nf x N, SoA) from lev_n (level t) and lev_nm1 (level t - dt;
+ * ignored when levels == 2); src_n / src_nm1 the source fields (nsrc x N) at the same two
+ * times (NULL when src_mode is 0; src_nm1 ignored when levels == 2). */
+int or_step_src(const or_problem* P, int form, const double* lev_n, const double* lev_nm1,
+                const double* src_n, const double* src_nm1, double* out) {
     or_lat L;
     if (check(P, &L) != OR_OK) return OR_EARG;
     node_fn fn = pick(form);
     if (!fn) return OR_EARG;
     if (P->levels == 3 && !lev_nm1) return OR_EARG;
+    if (check_src(P, form, src_n, src_nm1) != OR_OK) return OR_EARG;
     const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
     const int nf = nfields(P, &L);
     const double* levs[2] = {lev_n, lev_nm1};
+    const double* srcs[2] = {src_n, src_nm1};
 #pragma omp parallel for schedule(static)
     for (long long idx = 0; idx < N; ++idx) {
         double o[4];
-        fn(P, &L, levs, N, idx, o);
+        fn(P, &L, levs, srcs, N, idx, o);
         for (int i = 0; i < nf; ++i) out[i * N + idx] = o[i];
     }
     return OR_OK;
 }
 
+int or_step(const or_problem* P, int form, const double* lev_n, const double* lev_nm1, double* out) {
+    return or_step_src(P, form, lev_n, lev_nm1, 0, 0, out);
+}
+
 /* The step's outputs at a list of node indices only (out is count x nf, node-major). */
-int or_step_nodes(const or_problem* P, int form, const double* lev_n, const double* lev_nm1,
-                  const long long* nodes, long long count, double* out) {
+int or_step_nodes_src(const or_problem* P, int form, const double* lev_n, const double* lev_nm1,
+                      const double* src_n, const double* src_nm1, const long long* nodes, long long count,
+                      double* out) {
     or_lat L;
     if (check(P, &L) != OR_OK) return OR_EARG;
     node_fn fn = pick(form);
     if (!fn) return OR_EARG;
+    if (check_src(P, form, src_n, src_nm1) != OR_OK) return OR_EARG;
     const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
     const int nf = nfields(P, &L);
     const double* levs[2] = {lev_n, lev_nm1};
+    const double* srcs[2] = {src_n, src_nm1};
     for (long long i = 0; i < count; ++i) {
         if (nodes[i] < 0 || nodes[i] >= N) return OR_EARG;
     }
 #pragma omp parallel for schedule(static)
     for (long long i = 0; i < count; ++i) {
         double o[4];
-        fn(P, &L, levs, N, nodes[i], o);
+        fn(P, &L, levs, srcs, N, nodes[i], o);
         for (int f = 0; f < nf; ++f) out[i * nf + f] = o[f];
     }
     return OR_OK;
+}
+
+int or_step_nodes(const or_problem* P, int form, const double* lev_n, const double* lev_nm1,
+                  const long long* nodes, long long count, double* out) {
+    return or_step_nodes_src(P, form, lev_n, lev_nm1, 0, 0, nodes, count, out);
 }
 
 /* nsteps steps in place: on return lev_n holds level t + nsteps dt and lev_nm1 (three-level)
@@ -508,6 +591,7 @@ int or_step_nodes(const or_problem* P, int form, const double* lev_n, const doub
 int or_run(const or_problem* P, int form, long long nsteps, double* lev_n, double* lev_nm1) {
     or_lat L;
     if (check(P, &L) != OR_OK) return OR_EARG;
+    if (P->src_mode) return OR_EARG;  /* sources: step by step with or_step_src */
     const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
     const int nf = nfields(P, &L);
     double* tmp = (double*)malloc(sizeof(double) * (size_t)(nf * N));
@@ -530,6 +614,7 @@ int or_run(const or_problem* P, int form, long long nsteps, double* lev_n, doubl
 int or_lbgk_tau1_run(const or_problem* P, long long nsteps, double* fields) {
     or_lat L;
     if (check(P, &L) != OR_OK) return OR_EARG;
+    if (P->src_mode) return OR_EARG;
     const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
     const int nf = nfields(P, &L);
     double* f = (double*)malloc(sizeof(double) * (size_t)(L.b * N));
@@ -580,6 +665,7 @@ int or_lbgk_tau1_run(const or_problem* P, long long nsteps, double* fields) {
 int or_trt_run(const or_problem* P, double s_minus, long long nsteps, double* fields) {
     or_lat L;
     if (check(P, &L) != OR_OK) return OR_EARG;
+    if (P->src_mode) return OR_EARG;
     const double s_plus = 2.0 - s_minus;
     const long long N = (long long)P->n[0] * P->n[1] * P->n[2];
     const int nf = nfields(P, &L);

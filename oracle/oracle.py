@@ -27,6 +27,7 @@ SRC = os.path.join(HERE, "mmfd_oracle.c")
 LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q19": 3}
 PDES = {"LCDE": 0, "NCDE": 1, "NSE": 2}
 FORMS = {"mesofd": 1, "mmfd": 2, "central": 3, "mesofd_trt": 4}
+SOURCES = {"none": 0, "s": 1, "su": 2, "sm": 3}
 LATTICE_DIM = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q19": 3}
 
 _lock = threading.Lock()
@@ -57,6 +58,7 @@ class _Problem(C.Structure):
         ("two_sets", C.c_int),
         ("d2", (C.c_double * 3) * 2), ("d1", (C.c_double * 3) * 2),
         ("bar_d2", (C.c_double * 3) * 2), ("bar_d1", (C.c_double * 3) * 2),
+        ("dt", C.c_double), ("src_mode", C.c_int), ("b", C.c_double * 3), ("bhat", C.c_double * 3),
     ]
 
 
@@ -75,6 +77,8 @@ def lib():
             L.or_set_threads.argtypes = [C.c_int]
             L.or_step.argtypes = [pp, C.c_int, dp, dp, dp]
             L.or_step_nodes.argtypes = [pp, C.c_int, dp, dp, C.POINTER(C.c_longlong), C.c_longlong, dp]
+            L.or_step_src.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp]
+            L.or_step_nodes_src.argtypes = [pp, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_longlong), C.c_longlong, dp]
             L.or_run.argtypes = [pp, C.c_int, C.c_longlong, dp, dp]
             L.or_lbgk_tau1_run.argtypes = [pp, C.c_longlong, dp]
             L.or_trt_run.argtypes = [pp, C.c_double, C.c_longlong, dp]
@@ -103,6 +107,10 @@ class Problem:
     f^eq,+ of the phi / rho moment), "d1" (first-difference term on f^eq,-), and for the NSE
     momentum "bar_d2" (second difference on f^eq,-) and "bar_d1" (first difference on f^eq,+).
     a / ahat (abar / abarhat) keep the zeroth-order term.
+    source: "none", or the source distribution F_j = g_j^eq(S, M_1F, 0) of Eq. (SourceF) with
+    M_1F = 0 ("s"), M_1F = S u ("su", LCDE: the F_j of Example 1) or M_1F given as fields
+    ("sm"); b / bhat: the b_k of level t and t - dt (Eq. (2-1) / (3layer-1)); dt: the time step
+    that multiplies them.
     """
     lattice: str
     pde: str
@@ -120,6 +128,10 @@ class Problem:
     m2: Sequence[float] = field(default_factory=lambda: [0.0] * 5)
     rho0: float = 1.0
     sets: Optional[dict] = None
+    dt: float = 0.0
+    source: str = "none"
+    b: Sequence[float] = (0.0, 0.0, 0.0)
+    bhat: Sequence[float] = (0.0, 0.0, 0.0)
 
     @property
     def dim(self) -> int:
@@ -128,6 +140,10 @@ class Problem:
     @property
     def nf(self) -> int:
         return 1 + self.dim if self.pde == "NSE" else 1
+
+    @property
+    def nsrc(self) -> int:
+        return {"none": 0, "s": 1, "su": 1, "sm": 1 + self.dim}[self.source]
 
     @property
     def shape(self):
@@ -156,6 +172,10 @@ class Problem:
                 arr = getattr(p, name)
                 for l in range(2):
                     arr[l] = (C.c_double * 3)(*_arr3(lv[l]))
+        p.dt = float(self.dt)
+        p.src_mode = SOURCES[self.source]
+        p.b = (C.c_double * 3)(*_arr3(self.b))
+        p.bhat = (C.c_double * 3)(*_arr3(self.bhat))
         return p
 
 
@@ -219,31 +239,63 @@ def feq(prob: Problem, node_fields: Sequence[float]) -> np.ndarray:
     return out[: E.shape[0]].copy()
 
 
+def _pack_src(prob: Problem, src):
+    """(level t, level t - dt) source fields -> two packed buffers (or None)."""
+    if prob.source == "none":
+        return None, None
+    if src is None:
+        raise ValueError("this problem has source terms: pass src=(fields at t, fields at t - dt)")
+    s0 = _pack(src[0], prob.nsrc, prob.shape)
+    s1 = _pack(src[1], prob.nsrc, prob.shape) if (len(src) > 1 and src[1] is not None) else np.zeros_like(s0)
+    return s0, s1
+
+
+def _ptr(b):
+    return _dp(b) if b is not None else None
+
+
 def step(prob: Problem, level_n: Sequence[np.ndarray], level_nm1: Optional[Sequence[np.ndarray]] = None,
-         form: str = "mmfd") -> List[np.ndarray]:
-    """One explicit MMFD step; returns the new level as a list of fields."""
+         form: str = "mmfd", src=None) -> List[np.ndarray]:
+    """One explicit MMFD step; returns the new level as a list of fields.
+
+    src: for problems with source terms, (source fields at t, source fields at t - dt), each a
+    list of prob.nsrc arrays (the second may be None for two-level problems)."""
     bn = _pack(level_n, prob.nf, prob.shape)
     bm = _pack(level_nm1, prob.nf, prob.shape) if level_nm1 is not None else np.zeros_like(bn)
+    s0, s1 = _pack_src(prob, src)
     out = np.empty_like(bn)
     p = prob.to_c()
-    rc = lib().or_step(C.byref(p), FORMS[form], _dp(bn), _dp(bm), _dp(out))
+    rc = lib().or_step_src(C.byref(p), FORMS[form], _dp(bn), _dp(bm), _ptr(s0), _ptr(s1), _dp(out))
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return _unpack(out)
 
 
-def step_nodes(prob: Problem, level_n, level_nm1, nodes: np.ndarray, form: str = "mmfd") -> np.ndarray:
+def step_nodes(prob: Problem, level_n, level_nm1, nodes: np.ndarray, form: str = "mmfd", src=None) -> np.ndarray:
     """Outputs of one step at the given flat node indices; returns (count, nf)."""
     bn = _pack(level_n, prob.nf, prob.shape)
     bm = _pack(level_nm1, prob.nf, prob.shape) if level_nm1 is not None else np.zeros_like(bn)
+    s0, s1 = _pack_src(prob, src)
     idx = np.ascontiguousarray(nodes, dtype=np.int64)
     out = np.empty((idx.size, prob.nf))
     p = prob.to_c()
-    rc = lib().or_step_nodes(C.byref(p), FORMS[form], _dp(bn), _dp(bm),
-                             idx.ctypes.data_as(C.POINTER(C.c_longlong)), idx.size, _dp(out))
+    rc = lib().or_step_nodes_src(C.byref(p), FORMS[form], _dp(bn), _dp(bm), _ptr(s0), _ptr(s1),
+                                 idx.ctypes.data_as(C.POINTER(C.c_longlong)), idx.size, _dp(out))
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return out
+
+
+def run_source(prob: Problem, level_n, level_nm1, nsteps: int, source, form: str = "mmfd"):
+    """nsteps steps of a problem with source terms; source(m) gives the source fields at time
+    t0 + m dt (m = 0 is the time of level_n, m = -1 that of level_nm1).  Returns (level at the
+    end, level before it)."""
+    cur = [np.asarray(f, dtype=np.float64) for f in level_n]
+    prev = [np.asarray(f, dtype=np.float64) for f in level_nm1] if level_nm1 is not None else None
+    for m in range(int(nsteps)):
+        new = step(prob, cur, prev, form=form, src=(source(m), source(m - 1)))
+        prev, cur = cur, new
+    return cur, (prev if prob.levels == 3 else None)
 
 
 def run(prob: Problem, level_n, level_nm1=None, nsteps: int = 1, form: str = "mmfd"):

@@ -173,7 +173,7 @@ def problem_lcde(lattice: str, levels: int, n, dt: float, dx, K, u, a: Triple,
             cs2_i = (-A10 * K[i, i] / dt + (A21 - A20) * uu[i, i]) / A22
             d0v[i] = cs2_i / c[i] ** 2
     return Problem(lattice=lattice, pde="LCDE", levels=levels, n=n, c=c, d0=d0v, a=a, ahat=ahat,
-                   u=uv, Cmat=Cmat.ravel())
+                   u=uv, Cmat=Cmat.ravel(), dt=dt)
 
 
 def effective_diffusion(lattice: str, levels: int, dt: float, K, u, a: Triple,
@@ -213,7 +213,7 @@ def problem_ncde(lattice: str, levels: int, n, dt: float, dx, flux_poly, diff_po
     for p, v in enumerate(diff_poly):
         m2[p + 1] = -A10 * v / ((p + 1) * A22 * dt)
     return Problem(lattice=lattice, pde="NCDE", levels=levels, n=n, c=c, d0=d0v, a=a, ahat=ahat,
-                   flux=flux, m2=m2)
+                   flux=flux, m2=m2, dt=dt)
 
 
 def problem_nse(lattice: str, levels: int, n, dt: float, dx, a: Triple, abar: Triple,
@@ -226,7 +226,7 @@ def problem_nse(lattice: str, levels: int, n, dt: float, dx, a: Triple, abar: Tr
     d0v = list(d0) if d0 is not None else [1.0 / 3.0] * dim
     d0v = (d0v + [0.0] * 3)[:3]
     return Problem(lattice=lattice, pde="NSE", levels=levels, n=n, c=c, d0=d0v, a=a, ahat=ahat,
-                   abar=abar, abarhat=abarhat, rho0=rho0)
+                   abar=abar, abarhat=abarhat, rho0=rho0, dt=dt)
 
 
 def nse_viscosity(levels: int, abar: Triple, abarhat: Triple, dt: float, cs2: float) -> float:

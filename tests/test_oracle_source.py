@@ -1,0 +1,186 @@
+"""Pins of the oracle's source terms (CPU only): the b_kq F_j terms of Eq. (2-1) / (3layer-1)
+with the source distribution F_j = g_j^eq(S, M_1F, 0) of Eq. (SourceF).
+
+- The three forms (MesoFD per direction, direct MMFD, central Eq. (3layerMMFD-2)) agree.
+- Mass balance, exact on a periodic grid: differences sum to zero and sum_j F_j = S, so
+      sum_x phi^{new} = sum_l A_0^l sum_x phi_l + dt sum_l B_0^l sum_x S_l.
+- For the linear CDE the update with sources is linear and shift-invariant; written out
+  independently here in Fourier space from Eq. (2-1):
+      phi^{new} = sum_l [ A_l(theta) phi_l + dt beta_l(theta) S_l + dt sum_a gamma_la(theta) M_la ]
+  with A_l = sum_k a_kl sum_j ubar_j e^{i k theta.e_j}, beta_l = sum_k b_kl sum_j g_j^eq(1, 0, 0) e^{...}
+  and gamma_la the same with g_j^eq(0, e_a, 0) (S u folds into beta with g^eq(1, u, 0)).
+- Example 1 (isotropic CDE with the source R, D2Q9, Cases 1-3, b_{-1} = 3/2, bhat_{-1} = -1/2):
+  second-order convergence against the exact solution (the printed GRE values are not
+  reproduced under any reading; the order is pinned).
+"""
+import numpy as np
+import pytest
+
+from oracle import fourier as F
+from oracle import oracle as orc
+from oracle import params as P
+
+TWO = (0.95, 0.1, -0.05)
+THREE_A, THREE_AH = (7 / 8, 0.0, 1 / 8), (1 / 8, 0.0, -1 / 8)
+B2 = (0.8, 0.1, 0.1)
+B3, B3H = (1.2, 0.1, 0.2), (-0.4, 0.0, -0.1)
+
+
+def _problem(lat, pde, levels, n, source):
+    dim = 2 if lat.startswith("D2") else 3
+    dt, dx = 0.8, [1.0, 1.1, 0.9][:dim]
+    a = TWO if levels == 2 else THREE_A
+    ah = (0.0, 0.0, 0.0) if levels == 2 else THREE_AH
+    if pde == "LCDE":
+        K = np.diag([0.05, 0.04, 0.06][:dim])
+        if lat in ("D2Q9", "D3Q19"):
+            K = K + 0.006 * (1 - np.eye(dim))
+        prob = P.problem_lcde(lat, levels, n, dt, dx, K, [0.08, -0.05, 0.04][:dim], a, ah)
+    else:
+        flux = [[0, 0.05, 0.1, 0], [0, -0.03, 0.1, 0], [0, 0, 0.06, 0.02]][:dim]
+        prob = P.problem_ncde(lat, levels, n, dt, dx, flux, [0.15, 0, 0.05], a, ah)
+    prob.source = source
+    prob.b = B2 if levels == 2 else B3
+    prob.bhat = (0.0, 0.0, 0.0) if levels == 2 else B3H
+    return prob
+
+
+def _fields(prob, rng, count, base=0.5):
+    return [base + 0.2 * rng.standard_normal(prob.shape) for _ in range(count)]
+
+
+def _sources(prob, rng):
+    return _fields(prob, rng, prob.nsrc, 0.3), _fields(prob, rng, prob.nsrc, 0.3)
+
+
+COMBOS = [("D2Q5", "LCDE", 2, "s"), ("D2Q9", "LCDE", 2, "su"), ("D2Q9", "LCDE", 3, "su"),
+          ("D2Q9", "LCDE", 3, "sm"), ("D2Q9", "NCDE", 2, "sm"), ("D2Q9", "NCDE", 3, "s"),
+          ("D3Q7", "LCDE", 3, "su"), ("D3Q19", "LCDE", 2, "sm"), ("D3Q19", "NCDE", 3, "sm")]
+
+
+def _n(lat):
+    return [7, 6] if lat.startswith("D2") else [5, 4, 3]
+
+
+@pytest.mark.parametrize("lat,pde,levels,source", COMBOS)
+def test_three_forms_agree_with_sources(lat, pde, levels, source):
+    rng = np.random.default_rng(41)
+    prob = _problem(lat, pde, levels, _n(lat), source)
+    L0 = _fields(prob, rng, 1)
+    L1 = _fields(prob, rng, 1) if levels == 3 else None
+    src = _sources(prob, rng)
+    outs = [orc.step(prob, L0, L1, form=f, src=src)[0] for f in ("mesofd", "mmfd", "central")]
+    scale = np.abs(outs[1]).max()
+    assert np.abs(outs[0] - outs[1]).max() < 1e-13 * scale
+    assert np.abs(outs[2] - outs[1]).max() < 1e-13 * scale
+    # the source changes the answer, by dt times an O(1) amount
+    none = orc.step(_problem(lat, pde, levels, _n(lat), "none"), L0, L1)[0]
+    assert np.abs(outs[1] - none).max() > 0.05 * prob.dt * 0.3
+
+
+@pytest.mark.parametrize("lat,pde,levels,source", COMBOS)
+def test_mass_balance_with_sources(lat, pde, levels, source):
+    rng = np.random.default_rng(42)
+    prob = _problem(lat, pde, levels, _n(lat), source)
+    L0 = _fields(prob, rng, 1)
+    L1 = _fields(prob, rng, 1) if levels == 3 else None
+    src = _sources(prob, rng)
+    out = orc.step(prob, L0, L1, form="central", src=src)[0]
+    expect = sum(prob.a) * L0[0].sum() + prob.dt * sum(prob.b) * src[0][0].sum()
+    if levels == 3:
+        expect += sum(prob.ahat) * L1[0].sum() + prob.dt * sum(prob.bhat) * src[1][0].sum()
+    assert abs(out.sum() - expect) < 1e-12 * np.abs(out).sum()
+
+
+def _symbol(prob, coeffs, g, shape):
+    """sum_k c_k sum_j g_j exp(i k theta . e_j) on the grid's wave numbers."""
+    E, _, _ = orc.lattice(prob.lattice, prob.d0, prob.c)
+    th = F.thetas(shape)
+    dim = len(shape)
+    out = np.zeros(shape, dtype=complex)
+    for k, ck in zip((-1, 0, 1), coeffs):
+        for j in range(E.shape[0]):
+            ph = sum(th[i] * E[j][dim - 1 - i] for i in range(dim))
+            out += ck * g[j] * np.exp(1j * k * ph)
+    return out
+
+
+@pytest.mark.parametrize("lat,levels,source", [("D2Q9", 2, "su"), ("D2Q9", 3, "su"), ("D2Q5", 3, "s"),
+                                                ("D2Q9", 3, "sm"), ("D3Q7", 2, "sm")])
+def test_lcde_with_sources_is_its_fourier_update(lat, levels, source):
+    rng = np.random.default_rng(43)
+    n = [12, 10] if lat.startswith("D2") else [6, 5, 4]
+    prob = _problem(lat, "LCDE", levels, n, source)
+    shape = prob.shape
+    L0 = _fields(prob, rng, 1)
+    L1 = _fields(prob, rng, 1) if levels == 3 else None
+    src = _sources(prob, rng)
+    out = orc.step(prob, L0, L1, form="central", src=src)[0]
+    ub = F.ubar(prob)
+    zero = [0.0, 0.0, 0.0]
+    if source == "su":
+        gS = orc.geq(prob.lattice, prob.d0, prob.c, 1.0, list(prob.u), [0.0] * 9)
+    else:
+        gS = orc.geq(prob.lattice, prob.d0, prob.c, 1.0, zero, [0.0] * 9)
+    gM = []
+    for a in range(prob.dim):
+        e = [0.0, 0.0, 0.0]
+        e[a] = 1.0
+        gM.append(orc.geq(prob.lattice, prob.d0, prob.c, 0.0, e, [0.0] * 9))
+    levels_in = [(prob.a, prob.b, L0, src[0])]
+    if levels == 3:
+        levels_in.append((prob.ahat, prob.bhat, L1, src[1]))
+    acc = np.zeros(shape, dtype=complex)
+    for a_l, b_l, lev, s_l in levels_in:
+        acc += _symbol(prob, a_l, ub, shape) * np.fft.fftn(lev[0])
+        acc += prob.dt * _symbol(prob, b_l, gS, shape) * np.fft.fftn(s_l[0])
+        if source == "sm":
+            for a in range(prob.dim):
+                acc += prob.dt * _symbol(prob, b_l, gM[a], shape) * np.fft.fftn(s_l[1 + a])
+    exact = np.real(np.fft.ifftn(acc))
+    assert np.abs(out - exact).max() < 1e-13 * np.abs(exact).max()
+
+
+# ----------------------------------------------------------------------------- Example 1
+
+EX1_CASES = {
+    1: ((1.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
+    2: ((7 / 8, 1 / 4, -1 / 8), (1 / 8, -1 / 4, 1 / 8)),   # â_1 = +1/8 (Eq. (X); the text's sign breaks A_00 = 1)
+    3: ((7 / 8, 0.0, 1 / 8), (1 / 8, 0.0, -1 / 8)),
+}
+
+
+def example1_gre(case, nx_per_unit, nt_per_unit):
+    """GRE at T = 1 of Example 1 on [0, 2]^2 (periodic, period 2), Delta x = 1/N_x,
+    Delta t = 1/N_t, kappa = c_s^2 Delta t / 2 (beta = 1, the EDF of the example)."""
+    dx, dt = 1.0 / nx_per_unit, 1.0 / nt_per_unit
+    n = 2 * nx_per_unit
+    c = dx / dt
+    kappa = c * c / 3.0 * dt / 2.0
+    u = (0.1, 0.1)
+    a, ah = EX1_CASES[case]
+    prob = P.problem_lcde("D2Q9", 3, [n, n], dt, [dx, dx], kappa * np.eye(2), u, a, ah)
+    prob.source, prob.b, prob.bhat = "su", (1.5, 0.0, 0.0), (-0.5, 0.0, 0.0)
+    x = np.arange(n) * dx
+    X, Y = np.meshgrid(x, x, indexing="xy")        # numpy shape (ny, nx)
+    g = 1.0 - 2.0 * np.pi ** 2 * kappa
+
+    def exact(t):
+        return np.exp(g * t) * np.sin(np.pi * (X + Y))
+
+    def R(m):
+        t = m * dt
+        return [np.exp(g * t) * (np.sin(np.pi * (X + Y)) + np.pi * (u[0] + u[1]) * np.cos(np.pi * (X + Y)))]
+
+    out, _ = orc.run_source(prob, [exact(0.0)], [exact(-dt)], nt_per_unit, R)
+    ref = exact(1.0)
+    return float(np.abs(out[0] - ref).sum() / np.abs(ref).sum())
+
+
+@pytest.mark.parametrize("case", [1, 2, 3])
+def test_example1_second_order(case):
+    # N_x / N_t pairs of Table 1 (Delta t proportional to Delta x^2)
+    gre = [example1_gre(case, nx, nt) for nx, nt in [(10, 6), (20, 24), (40, 96)]]
+    orders = [np.log2(gre[i] / gre[i + 1]) for i in range(2)]
+    assert all(o >= 1.8 for o in orders), (gre, orders)
+    assert gre[-1] < 2e-2
