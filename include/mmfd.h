@@ -45,6 +45,9 @@ typedef enum { MMFD_FP64 = 0, MMFD_FP32 = 1, MMFD_BF16 = 2 } mmfd_storage;
 enum { MMFD_HOST = 0, MMFD_DEVICE = 1 };
 enum { MMFD_DT_F64 = 0, MMFD_DT_F32 = 1 };          /* element type of user buffers */
 enum { MMFD_COEF_EXPLICIT = 0, MMFD_COEF_TARGETS = 1 };
+/* Source distribution F_j = g_j^eq(S, M_1F, 0) (Eq. (SourceF)) of the source terms of Eq. (2-1):
+ * none; M_1F = 0; M_1F = S u (LCDE, with its u: the F_j of Example 1); or M_1F given as fields. */
+enum { MMFD_SRC_NONE = 0, MMFD_SRC_S = 1, MMFD_SRC_SU = 2, MMFD_SRC_SM = 3 };
 
 #define MMFD_FLAG_ALLOW_UNSTABLE 0x1u   /* skip the create-time stability rejection */
 #define MMFD_FLAG_DROP_OFFDIAG 0x2u     /* axis lattices: drop K_xy (solve with diag(K)) */
@@ -100,6 +103,15 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *  seed                  BF16 stochastic-rounding seed.
  *  stream                cudaStream_t (NULL = legacy default stream).
  *  alloc/free_fn/ctx     device allocator for the level buffers (NULL = cudaMalloc/cudaFree).
+ *  source, b, bhat       source terms of Eq. (2-1) / (3layer-1): the update gains
+ *                        dt sum_j sum_k [ b_k F_j(x + k c_j dt, t) + bhat_k F_j(x + k c_j dt, t - dt) ]
+ *                        with F_j = g_j^eq(S, M_1F, 0) (Eq. (SourceF)); source = MMFD_SRC_*
+ *                        (LCDE / NCDE only; MMFD_SRC_SU: LCDE only).  b, bhat are (b_{-1}, b_0,
+ *                        b_1); bhat is for three-level solvers (it must be zero for two-level
+ *                        ones).  b = bhat = 0 selects the defaults b = (1, 0, 0) (two-level) and
+ *                        b = (3/2, 0, 0), bhat = (-1/2, 0, 0) (three-level, as in Sec. III.C and
+ *                        Example 1).  The source fields are set with mmfd_set_source.  A solver
+ *                        with sources runs unblocked (temporal_depth 1).
  */
 typedef struct {
     int pde, lattice, levels;
@@ -126,6 +138,8 @@ typedef struct {
     mmfd_alloc_fn alloc;
     mmfd_free_fn free_fn;
     void* alloc_ctx;
+    int source;
+    double b[3], bhat[3];
 } mmfd_desc;
 
 /* Derived constants of a created solver (read-only view, for checking and reporting). */
@@ -167,6 +181,18 @@ int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
  * unchanged until the stream has passed this call; pageable host buffers are staged first.  Setting level 0 of a three-level solver also sets level 1
  * to the same values (the equilibrium start) unless level 1 is set afterwards. */
 int mmfd_set_fields(mmfd_solver* s, int level, const void* const* fields, int where, int dtype);
+
+/* Source fields of a solver created with a source (Eq. (2-1), F_j = g_j^eq(S, M_1F, 0) of
+ * Eq. (SourceF)).  level 0 is the source at t_n (the current level), 1 at t_{n-1} (three-level
+ * only).  fields: S, then, for MMFD_SRC_SM, the dim components of M_1F; each a dense nx*ny*nz
+ * array as in mmfd_set_fields (same transfer rules).  The solver keeps them in FP64 (FP64
+ * storage) or FP32 (otherwise).  Time levels: a step uses the sources of levels 0 and 1;
+ * afterwards level 1 holds what level 0 held and level 0 keeps its values, so a source stays
+ * constant in time until it is replaced -- a time-dependent source is set (level 0) before
+ * every step.  Before the first step after creation or after mmfd_set_fields(level 0), setting
+ * level 0 also sets level 1 unless level 1 is set explicitly.  Both levels start at zero.
+ * MMFD_ERR_STATE if the solver has no source. */
+int mmfd_set_source(mmfd_solver* s, int level, const void* const* fields, int where, int dtype);
 
 /* Advance nsteps time levels (Eq. (2-2-2) / Eq. (3layerMMFD-1)), asynchronously on the
  * solver's stream. */

@@ -18,15 +18,42 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
+// Source term of level l at node c0 (weights folded on the host, see SrcCoef): SRC 1 reads S
+// only (M_1F = 0 or S u), SRC 2 also the M_1F components.  Source levels are read-only for
+// the whole launch, so they go through the read-only data path.
+template <int LAT, int SRC, typename T>
+__device__ __forceinline__ T source_level(const Geom& g, const T* __restrict__ src, const SrcCoef<T>& w, int l,
+                                          long long c0) {
+    constexpr int NP = lat_npair(LAT);
+    constexpr int D = lat_dim(LAT);
+    T acc = w.W0[l] * __ldg(src + c0);
+    static_for<0, NP>([&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        const long long off = pair_offset<LAT>(g, P);
+        acc += w.Wp[l][P] * __ldg(src + c0 + off) + w.Wm[l][P] * __ldg(src + c0 - off);
+        if constexpr (SRC == 2) {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (pair_e(LAT, P, a) != 0) {
+                    const T* m = src + (long long)(1 + a) * g.fs;
+                    acc += w.M[l][P][a] * (__ldg(m + c0 + off) - __ldg(m + c0 - off));
+                }
+        }
+    });
+    return acc;
+}
+
 // The update of one node (x, y, z): reads levels t (in0) and t - dt (in1) in the ghosted
 // layout, writes level t + dt (out) and its periodic ghost images.  Shared by the one-solve
 // kernel below and the batched multi-request kernel, so a request computes the same bits
 // alone and inside a batch.
-template <int LAT, int PDE, int LEVELS, int ST>
+// With SRC != 0 the source terms of `sa` are added before the store.
+template <int LAT, int PDE, int LEVELS, int ST, int SRC = 0>
 __device__ __forceinline__ void direct_node(const Geom& g, const void* __restrict__ in0v,
                                             const void* __restrict__ in1v, void* __restrict__ outv,
                                             const Coef<typename Storage<ST>::T>& cf, const StepExtra& ex,
-                                            int x, int y, int z) {
+                                            int x, int y, int z,
+                                            const SrcArgs<typename Storage<ST>::T>* sa = nullptr) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
@@ -86,6 +113,10 @@ __device__ __forceinline__ void direct_node(const Geom& g, const void* __restric
             });
         }
     }
+    if constexpr (SRC != 0) {
+#pragma unroll
+        for (int l = 0; l < LEVELS - 1; ++l) acc[0] += source_level<LAT, SRC, T>(g, sa->s[l], sa->w, l, c0);
+    }
     S* out = static_cast<S*>(outv);
     const long long node = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
@@ -113,6 +144,32 @@ cudaError_t launch_direct(const LaunchArgs& a) {
     dim3 grid((a.g.nx + block.x - 1) / block.x, (a.g.ny + block.y - 1) / block.y, a.g.nz);
     k_direct<LAT, PDE, LEVELS, ST><<<grid, block, 0, a.stream>>>(a.g, a.in0, a.in1, a.out,
                                                                   *static_cast<const Coef<T>*>(a.coef), a.ex);
+    return cudaGetLastError();
+}
+
+template <int LAT, int PDE, int LEVELS, int ST, int SRC>
+__global__ void __launch_bounds__(256) k_direct_src(Geom g, const void* __restrict__ in0v,
+                                                    const void* __restrict__ in1v, void* __restrict__ outv,
+                                                    Coef<typename Storage<ST>::T> cf, StepExtra ex,
+                                                    const __grid_constant__ SrcArgs<typename Storage<ST>::T> sa) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    direct_node<LAT, PDE, LEVELS, ST, SRC>(g, in0v, in1v, outv, cf, ex, x, y, z, &sa);
+}
+
+template <int LAT, int PDE, int LEVELS, int ST, int SRC>
+cudaError_t launch_direct_src(const LaunchArgs& a) {
+    using T = typename Storage<ST>::T;
+    SrcArgs<T> sa;
+    sa.s[0] = static_cast<const T*>(a.src[0]);
+    sa.s[1] = static_cast<const T*>(LEVELS == 3 ? a.src[1] : a.src[0]);
+    sa.w = *static_cast<const SrcCoef<T>*>(a.src_coef);
+    dim3 block(64, 4, 1);
+    dim3 grid((a.g.nx + block.x - 1) / block.x, (a.g.ny + block.y - 1) / block.y, a.g.nz);
+    k_direct_src<LAT, PDE, LEVELS, ST, SRC><<<grid, block, 0, a.stream>>>(
+        a.g, a.in0, a.in1, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, sa);
     return cudaGetLastError();
 }
 

@@ -28,11 +28,15 @@ struct LaunchArgs {
     const TmapSet* maps;  // TMA descriptors of the input levels (march / blocked kernels)
     int H;                // rows (2D) or planes (3D) per CTA
     int* err;             // device error flag (bounded waits that ran out)
+    const void* src[2];   // source levels t, t - dt (solvers with source terms; else null)
+    const void* src_coef; // SrcCoef<double> or SrcCoef<float> matching the storage type
 };
 using LaunchFn = cudaError_t (*)(const LaunchArgs&);
 
 // One node per thread, neighbours read straight from the ghosted layout (any shape).
 LaunchFn find_direct(int lat, int pde, int levels, int st);
+// The same with source terms: src 1 (a source S, M_1F = 0 or S u folded) or 2 (S and M_1F fields).
+LaunchFn find_direct_src(int lat, int pde, int levels, int st, int src);
 // Row-marching 2D kernels fed by a TMA (cp.async.bulk.tensor) shared-memory ring.
 LaunchFn find_march2d(int lat, int pde, int levels, int st);
 // Input rows per TMA box (stage) of the 2D marching kernel for this PDE; its tensor maps use

@@ -78,6 +78,26 @@ struct Coef {
     T ref[4];                          // BF16 offsets per field
 };
 
+// Source terms of one step (Eq. (2-1) with F_j = g_j^eq(S, M_1F, 0), Eq. (SourceF)), folded on
+// the host from the central form Eq. (3layerMMFD-2) per level l (0: t, 1: t - dt):
+//   dt [ B_0 S(x) + sum_p omega_p ( b+ (S(x+e_p) - 2 S(x) + S(x-e_p))
+//                                   + b- ctilde_p . (M_1F(x+e_p) - M_1F(x-e_p)) ) ]
+// = W0 S(x) + sum_p [ Wp S(x+e_p) + Wm S(x-e_p) + M_p . (M_1F(x+e_p) - M_1F(x-e_p)) ];
+// M_1F = S u (constant u) is folded into Wp / Wm.
+template <typename T>
+struct SrcCoef {
+    T W0[2], Wp[2][kMaxPair], Wm[2][kMaxPair];
+    T M[2][kMaxPair][3];
+};
+
+// Source levels (S, then the M_1F components, one field stride g.fs apart, in the level
+// geometry g, compute type T) and their weights.
+template <typename T>
+struct SrcArgs {
+    const T* s[2];
+    SrcCoef<T> w;
+};
+
 struct StepExtra {
     unsigned long long seed;  // stochastic rounding
     long long step;           // global step index of the level being written

@@ -373,6 +373,55 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
         for (size_t i = 0; i < sizeof(Coef<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
     }
 
+    // ---- source terms (Eq. (2-1); F_j = g_j^eq(S, M_1F, 0), Eq. (SourceF)), folded per level
+    // from the central form Eq. (3layerMMFD-2): omega_p = eA[p], omega_p ctilde_p = oB[p].
+    r.src = d.source;
+    if (d.source < MMFD_SRC_NONE || d.source > MMFD_SRC_SM) return fail(msg, MMFD_ERR_ARG, "unknown source mode");
+    if (d.source != MMFD_SRC_NONE) {
+        if (d.pde == PDE_NSE) return fail(msg, MMFD_ERR_UNSUPPORTED, "source terms: LCDE and NCDE only");
+        if (d.source == MMFD_SRC_SU && d.pde != PDE_LCDE)
+            return fail(msg, MMFD_ERR_ARG, "MMFD_SRC_SU takes the LCDE's velocity u");
+        bool zero = true;
+        for (int k = 0; k < 3; ++k) {
+            if (!finite(d.b[k]) || !finite(d.bhat[k])) return fail(msg, MMFD_ERR_ARG, "non-finite source coefficient");
+            if (d.b[k] != 0.0 || d.bhat[k] != 0.0) zero = false;
+        }
+        if (d.levels == 2 && (d.bhat[0] != 0.0 || d.bhat[1] != 0.0 || d.bhat[2] != 0.0))
+            return fail(msg, MMFD_ERR_ARG, "bhat must be zero for a two-level solver");
+        for (int k = 0; k < 3; ++k) {
+            r.b[k] = d.b[k];
+            r.bhat[k] = d.bhat[k];
+        }
+        if (zero) {
+            r.b[0] = d.levels == 3 ? 1.5 : 1.0;
+            r.bhat[0] = d.levels == 3 ? -0.5 : 0.0;
+        }
+        r.nsrc = d.source == MMFD_SRC_SM ? 1 + dim : 1;
+        SrcCoef<double>& sc = r.sd;
+        std::memset(&sc, 0, sizeof(sc));
+        const double* bl[2] = {r.b, r.bhat};
+        double wsum = 0.0;
+        for (int p = 0; p < NP; ++p) wsum += c.eA[p];
+        for (int l = 0; l < d.levels - 1; ++l) {
+            const double B0 = bl[l][0] + bl[l][1] + bl[l][2];
+            const double bp = bl[l][2] + bl[l][0], bm = bl[l][2] - bl[l][0];
+            sc.W0[l] = d.dt * (B0 - 2.0 * bp * wsum);
+            for (int p = 0; p < NP; ++p) {
+                double cu = 0.0;  // ctilde_p . u (M_1F = S u), per unit omega_p
+                if (d.source == MMFD_SRC_SU)
+                    for (int a = 0; a < dim; ++a) cu += c.oB[p][a] * d.u[a];
+                sc.Wp[l][p] = d.dt * (bp * c.eA[p] + bm * cu);
+                sc.Wm[l][p] = d.dt * (bp * c.eA[p] - bm * cu);
+                if (d.source == MMFD_SRC_SM)
+                    for (int a = 0; a < dim; ++a) sc.M[l][p][a] = d.dt * bm * c.oB[p][a];
+            }
+        }
+        const double* ssrc = reinterpret_cast<const double*>(&r.sd);
+        float* sdst = reinterpret_cast<float*>(&r.sf);
+        static_assert(sizeof(SrcCoef<double>) == 2 * sizeof(SrcCoef<float>), "SrcCoef layout");
+        for (size_t i = 0; i < sizeof(SrcCoef<double>) / sizeof(double); ++i) sdst[i] = (float)ssrc[i];
+    }
+
     // ---- create-time stability check (LCDE: exact symbol on the grid's wave numbers)
     r.max_lambda = -1.0;
     if (d.pde == PDE_LCDE) {
@@ -421,7 +470,9 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
 }
 
 double bytes_per_lu(const Resolved& r) {
-    return (double)storage_bytes(r.st) * r.nf * (r.levels - 1 + 1);
+    // levels read and the one written; source levels (compute type) read once per step
+    const double src = r.src ? (double)(r.st == ST_F64 ? 8 : 4) * r.nsrc * (r.levels - 1) : 0.0;
+    return (double)storage_bytes(r.st) * r.nf * (r.levels - 1 + 1) + src;
 }
 
 }  // namespace mmfd

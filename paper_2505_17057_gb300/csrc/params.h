@@ -22,6 +22,11 @@ struct Resolved {
     double max_lambda;
     Coef<double> cd;
     Coef<float> cf;
+    int src;            // MMFD_SRC_* (0: none)
+    int nsrc;           // source fields per level (S, then M_1F components)
+    double b[3], bhat[3];
+    SrcCoef<double> sd;
+    SrcCoef<float> sf;
 };
 
 // Returns MMFD_OK or an error code; *msg gets a human-readable reason on error.

@@ -579,6 +579,12 @@ int mmfd_submit(mmfd_server* h, const mmfd_desc* d, const void* const* init, int
         s->st.rejected++;
         return set_error(rc, msg);
     }
+    if (q->r->src) {
+        delete q->r;
+        delete q;
+        s->st.rejected++;
+        return set_error(MMFD_ERR_UNSUPPORTED, "the server does not take requests with source terms");
+    }
     q->desc = *d;
     q->g = make_geom(*q->r);
     q->footprint = footprint_of(*q->r, q->g);

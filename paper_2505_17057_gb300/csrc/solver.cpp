@@ -48,6 +48,18 @@ int solver_init_device(Solver* s) {
     }
     int rc = dev_alloc(s, (size_t)(reduce_parts_needed() + 64) * sizeof(double), reinterpret_cast<void**>(&s->d_red));
     if (rc != MMFD_OK) return rc;
+    if (s->r.src) {
+        // two source buffers (levels t_n, t_{n-1}, aliased while equal), zero until set
+        s->src_bytes = (size_t)s->g.fs * s->r.nsrc * (s->r.st == ST_F64 ? 8 : 4);
+        for (int i = 0; i < 2; ++i) {
+            rc = dev_alloc(s, s->src_bytes, &s->srcbuf[i]);
+            if (rc != MMFD_OK) return rc;
+            cudaError_t e = cudaMemsetAsync(s->srcbuf[i], 0, s->src_bytes, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        }
+        s->src_i0 = s->src_i1 = 0;
+        s->src_fresh = true;
+    }
     rc = dev_alloc(s, 256, reinterpret_cast<void**>(&s->d_flag));
     if (rc != MMFD_OK) return rc;
     cudaError_t e = cudaMemsetAsync(s->d_flag, 0, 256, s->stream);
@@ -65,6 +77,10 @@ void solver_free_device(Solver* s) {
     }
     dev_free(s, s->stage);
     s->stage = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        dev_free(s, s->srcbuf[i]);
+        s->srcbuf[i] = nullptr;
+    }
     dev_free(s, s->d_red);
     s->d_red = nullptr;
     dev_free(s, s->d_flag);
@@ -118,6 +134,52 @@ int solver_set_fields(Solver* s, int level, const void* const* fields, int where
         }
     }
     s->fields_set = true;
+    if (level == 0) s->src_fresh = true;
+    return MMFD_OK;
+}
+
+int solver_set_source(Solver* s, int level, const void* const* fields, int where, int dtype) {
+    if (!s->r.src) return set_error(MMFD_ERR_STATE, "the solver was created without a source");
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    if (where != MMFD_HOST && where != MMFD_DEVICE) return set_error(MMFD_ERR_ARG, "where must be HOST or DEVICE");
+    if (level != 0 && !(level == 1 && s->nlev == 3))
+        return set_error(MMFD_ERR_ARG, "level must be 0 (t_n) or, for three-level solvers, 1 (t_{n-1})");
+    // Level 0 while the two levels share a buffer: write the other buffer, so that level 1 keeps
+    // its values -- except before the first step, where level 1 follows level 0 (the sources'
+    // counterpart of the equilibrium start).  Level 1 while shared: split off the other buffer.
+    int idx;
+    if (level == 0) {
+        if (s->src_i0 == s->src_i1 && !s->src_fresh) s->src_i0 = 1 - s->src_i1;
+        idx = s->src_i0;
+    } else {
+        if (s->src_i0 == s->src_i1) s->src_i1 = 1 - s->src_i0;
+        idx = s->src_i1;
+    }
+    Geom gs = s->g;
+    gs.es = s->r.st == ST_F64 ? 8 : 4;
+    const int sst = s->r.st == ST_F64 ? ST_F64 : ST_F32;
+    const size_t esz = dtype == MMFD_DT_F64 ? 8 : 4;
+    const size_t bytes = (size_t)nodes(s) * esz;
+    int rc;
+    if (where == MMFD_HOST && (rc = ensure_stage(s)) != MMFD_OK) return rc;
+    for (int f = 0; f < s->r.nsrc; ++f) {
+        if (!fields[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
+        const void* src = fields[f];
+        if (where == MMFD_HOST) {
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, src) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                pa.devicePointer) {
+                src = pa.devicePointer;
+            } else {
+                cudaGetLastError();
+                cudaError_t e = cudaMemcpyAsync(s->stage, src, bytes, cudaMemcpyHostToDevice, s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+                src = s->stage;
+            }
+        }
+        cudaError_t e = launch_pack(gs, sst, src, dtype, s->srcbuf[idx], f, 0.0, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
+    }
     return MMFD_OK;
 }
 
@@ -135,6 +197,9 @@ void solver_launch_args(Solver* s, LaunchArgs& a) {
     a.H = s->H;
     a.err = s->d_flag;
     a.maps = nullptr;
+    a.src[0] = s->r.src ? s->srcbuf[s->src_i0] : nullptr;
+    a.src[1] = s->r.src ? s->srcbuf[s->src_i1] : nullptr;
+    a.src_coef = s->r.st == ST_F64 ? static_cast<const void*>(&s->r.sd) : static_cast<const void*>(&s->r.sf);
     if (s->use_tma) {
         const int nf = s->g.nf;
         for (int f = 0; f < nf; ++f) {
@@ -167,6 +232,11 @@ int solver_step(Solver* s, long long nsteps) {
             s->cur = s->next();
             s->steps_done += 1;
             done += 1;
+            if (s->r.src) {
+                // the source at t_n becomes the one at t_{n-1}; level 0 keeps it until replaced
+                s->src_i1 = s->src_i0;
+                s->src_fresh = false;
+            }
         }
     }
     return MMFD_OK;
@@ -271,6 +341,13 @@ int solver_pick_kernels(Solver* s) {
     s->variant = 0;
     s->use_tma = false;
     s->fn = nullptr;
+    if (s->r.src) {
+        // source terms: the one-node-per-thread kernels, unblocked
+        s->fn = find_direct_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, s->r.src == MMFD_SRC_SM ? 2 : 1);
+        s->kernel_name = "k_direct_src";
+        if (!s->fn) return set_error(MMFD_ERR_UNSUPPORTED, "no source kernel for this lattice/PDE/levels/storage");
+        return MMFD_OK;
+    }
     const char* force = std::getenv("MMFD_FORCE_KERNEL");
     const bool want_direct = force && std::strcmp(force, "direct") == 0;
     if (s->r.dim == 2 && s->g.nx >= 128 && !want_direct) {

@@ -39,6 +39,10 @@ struct Solver {
     CUtensorMap tmaps[3][4];                     // per level buffer, per field
     TmapSet launch_maps;                         // assembled per launch (inputs of this step)
     int H = 0;                                   // rows / planes per CTA
+    void* srcbuf[2] = {nullptr, nullptr};        // source levels (compute type, ghosted layout)
+    size_t src_bytes = 0;
+    int src_i0 = 0, src_i1 = 0;                  // buffers holding the sources at t_n and t_{n-1}
+    bool src_fresh = true;                       // no step since creation or set_fields(level 0)
 
     int prev() const { return nlev == 2 ? 1 - cur : (cur + 2) % 3; }
     int next() const { return nlev == 2 ? 1 - cur : (cur + 1) % 3; }
@@ -54,6 +58,7 @@ void dev_free(Solver* s, void* p);
 int solver_init_device(Solver* s);
 void solver_free_device(Solver* s);
 int solver_set_fields(Solver* s, int level, const void* const* fields, int where, int dtype);
+int solver_set_source(Solver* s, int level, const void* const* fields, int where, int dtype);
 int solver_step(Solver* s, long long nsteps);
 int solver_get_fields(Solver* s, int level, void* const* out, int where, int dtype);
 int solver_reduce(Solver* s, int what, double* out);

@@ -42,10 +42,12 @@ MMFD_FLAG_DROP_OFFDIAG = 0x2
 MMFD_FLAG_STOCHASTIC_ROUND = 0x4
 MMFD_FLAG_TWO_SETS = 0x8
 MMFD_RED_SUM, MMFD_RED_MAXABS, MMFD_RED_NONFINITE = 0, 1, 2
+MMFD_SRC_NONE, MMFD_SRC_S, MMFD_SRC_SU, MMFD_SRC_SM = 0, 1, 2, 3
 
 PDE = {"LCDE": MMFD_LCDE, "NCDE": MMFD_NCDE, "NSE": MMFD_NSE}
 LATTICE = {"D2Q5": MMFD_D2Q5, "D2Q9": MMFD_D2Q9, "D3Q7": MMFD_D3Q7, "D3Q19": MMFD_D3Q19}
 STORAGE = {"fp64": MMFD_FP64, "fp32": MMFD_FP32, "bf16": MMFD_BF16}
+SOURCE = {"none": MMFD_SRC_NONE, "s": MMFD_SRC_S, "su": MMFD_SRC_SU, "sm": MMFD_SRC_SM}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_int, C.c_size_t, C.POINTER(C.c_void_p), C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -65,6 +67,7 @@ class mmfd_desc(C.Structure):
         ("storage", C.c_int), ("flags", C.c_uint), ("ref", C.c_double * 4), ("temporal_depth", C.c_int),
         ("seed", C.c_ulonglong), ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p),
+        ("source", C.c_int), ("b", C.c_double * 3), ("bhat", C.c_double * 3),
     ]
 
 
@@ -109,6 +112,7 @@ SIGNATURES = {
     "mmfd_desc_init": (C.c_int, [C.POINTER(mmfd_desc)]),
     "mmfd_create": (C.c_int, [C.POINTER(mmfd_desc), _PV]),
     "mmfd_set_fields": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
+    "mmfd_set_source": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
     "mmfd_step": (C.c_int, [_VP, C.c_longlong]),
     "mmfd_fields": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
     "mmfd_reduce": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_double)]),
@@ -220,6 +224,10 @@ def mmfd_set_fields(h: int, level: int, ptrs: Sequence[int], where: int, dtype: 
     check(lib.mmfd_set_fields(h, level, _ptr_array(ptrs), where, dtype), "mmfd_set_fields")
 
 
+def mmfd_set_source(h: int, level: int, ptrs: Sequence[int], where: int, dtype: int) -> None:
+    check(lib.mmfd_set_source(h, level, _ptr_array(ptrs), where, dtype), "mmfd_set_source")
+
+
 def mmfd_step(h: int, nsteps: int) -> None:
     check(lib.mmfd_step(h, int(nsteps)), "mmfd_step")
 
@@ -277,11 +285,14 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
               storage: str = "fp32", K=None, u=None, lambda_bar: float = 1.0, flux=None, diff=None,
               rho0: float = 1.0, a=None, ahat=None, abar=None, abarhat=None, targets=None, targets_bar=None,
               d0=None, flags: int = 0, ref=None, temporal_depth: int = 1, seed: Optional[int] = None,
-              stream: Optional[int] = None, sets: Optional[dict] = None) -> mmfd_desc:
+              stream: Optional[int] = None, sets: Optional[dict] = None, source: str = "none",
+              b=None, bhat=None) -> mmfd_desc:
     """Fill an mmfd_desc (plain field assignment; every derived constant is computed by the library).
 
     sets: the multiple-parameter-set scheme (MMFD_FLAG_TWO_SETS): a dict with "d2", "d1" and,
     for the NSE momentum, "bar_d2", "bar_d1", each a pair of triples (level t, level t - dt).
+    source: "none", "s" (M_1F = 0), "su" (M_1F = S u) or "sm" (M_1F given); b, bhat: the source
+    coefficient triples (None: the library's defaults).
     """
     d = mmfd_desc_init()
     d.pde = PDE[pde]
@@ -344,6 +355,10 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
         for i, v in enumerate(ref):
             d.ref[i] = float(v)
     d.temporal_depth = int(temporal_depth)
+    d.source = SOURCE[source]
+    for i in range(3):
+        d.b[i] = float(b[i]) if b is not None else 0.0
+        d.bhat[i] = float(bhat[i]) if bhat is not None else 0.0
     if seed is not None:
         d.seed = int(seed)
     if stream is not None:
@@ -428,6 +443,18 @@ class Solver:
         else:
             arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
             mmfd_set_fields(self.h, level, [a.ctypes.data for a in arrs], MMFD_HOST, MMFD_DT_F64)
+
+    def set_source(self, fields, level: int = 0):
+        """Source fields (S, then the M_1F components for source "sm"): numpy arrays (host) or
+        CUDA torch tensors."""
+        t = self.torch
+        if fields and isinstance(fields[0], t.Tensor) and fields[0].is_cuda:
+            ts = [f.contiguous().to(t.float64) for f in fields]
+            mmfd_set_source(self.h, level, [f.data_ptr() for f in ts], MMFD_DEVICE, MMFD_DT_F64)
+            self._keep_src = ts
+        else:
+            arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+            mmfd_set_source(self.h, level, [a.ctypes.data for a in arrs], MMFD_HOST, MMFD_DT_F64)
 
     def step(self, nsteps: int = 1):
         mmfd_step(self.h, nsteps)

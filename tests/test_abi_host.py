@@ -200,3 +200,24 @@ def test_stability_check_trt_is_corollary1(mm):
         assert (info.max_lambda > 1 + 1e-12) == (q > 1), (lat, s, mag, q, info.max_lambda)
         verdicts.append(q > 1)
     assert len(verdicts) > 30 and 3 <= sum(verdicts) <= len(verdicts) - 3
+
+
+def test_source_descriptor_validation(mm):
+    K = np.eye(2) * 0.02
+    base = dict(lattice="D2Q9", n=[32, 16], dt=1.0, dx=[1, 1])
+    with pytest.raises(mm.MMFDError) as e:
+        _describe(mm, pde="NSE", levels=2, a=(1, 0, 0), source="s", **base)
+    assert e.value.code == mm.MMFD_ERR_UNSUPPORTED
+    with pytest.raises(mm.MMFDError) as e:
+        _describe(mm, pde="NCDE", levels=2, flux=[[0, 0.1, 0, 0], [0, 0.1, 0, 0]], diff=[0.1, 0, 0, 0],
+                  source="su", **base)
+    assert e.value.code == mm.MMFD_ERR_ARG
+    with pytest.raises(mm.MMFDError) as e:
+        _describe(mm, pde="LCDE", levels=2, K=K, u=[0.1, 0], source="s", bhat=(0.5, 0, 0), **base)
+    assert e.value.code == mm.MMFD_ERR_ARG
+    # compulsory bytes: FP32 levels (read one, write one) plus the source fields read once
+    info = _describe(mm, pde="LCDE", levels=2, K=K, u=[0.1, 0], source="sm", storage="fp32", **base)
+    assert info.bytes_per_lu == 4 * 2 + 4 * 3
+    info = _describe(mm, pde="LCDE", levels=3, K=K, u=[0.1, 0], source="su", storage="fp64",
+                     targets=[0, -1, -1, 0.25, 0.5], **base)
+    assert info.bytes_per_lu == 8 * 3 + 8 * 2
