@@ -74,6 +74,8 @@ KERNEL_SOURCES = {
                      "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     "k_march3d": ["k_march3d.cuh", "k_march3d.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
                   "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+    "k_march2d_src": ["k_march2d_src.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
+                      "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
 }
 
 
@@ -343,15 +345,27 @@ def run_ours(args):
 
     kind, n = args.workload.split("_")
     n = int(n)
-    maker = {"tgv2d": configs.tgv2d_4096, "cde3d": configs.cde3d_512, "nse3d": configs.nse3d_512,
-             "ncde2d": configs.ncde2d_1024, "lcde2d": configs.lcde2d_8192}[kind]
-    desc_kw, fields, _ = maker(n=n, storage=args.storage)
+    # srccde2d: a time-dependent source, set (from device memory) before every step
+    has_src = kind == "srccde2d"
+    if has_src:
+        desc_kw, fields, fields_m1, source = configs.srccde2d_4096(n=n, storage=args.storage)
+    else:
+        maker = {"tgv2d": configs.tgv2d_4096, "cde3d": configs.cde3d_512, "nse3d": configs.nse3d_512,
+                 "ncde2d": configs.ncde2d_1024, "lcde2d": configs.lcde2d_8192}[kind]
+        desc_kw, fields, _ = maker(n=n, storage=args.storage)
     dim = 3 if kind.endswith("3d") else 2
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         d = mmfd.make_desc(**desc_kw, temporal_depth=args.depth)
         s = mmfd.Solver(d, stream=stream)
         s.set_fields(fields)
+        srcs = []
+        if has_src:
+            s.set_fields(fields_m1, level=1)
+            # eight consecutive source levels, cycled (the values repeat; the work per step does not)
+            srcs = [torch.tensor(source(m)[0], dtype=torch.float32, device="cuda") for m in range(-1, 7)]
+            s.set_source([srcs[0]], level=1)
+            s.set_source([srcs[1]])
         tuned = None
         if args.tune:
             # outside the timed region: trial launches write only the spare buffer
@@ -367,8 +381,17 @@ def run_ours(args):
             if ws > 1:
                 torch.distributed.barrier()
 
+        def set_src(i):
+            if has_src:
+                s.set_source([srcs[1 + i % 7]])
+
         # warm-up
-        s.step(args.warmup * depth)
+        if has_src:
+            for i in range(args.warmup):
+                set_src(i)
+                s.step(1)
+        else:
+            s.step(args.warmup * depth)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -379,6 +402,7 @@ def run_ours(args):
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
         for i in range(args.steps):
+            set_src(i)
             ev[i][0].record(stream)
             s.step(depth)
             ev[i][1].record(stream)
@@ -411,17 +435,27 @@ def run_ours(args):
         host_ptrs = [p.data_ptr() for p in pinned]
         h2d = sum(p.numel() * 4 for p in pinned)
         d2h = 8 * len(pinned)
-        for _ in range(2):
+        src_ptrs = []
+        if has_src:
+            # the step's source comes from the host too
+            src_pinned = [torch.from_numpy(np.ascontiguousarray(source(0)[0], dtype=np.float32)).pin_memory()]
+            src_ptrs = [p.data_ptr() for p in src_pinned]
+            h2d += sum(p.numel() * 4 for p in src_pinned)
+
+        def e2e_step():
             mmfd.mmfd_set_fields(s.h, 0, host_ptrs, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
+            if has_src:
+                mmfd.mmfd_set_source(s.h, 0, src_ptrs, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
             s.step(1)
             s.reduce(mmfd.MMFD_RED_SUM)
+
+        for _ in range(2):
+            e2e_step()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            mmfd.mmfd_set_fields(s.h, 0, host_ptrs, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
-            s.step(1)
-            s.reduce(mmfd.MMFD_RED_SUM)
+            e2e_step()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e_s = max_over_ranks(e2e_s, "cuda")
@@ -441,6 +475,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "grid": [n] * dim, "lattice": desc_kw["lattice"],
                    "pde": {"NSE": "NSE (He-Luo)"}.get(desc_kw["pde"], desc_kw["pde"]),
                    "levels": desc_kw["levels"], "storage": args.storage, "temporal_depth": depth,
+                   **({"source": "su, set from device memory before every step"} if has_src else {}),
                    "autotuned": tuned,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},
@@ -452,7 +487,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if has_src else 1),
     }
     if args.serve > 0:
         with torch.cuda.stream(stream):

@@ -18,6 +18,11 @@ Workload recipe (seeded, synthetic; the paper uses analytic test problems, no da
                   phi0 = 1 + 0.5 Sx Sy Sz (16-mode seeded cosine series), 1k steps.
   nse3d_512       512^3 He-Luo NSE on D3Q19, LBGK tau = 1, rho0 = 1, divergence-free seeded
                   velocity with max |u| = 0.05, 1k steps.
+  srccde2d_4096   Example 1 (isotropic CDE with the time-dependent source R) scaled to 4096^2 on the
+                  periodic [0, 2]^2: D2Q9 three-level Case 3 (a = (7/8, 0, 1/8), ahat = (1/8, 0, -1/8)),
+                  b_{-1} = 3/2, bhat_{-1} = -1/2, F_j = w_j R (1 + c_j.u/c_s^2), u = (0.1, 0.1),
+                  kappa = 0.01, dt = 1 / (0.06 N_x^2) with N_x = n / 2 (Example 1's N_t / N_x^2);
+                  phi at t = 0 and -dt from the exact solution; FP32.
 """
 from __future__ import annotations
 
@@ -28,7 +33,7 @@ import numpy as np
 from . import inputs
 
 CONFIG_INDEX = {"cde2d_64": 0, "ncde2d_1024": 1, "lcde2d_8192": 1, "tgv2d_4096": 2, "cde3d_512": 3, "nse3d_512": 3,
-                "serve": 4}
+                "serve": 4, "srccde2d_4096": 1}
 
 NU_LBGK = 1.0 / 6.0          # -(Abar_22 / Abar_10) dt c_s^2 with a_0 = 0, c_s^2 = 1/3
 THREE_LEVEL_A = (7 / 8, 0.0, 1 / 8)
@@ -94,3 +99,25 @@ def nse3d_512(n: int = 512, storage: str = "fp32"):
     desc = dict(pde="NSE", lattice="D3Q19", levels=2, n=[n, n, n], dt=1.0, dx=[1.0, 1.0, 1.0],
                 a=(1.0, 0.0, 0.0), abar=(1.0, 0.0, 0.0), storage=storage, ref=[1.0, 0.0, 0.0, 0.0])
     return desc, [rho, ux, uy, uz], 1000
+
+
+def srccde2d_4096(n: int = 4096, storage: str = "fp32"):
+    """(desc, [phi(0)], [phi(-dt)], source) with source(m) = [R(x, m dt)] (Example 1)."""
+    nx = n // 2
+    dx = 2.0 / n
+    dt = 1.0 / (0.06 * nx * nx)
+    kappa = (dx / dt) ** 2 / 3.0 * dt / 2.0
+    u = (0.1, 0.1)
+    x = np.arange(n) * dx
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    s_, c_ = np.sin(np.pi * (X + Y)), np.cos(np.pi * (X + Y))
+    g = 1.0 - 2.0 * np.pi ** 2 * kappa
+    desc = dict(pde="LCDE", lattice="D2Q9", levels=3, n=[n, n], dt=dt, dx=[dx, dx], K=np.eye(2) * kappa, u=list(u),
+                a=THREE_LEVEL_A, ahat=THREE_LEVEL_AHAT, source="su", b=(1.5, 0.0, 0.0), bhat=(-0.5, 0.0, 0.0),
+                storage=storage)
+    base = s_ + np.pi * (u[0] + u[1]) * c_
+
+    def source(m: int):
+        return [np.exp(g * m * dt) * base]
+
+    return desc, [s_.copy()], [np.exp(-g * dt) * s_], source

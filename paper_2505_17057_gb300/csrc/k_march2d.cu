@@ -5,19 +5,6 @@ namespace mmfd {
 
 namespace {
 
-// Rows per stage: two input rows per TMA box halve the per-row waits, copy issues and
-// accumulator rotations.  For the NSE it costs registers (128 instead of 96, four CTAs per SM
-// instead of five) and still measured faster on 4096^2 (207 vs 191 GLUPS).
-constexpr int rows_per_stage(int) { return 2; }
-
-// Ring depth per warp: about 8 KB of stages, between 3 and 12 stages in flight.
-template <int LAT, int PDE, int LEVELS, int ST, int LN>
-constexpr int march2d_stages() {
-    constexpr size_t per = (march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 1, 1, LN, rows_per_stage(PDE)>() - 256);
-    constexpr size_t n = 8192 / per;
-    return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
-}
-
 template <int LAT, int PDE, int LEVELS, int ST, int LN>
 cudaError_t launch_variant(const LaunchArgs& a) {
     return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST, LN>(), LN,

@@ -221,10 +221,69 @@ __host__ __device__ constexpr int pushed_pairs(int C) {
     return m;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS>
+// Six consecutive source values xb-1 .. xb+4 of one padded row (xb a multiple of 4): a vector
+// load for the lane's own four (16-byte aligned in the source layout) and two scalars; columns
+// beyond the right ghost column are not read (lanes past nx only feed nodes that are not stored).
+template <typename T>
+__device__ __forceinline__ void ld_src6(const T* __restrict__ row, int xb, int nx, T (&v)[6]) {
+    if (xb + 3 < nx) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(row + xb));
+            v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+        } else {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(row + xb));
+            const double2 b = __ldg(reinterpret_cast<const double2*>(row + xb + 2));
+            v[1] = a.x; v[2] = a.y; v[3] = b.x; v[4] = b.y;
+        }
+        v[0] = __ldg(row + xb - 1);
+        v[5] = __ldg(row + xb + 4);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = xb - 1 + c <= nx ? __ldg(row + xb - 1 + c) : T(0);
+    }
+}
+
+// Source terms of the four output nodes xb .. xb+3 of row yo (see SrcCoef): the folded stencil
+// over rows yo-1 .. yo+1 of each source level.  Each source value is read by three output rows
+// and two neighbouring lanes, which the L1 serves; DRAM sees it about once.
+template <int LAT, int SRC, int LEVELS, typename T>
+__device__ __forceinline__ void source_row4(const Geom& g, const SrcArgs<T>& sa, int yo, int xb, T (&add)[4]) {
+    constexpr int NP = lat_npair(LAT);
+    constexpr int NS = SRC == 2 ? 3 : 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) add[k] = T(0);
+    if (xb >= g.nx) return;
+#pragma unroll
+    for (int l = 0; l < LEVELS - 1; ++l) {
+        T v[NS][3][6];
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) ld_src6<T>(sa.s[l] + (size_t)q * g.fs + g.at(0, yo - 1 + r, 0), xb, g.nx, v[q][r]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T acc = sa.w.W0[l] * v[0][1][k + 1];
+            static_for<0, NP>([&](auto pc) {
+                constexpr int P = decltype(pc)::value;
+                constexpr int EX = pair_e(LAT, P, 0), EY = pair_e(LAT, P, 1);
+                acc += sa.w.Wp[l][P] * v[0][1 + EY][k + 1 + EX] + sa.w.Wm[l][P] * v[0][1 - EY][k + 1 - EX];
+                if constexpr (SRC == 2) {
+                    if constexpr (EX != 0)
+                        acc += sa.w.M[l][P][0] * (v[1][1 + EY][k + 1 + EX] - v[1][1 - EY][k + 1 - EX]);
+                    if constexpr (EY != 0)
+                        acc += sa.w.M[l][P][1] * (v[2][1 + EY][k + 1 + EX] - v[2][1 - EY][k + 1 - EX]);
+                }
+            });
+            add[k] += acc;
+        }
+    }
+}
+
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0>
 __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ TmapSet maps, Geom g,
                                                      void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
-                                                     StepExtra ex, int H, int nitems, int* __restrict__ err) {
+                                                     StepExtra ex, int H, int nitems, int* __restrict__ err,
+                                                     const __grid_constant__ SrcParam<typename Storage<ST>::T, SRC> sa) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
@@ -419,6 +478,8 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     EdgeStore<2, ST> es;
     auto store_row = [&](int yo, int xb, const T (&acc)[LN][NF]) {
         const long long nb = (long long)yo * g.nx;
+        [[maybe_unused]] T add[4];
+        if constexpr (SRC != 0) source_row4<LAT, SRC, LEVELS, T>(g, sa, yo, xb, add);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             S* fo = out + (size_t)f * g.fs;
@@ -428,7 +489,11 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
-                    sv[k] = Tr::pack(acc[k4 + k][f], cf.ref[f], rnd);
+                    T v = acc[k4 + k][f];
+                    if constexpr (SRC != 0) {
+                        if (f == 0) v += add[k];
+                    }
+                    sv[k] = Tr::pack(v, cf.ref[f], rnd);
                 }
                 es.put(fo, g, xb + k4, yo, 0, sv);
             }
@@ -504,12 +569,25 @@ constexpr size_t march2d_smem() {
     return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * NF * (LEVELS - 1) * SLOT;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS>
+// Rows per stage: two input rows per TMA box halve the per-row waits, copy issues and
+// accumulator rotations.  For the NSE it costs registers (128 instead of 96, four CTAs per SM
+// instead of five) and still measured faster on 4096^2 (207 vs 191 GLUPS).
+constexpr int rows_per_stage(int) { return 2; }
+
+// Ring depth per warp: about 8 KB of stages, between 3 and 12 stages in flight.
+template <int LAT, int PDE, int LEVELS, int ST, int LN>
+constexpr int march2d_stages() {
+    constexpr size_t per = (march2d_smem<ST, LEVELS, pde_nf(PDE, LAT), 1, 1, LN, rows_per_stage(PDE)>() - 256);
+    constexpr size_t n = 8192 / per;
+    return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
+}
+
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0>
 cudaError_t launch_march2d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE, LN, RPS>();
-    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS>;
+    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -543,8 +621,14 @@ cudaError_t launch_march2d_t(const LaunchArgs& a) {
     const int nitems = strips * ((a.g.ny + H - 1) / H);
     const int blocks_needed = (nitems + NW - 1) / NW;
     const int grid = blocks_needed < resident ? blocks_needed : resident;
+    SrcParam<T, SRC> sa{};
+    if constexpr (SRC != 0) {
+        sa.s[0] = static_cast<const T*>(a.src[0]);
+        sa.s[1] = static_cast<const T*>(LEVELS == 3 ? a.src[1] : a.src[0]);
+        sa.w = *static_cast<const SrcCoef<T>*>(a.src_coef);
+    }
     kern<<<grid, NW * 32, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
-                                             nitems, a.err);
+                                             nitems, a.err, sa);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,48 @@
+// k_march2d_src.cu -- the 2D row-marching TMA kernels with source terms (LCDE on D2Q5 / D2Q9,
+// NCDE on D2Q9): the same kernels and tiling as k_march2d.cu, plus the source stencil in the
+// store epilogue.
+#include "k_march2d.cuh"
+
+namespace mmfd {
+
+namespace {
+
+template <int LAT, int PDE, int LEVELS, int ST, int SRC>
+cudaError_t launch_src(const LaunchArgs& a) {
+    return launch_march2d_t<LAT, PDE, LEVELS, ST, 4, march2d_stages<LAT, PDE, LEVELS, ST, 4>(), 4,
+                            rows_per_stage(PDE), SRC>(a);
+}
+
+template <int LAT, int PDE, int SRC>
+LaunchFn pick_ls(int levels, int st) {
+    if (levels == 2) {
+        if (st == ST_F64) return launch_src<LAT, PDE, 2, ST_F64, SRC>;
+        if (st == ST_F32) return launch_src<LAT, PDE, 2, ST_F32, SRC>;
+        if (st == ST_BF16) return launch_src<LAT, PDE, 2, ST_BF16, SRC>;
+    } else if (levels == 3) {
+        if (st == ST_F64) return launch_src<LAT, PDE, 3, ST_F64, SRC>;
+        if (st == ST_F32) return launch_src<LAT, PDE, 3, ST_F32, SRC>;
+        if (st == ST_BF16) return launch_src<LAT, PDE, 3, ST_BF16, SRC>;
+    }
+    return nullptr;
+}
+
+template <int LAT, int PDE>
+LaunchFn pick_src(int levels, int st, int src) {
+    if (src == 1) return pick_ls<LAT, PDE, 1>(levels, st);
+    if (src == 2) return pick_ls<LAT, PDE, 2>(levels, st);
+    return nullptr;
+}
+
+}  // namespace
+
+LaunchFn find_march2d_src(int lat, int pde, int levels, int st, int src) {
+    if (lat == LAT_D2Q5) return pde == PDE_LCDE ? pick_src<LAT_D2Q5, PDE_LCDE>(levels, st, src) : nullptr;
+    if (lat == LAT_D2Q9) {
+        if (pde == PDE_LCDE) return pick_src<LAT_D2Q9, PDE_LCDE>(levels, st, src);
+        if (pde == PDE_NCDE) return pick_src<LAT_D2Q9, PDE_NCDE>(levels, st, src);
+    }
+    return nullptr;
+}
+
+}  // namespace mmfd

@@ -39,6 +39,8 @@ LaunchFn find_direct(int lat, int pde, int levels, int st);
 LaunchFn find_direct_src(int lat, int pde, int levels, int st, int src);
 // Row-marching 2D kernels fed by a TMA (cp.async.bulk.tensor) shared-memory ring.
 LaunchFn find_march2d(int lat, int pde, int levels, int st);
+// The same with source terms in the store epilogue (src as for find_direct_src; LCDE / NCDE).
+LaunchFn find_march2d_src(int lat, int pde, int levels, int st, int src);
 // Input rows per TMA box (stage) of the 2D marching kernel for this PDE; its tensor maps use
 // boxes of 128 + 2 x 16 bytes by this many rows.
 int march2d_rows_per_stage(int pde);

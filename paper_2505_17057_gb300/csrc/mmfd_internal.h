@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace mmfd {
@@ -97,6 +98,11 @@ struct SrcArgs {
     const T* s[2];
     SrcCoef<T> w;
 };
+
+// Kernel parameter of a kernel family with (SRC != 0) or without source terms.
+struct NoSrc {};
+template <typename T, int SRC>
+using SrcParam = std::conditional_t<SRC != 0, SrcArgs<T>, NoSrc>;
 
 struct StepExtra {
     unsigned long long seed;  // stochastic rounding

@@ -330,7 +330,8 @@ void solver_use_depth(Solver* s, int depth) {
     } else {
         s->fn_block = nullptr;
         s->depth = 1;
-        s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
+        if (s->r.src) s->kernel_name = s->use_tma ? "k_march2d_src" : "k_direct_src";
+        else s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
     }
 }
 
@@ -341,17 +342,14 @@ int solver_pick_kernels(Solver* s) {
     s->variant = 0;
     s->use_tma = false;
     s->fn = nullptr;
-    if (s->r.src) {
-        // source terms: the one-node-per-thread kernels, unblocked
-        s->fn = find_direct_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, s->r.src == MMFD_SRC_SM ? 2 : 1);
-        s->kernel_name = "k_direct_src";
-        if (!s->fn) return set_error(MMFD_ERR_UNSUPPORTED, "no source kernel for this lattice/PDE/levels/storage");
-        return MMFD_OK;
-    }
     const char* force = std::getenv("MMFD_FORCE_KERNEL");
     const bool want_direct = force && std::strcmp(force, "direct") == 0;
+    // source terms: kernel variant 1 (S only, M_1F = 0 or S u folded) or 2 (S and M_1F fields);
+    // such solvers run unblocked
+    const int srcv = s->r.src == 0 ? 0 : (s->r.src == MMFD_SRC_SM ? 2 : 1);
     if (s->r.dim == 2 && s->g.nx >= 128 && !want_direct) {
-        s->fn = find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        s->fn = srcv ? find_march2d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
+                     : find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
         if (s->fn) {
             const int es = s->g.es;
             const int boxw = 128 + 2 * (16 / es);
@@ -367,7 +365,7 @@ int solver_pick_kernels(Solver* s) {
         }
         if (s->fn) {
             s->use_tma = true;
-            s->kernel_name = "k_march2d";
+            s->kernel_name = srcv ? "k_march2d_src" : "k_march2d";
             s->H = 0;  // chosen by the launcher from the kernel's occupancy
             // temporal blocking: 0 asks for the deepest blocking the storage allows (the
             // autotuner may then pick a shallower one); the x ghost columns, kept current to
@@ -375,7 +373,7 @@ int solver_pick_kernels(Solver* s) {
             // (The blocked kernel stages two rows per box, as the solver's maps for these PDEs do.)
             int maxd = march2d_tb_max_depth(s->r.st);
             while (maxd >= 2 && s->g.ny < 2 * maxd) --maxd;
-            if (s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
+            if (!srcv && s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
                 find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
                 s->max_depth = maxd;
                 int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
@@ -385,7 +383,7 @@ int solver_pick_kernels(Solver* s) {
             return MMFD_OK;
         }
     }
-    if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct) {
+    if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct && !srcv) {
         s->fn = find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
         if (s->fn) {
             const int es = s->g.es;
@@ -407,8 +405,9 @@ int solver_pick_kernels(Solver* s) {
             return MMFD_OK;
         }
     }
-    s->fn = find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
-    s->kernel_name = "k_direct";
+    s->fn = srcv ? find_direct_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
+                 : find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+    s->kernel_name = srcv ? "k_direct_src" : "k_direct";
     if (!s->fn) return set_error(MMFD_ERR_UNSUPPORTED, "no kernel for this lattice/PDE/levels/storage");
     return MMFD_OK;
 }

@@ -449,8 +449,10 @@ class Solver:
         CUDA torch tensors."""
         t = self.torch
         if fields and isinstance(fields[0], t.Tensor) and fields[0].is_cuda:
-            ts = [f.contiguous().to(t.float64) for f in fields]
-            mmfd_set_source(self.h, level, [f.data_ptr() for f in ts], MMFD_DEVICE, MMFD_DT_F64)
+            f32 = all(f.dtype == t.float32 and f.is_contiguous() for f in fields)
+            ts = list(fields) if f32 else [f.contiguous().to(t.float64) for f in fields]
+            mmfd_set_source(self.h, level, [f.data_ptr() for f in ts], MMFD_DEVICE,
+                            MMFD_DT_F32 if f32 else MMFD_DT_F64)
             self._keep_src = ts
         else:
             arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]

@@ -39,8 +39,9 @@ def src_fields(prob, rng):
     return [0.3 + 0.2 * rng.standard_normal(prob.shape) for _ in range(prob.nsrc)]
 
 
-def run_both(mm, kw, prob, rng, steps, static=False, storage_round=None):
-    """GPU and oracle runs with the same sources; returns (gpu, oracle)."""
+def run_both(mm, kw, prob, rng, steps, static=False, storage_round=None, kernels=None):
+    """GPU and oracle runs with the same sources; returns (gpu, oracle).  The name of the step
+    kernel that ran is added to `kernels`."""
     L0 = G.random_level(prob, rng)
     L1 = G.random_level(prob, rng) if prob.levels == 3 else None
     srcs = {m: src_fields(prob, rng) for m in range(-1, steps)}
@@ -49,7 +50,10 @@ def run_both(mm, kw, prob, rng, steps, static=False, storage_round=None):
             srcs[m] = srcs[0]
     s = mm.Solver(mm.make_desc(**kw, flags=mm.MMFD_FLAG_ALLOW_UNSTABLE))
     try:
-        assert s.get_info().kernel.decode() == "k_direct_src"
+        kern = s.get_info().kernel.decode()
+        assert kern in ("k_direct_src", "k_march2d_src"), kern
+        if kernels is not None:
+            kernels.add(kern)
         s.set_fields(L0)
         if L1 is not None:
             s.set_fields(L1, level=1)
@@ -80,11 +84,15 @@ CASES = [("D2Q5", "LCDE", 2, "s"), ("D2Q5", "LCDE", 3, "su"), ("D2Q9", "LCDE", 2
 @pytest.mark.parametrize("lat,pde,levels,source", CASES)
 def test_source_fp64_matches_oracle(mm, lat, pde, levels, source):
     rng = np.random.default_rng(G.RNG_SEED + 100)
-    sizes = [[300, 70], [67, 45]] if G.dims(lat) == 2 else [[150, 21, 9], [40, 21, 9]]
+    # 2D: ragged strips and tails on the marching kernel (nx >= 128), and the direct kernel
+    sizes = [[300, 70], [517, 131], [67, 45]] if G.dims(lat) == 2 else [[150, 21, 9], [40, 21, 9]]
+    kernels = set()
     for n in sizes:
         kw, prob = source_case(lat, pde, levels, n, "fp64", source)
-        out, ref = run_both(mm, kw, prob, rng, 4)
+        out, ref = run_both(mm, kw, prob, rng, 4, kernels=kernels)
         assert G.rel_err(out, ref) < 1e-12, (n, G.rel_err(out, ref))
+    if G.dims(lat) == 2:
+        assert kernels == {"k_direct_src", "k_march2d_src"}, kernels
 
 
 @pytest.mark.parametrize("lat,pde,levels,source", [("D2Q9", "LCDE", 3, "su"), ("D2Q9", "NCDE", 2, "sm"),
@@ -199,3 +207,35 @@ def test_example1_on_gpu(mm, case):
         assert abs(gpu - oracle) < 1e-9 * oracle
     orders = [np.log2(res[i][0] / res[i + 1][0]) for i in range(2)]
     assert all(o >= 1.8 for o in orders), orders
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("bf16", 0.0)])
+def test_march_source_matches_direct(mm, monkeypatch, storage, tol):
+    # the fused epilogue of the marching kernel against the one-node-per-thread kernel, on a
+    # grid with ragged strips, from the same stored state
+    rng = np.random.default_rng(G.RNG_SEED + 105)
+    kw, prob = source_case("D2Q9", "NCDE", 3, [517, 131], storage, "sm")
+    L0 = G.random_level(prob, rng)
+    L1 = G.random_level(prob, rng)
+    S0, S1 = src_fields(prob, rng), src_fields(prob, rng)
+    outs = {}
+    for force in ("", "direct"):
+        monkeypatch.setenv("MMFD_FORCE_KERNEL", force)
+        s = mm.Solver(mm.make_desc(**kw, flags=mm.MMFD_FLAG_ALLOW_UNSTABLE))
+        try:
+            outs[force] = s.get_info().kernel.decode()
+            s.set_fields(L0)
+            s.set_fields(L1, level=1)
+            s.set_source(S1, level=1)
+            s.set_source(S0)
+            s.step(1)
+            outs[force + "f"] = s.fields(0)[0]
+        finally:
+            s.close()
+    assert outs[""] == "k_march2d_src" and outs["direct"] == "k_direct_src"
+    a, b = outs["f"], outs["directf"]
+    if storage == "bf16":
+        # the two kernels round FP32 sums taken in different orders: at most one ulp apart
+        assert np.all(np.abs(a - b) <= G.bf16_ulp(b) + 1e-6 * np.abs(b))
+    else:
+        assert np.abs(a - b).max() <= tol * np.abs(b).max()
