@@ -243,39 +243,67 @@ __device__ __forceinline__ void ld_src6(const T* __restrict__ row, int xb, int n
     }
 }
 
-// Source terms of the four output nodes xb .. xb+3 of row yo (see SrcCoef): the folded stencil
-// over rows yo-1 .. yo+1 of each source level.  Each source value is read by three output rows
-// and two neighbouring lanes, which the L1 serves; DRAM sees it about once.
+// Whether source row (y + DY, z + DZ) feeds an output node: the centre row, or the row of a
+// pair's plus (+e_p) or minus (-e_p) neighbour.
+template <int LAT>
+__host__ __device__ constexpr bool src_row_used(int DY, int DZ) {
+    if (DY == 0 && DZ == 0) return true;
+    for (int p = 0; p < lat_npair(LAT); ++p) {
+        const int ey = pair_e(LAT, p, 1), ez = lat_dim(LAT) == 3 ? pair_e(LAT, p, 2) : 0;
+        if ((ey == DY && ez == DZ) || (-ey == DY && -ez == DZ)) return true;
+    }
+    return false;
+}
+
+// Source terms of the four output nodes xb .. xb+3 of row y, plane z (see SrcCoef): the folded
+// stencil, taken one source row (y + DY, z + DZ) at a time so that only six values per source
+// field are live.  Each source value is read by several output rows and neighbouring lanes,
+// which the L1 serves; DRAM sees it about once.
 template <int LAT, int SRC, int LEVELS, typename T>
-__device__ __forceinline__ void source_row4(const Geom& g, const SrcArgs<T>& sa, int yo, int xb, T (&add)[4]) {
+__device__ __forceinline__ void source_quad(const Geom& g, const SrcArgs<T>& sa, int y, int z, int xb, T (&add)[4]) {
     constexpr int NP = lat_npair(LAT);
-    constexpr int NS = SRC == 2 ? 3 : 1;
+    constexpr int DIM = lat_dim(LAT);
+    constexpr int NS = SRC == 2 ? 1 + DIM : 1;
 #pragma unroll
     for (int k = 0; k < 4; ++k) add[k] = T(0);
     if (xb >= g.nx) return;
 #pragma unroll
     for (int l = 0; l < LEVELS - 1; ++l) {
-        T v[NS][3][6];
+        static_for<0, 9>([&](auto rc) {
+            constexpr int DY = decltype(rc)::value / 3 - 1, DZ = decltype(rc)::value % 3 - 1;
+            if constexpr ((DIM == 3 || DZ == 0) && src_row_used<LAT>(DY, DZ)) {
+                T v[NS][6];
 #pragma unroll
-        for (int q = 0; q < NS; ++q)
+                for (int q = 0; q < NS; ++q) ld_src6<T>(sa.s[l] + (size_t)q * g.fs + g.at(0, y + DY, z + DZ), xb, g.nx, v[q]);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) ld_src6<T>(sa.s[l] + (size_t)q * g.fs + g.at(0, yo - 1 + r, 0), xb, g.nx, v[q][r]);
+                for (int k = 0; k < 4; ++k) {
+                    T acc = T(0);
+                    if constexpr (DY == 0 && DZ == 0) acc = sa.w.W0[l] * v[0][k + 1];
+                    static_for<0, NP>([&](auto pc) {
+                        constexpr int P = decltype(pc)::value;
+                        constexpr int EX = pair_e(LAT, P, 0), EY = pair_e(LAT, P, 1);
+                        constexpr int EZ = DIM == 3 ? pair_e(LAT, P, 2) : 0;
+                        if constexpr (EY == DY && EZ == DZ) {
+                            acc += sa.w.Wp[l][P] * v[0][k + 1 + EX];
+                            if constexpr (SRC == 2) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            T acc = sa.w.W0[l] * v[0][1][k + 1];
-            static_for<0, NP>([&](auto pc) {
-                constexpr int P = decltype(pc)::value;
-                constexpr int EX = pair_e(LAT, P, 0), EY = pair_e(LAT, P, 1);
-                acc += sa.w.Wp[l][P] * v[0][1 + EY][k + 1 + EX] + sa.w.Wm[l][P] * v[0][1 - EY][k + 1 - EX];
-                if constexpr (SRC == 2) {
-                    if constexpr (EX != 0)
-                        acc += sa.w.M[l][P][0] * (v[1][1 + EY][k + 1 + EX] - v[1][1 - EY][k + 1 - EX]);
-                    if constexpr (EY != 0)
-                        acc += sa.w.M[l][P][1] * (v[2][1 + EY][k + 1 + EX] - v[2][1 - EY][k + 1 - EX]);
+                                for (int a = 0; a < DIM; ++a)
+                                    if (pair_e(LAT, P, a) != 0) acc += sa.w.M[l][P][a] * v[1 + a][k + 1 + EX];
+                            }
+                        }
+                        if constexpr (-EY == DY && -EZ == DZ) {
+                            acc += sa.w.Wm[l][P] * v[0][k + 1 - EX];
+                            if constexpr (SRC == 2) {
+#pragma unroll
+                                for (int a = 0; a < DIM; ++a)
+                                    if (pair_e(LAT, P, a) != 0) acc -= sa.w.M[l][P][a] * v[1 + a][k + 1 - EX];
+                            }
+                        }
+                    });
+                    add[k] += acc;
                 }
-            });
-            add[k] += acc;
-        }
+            }
+        });
     }
 }
 
@@ -479,7 +507,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
     auto store_row = [&](int yo, int xb, const T (&acc)[LN][NF]) {
         const long long nb = (long long)yo * g.nx;
         [[maybe_unused]] T add[4];
-        if constexpr (SRC != 0) source_row4<LAT, SRC, LEVELS, T>(g, sa, yo, xb, add);
+        if constexpr (SRC != 0) source_quad<LAT, SRC, LEVELS, T>(g, sa, yo, 0, xb, add);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             S* fo = out + (size_t)f * g.fs;

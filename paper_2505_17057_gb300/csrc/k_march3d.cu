@@ -5,17 +5,6 @@ namespace mmfd {
 
 namespace {
 
-// Rows per CTA tile: 8 for the light linear stencil, 4 where registers are scarce.
-constexpr int tile_rows(int pde) { return pde == PDE_LCDE ? 8 : 4; }
-
-// Ring depth: about 48 KB of stages per CTA, between 2 and 8 planes in flight.
-template <int LAT, int PDE, int LEVELS, int ST>
-constexpr int march3d_stages() {
-    constexpr size_t per = march3d_smem<ST, LEVELS, pde_nf(PDE, LAT), tile_rows(PDE), 1>() - 256;
-    constexpr size_t n = 49152 / per;
-    return n < 2 ? 2 : (n > 8 ? 8 : (int)n);
-}
-
 template <int LAT, int PDE, int LEVELS, int ST>
 LaunchFn pick() {
     return launch_march3d_t<LAT, PDE, LEVELS, ST, tile_rows(PDE), march3d_stages<LAT, PDE, LEVELS, ST>()>;

@@ -26,10 +26,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE>
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0>
 __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant__ TmapSet maps, Geom g,
                                                            void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
-                                                           StepExtra ex, int H, int nitems, int* __restrict__ err) {
+                                                           StepExtra ex, int H, int nitems, int* __restrict__ err,
+                                                           const __grid_constant__ SrcParam<typename Storage<ST>::T, SRC> sa) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
@@ -238,13 +239,19 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
             if (i >= 2 && y < g.ny) {
                 const int zo = z0 + i - 2;
                 const long long nb = ((long long)zo * g.ny + y) * g.nx;
+                [[maybe_unused]] T add[4];
+                if constexpr (SRC != 0) source_quad<LAT, SRC, LEVELS, T>(g, sa, y, zo, xb, add);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     S sv[4];
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
                         const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + n, f) : 0u;
-                        sv[n] = Tr::pack(accP[n][f], cf.ref[f], rnd);
+                        T v = accP[n][f];
+                        if constexpr (SRC != 0) {
+                            if (f == 0) v += add[n];
+                        }
+                        sv[n] = Tr::pack(v, cf.ref[f], rnd);
                     }
                     S* fo = out + (size_t)f * g.fs;
                     es.put(fo, g, xb, y, zo, sv);
@@ -271,13 +278,24 @@ constexpr size_t march3d_smem() {
     return 128 + 128 * ((2 * NSTAGE * 8 + 127) / 128) + (size_t)NSTAGE * NF * (LEVELS - 1) * SLOT;
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE>
+// Rows per CTA tile: 8 for the light linear stencil, 4 where registers are scarce.
+constexpr int tile_rows(int pde) { return pde == PDE_LCDE ? 8 : 4; }
+
+// Ring depth: about 48 KB of stages per CTA, between 2 and 8 planes in flight.
+template <int LAT, int PDE, int LEVELS, int ST>
+constexpr int march3d_stages() {
+    constexpr size_t per = march3d_smem<ST, LEVELS, pde_nf(PDE, LAT), tile_rows(PDE), 1>() - 256;
+    constexpr size_t n = 49152 / per;
+    return n < 2 ? 2 : (n > 8 ? 8 : (int)n);
+}
+
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0>
 cudaError_t launch_march3d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march3d_smem<ST, LEVELS, NF, TY, NSTAGE>();
     constexpr int THREADS = (TY + 1) * 32;
-    auto kern = k_march3d<LAT, PDE, LEVELS, ST, TY, NSTAGE>;
+    auto kern = k_march3d<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -308,8 +326,14 @@ cudaError_t launch_march3d_t(const LaunchArgs& a) {
     }
     const int nitems = xs * ys * ((a.g.nz + H - 1) / H);
     const int grid = nitems < resident ? nitems : resident;
+    SrcParam<T, SRC> sa{};
+    if constexpr (SRC != 0) {
+        sa.s[0] = static_cast<const T*>(a.src[0]);
+        sa.s[1] = static_cast<const T*>(LEVELS == 3 ? a.src[1] : a.src[0]);
+        sa.w = *static_cast<const SrcCoef<T>*>(a.src_coef);
+    }
     kern<<<grid, THREADS, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
-                                            nitems, a.err);
+                                            nitems, a.err, sa);
     return cudaGetLastError();
 }
 

@@ -330,7 +330,7 @@ void solver_use_depth(Solver* s, int depth) {
     } else {
         s->fn_block = nullptr;
         s->depth = 1;
-        if (s->r.src) s->kernel_name = s->use_tma ? "k_march2d_src" : "k_direct_src";
+        if (s->r.src) s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d_src" : "k_march3d_src") : "k_direct_src";
         else s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
     }
 }
@@ -383,8 +383,9 @@ int solver_pick_kernels(Solver* s) {
             return MMFD_OK;
         }
     }
-    if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct && !srcv) {
-        s->fn = find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+    if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct) {
+        s->fn = srcv ? find_march3d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
+                     : find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
         if (s->fn) {
             const int es = s->g.es;
             const int boxw = 128 + 2 * (16 / es);
@@ -400,7 +401,7 @@ int solver_pick_kernels(Solver* s) {
         }
         if (s->fn) {
             s->use_tma = true;
-            s->kernel_name = "k_march3d";
+            s->kernel_name = srcv ? "k_march3d_src" : "k_march3d";
             s->H = 0;
             return MMFD_OK;
         }

@@ -51,7 +51,7 @@ def run_both(mm, kw, prob, rng, steps, static=False, storage_round=None, kernels
     s = mm.Solver(mm.make_desc(**kw, flags=mm.MMFD_FLAG_ALLOW_UNSTABLE))
     try:
         kern = s.get_info().kernel.decode()
-        assert kern in ("k_direct_src", "k_march2d_src"), kern
+        assert kern in ("k_direct_src", "k_march2d_src", "k_march3d_src"), kern
         if kernels is not None:
             kernels.add(kern)
         s.set_fields(L0)
@@ -84,15 +84,15 @@ CASES = [("D2Q5", "LCDE", 2, "s"), ("D2Q5", "LCDE", 3, "su"), ("D2Q9", "LCDE", 2
 @pytest.mark.parametrize("lat,pde,levels,source", CASES)
 def test_source_fp64_matches_oracle(mm, lat, pde, levels, source):
     rng = np.random.default_rng(G.RNG_SEED + 100)
-    # 2D: ragged strips and tails on the marching kernel (nx >= 128), and the direct kernel
-    sizes = [[300, 70], [517, 131], [67, 45]] if G.dims(lat) == 2 else [[150, 21, 9], [40, 21, 9]]
+    # ragged strips and tails on the marching kernels (nx >= 128), and the direct kernel
+    sizes = [[300, 70], [517, 131], [67, 45]] if G.dims(lat) == 2 else [[150, 21, 9], [131, 13, 7], [40, 21, 9]]
     kernels = set()
     for n in sizes:
         kw, prob = source_case(lat, pde, levels, n, "fp64", source)
         out, ref = run_both(mm, kw, prob, rng, 4, kernels=kernels)
         assert G.rel_err(out, ref) < 1e-12, (n, G.rel_err(out, ref))
-    if G.dims(lat) == 2:
-        assert kernels == {"k_direct_src", "k_march2d_src"}, kernels
+    march = "k_march2d_src" if G.dims(lat) == 2 else "k_march3d_src"
+    assert kernels == {"k_direct_src", march}, kernels
 
 
 @pytest.mark.parametrize("lat,pde,levels,source", [("D2Q9", "LCDE", 3, "su"), ("D2Q9", "NCDE", 2, "sm"),
@@ -209,12 +209,13 @@ def test_example1_on_gpu(mm, case):
     assert all(o >= 1.8 for o in orders), orders
 
 
+@pytest.mark.parametrize("lat,n", [("D2Q9", [517, 131]), ("D3Q19", [150, 21, 9])])
 @pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("bf16", 0.0)])
-def test_march_source_matches_direct(mm, monkeypatch, storage, tol):
-    # the fused epilogue of the marching kernel against the one-node-per-thread kernel, on a
+def test_march_source_matches_direct(mm, monkeypatch, storage, tol, lat, n):
+    # the fused epilogue of the marching kernels against the one-node-per-thread kernel, on a
     # grid with ragged strips, from the same stored state
     rng = np.random.default_rng(G.RNG_SEED + 105)
-    kw, prob = source_case("D2Q9", "NCDE", 3, [517, 131], storage, "sm")
+    kw, prob = source_case(lat, "NCDE", 3, n, storage, "sm")
     L0 = G.random_level(prob, rng)
     L1 = G.random_level(prob, rng)
     S0, S1 = src_fields(prob, rng), src_fields(prob, rng)
@@ -232,7 +233,7 @@ def test_march_source_matches_direct(mm, monkeypatch, storage, tol):
             outs[force + "f"] = s.fields(0)[0]
         finally:
             s.close()
-    assert outs[""] == "k_march2d_src" and outs["direct"] == "k_direct_src"
+    assert outs[""] == ("k_march2d_src" if len(n) == 2 else "k_march3d_src") and outs["direct"] == "k_direct_src"
     a, b = outs["f"], outs["directf"]
     if storage == "bf16":
         # the two kernels round FP32 sums taken in different orders: at most one ulp apart
