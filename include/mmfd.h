@@ -37,7 +37,8 @@ extern "C" {
 #define MMFD_ERR_STATE (-10)         /* call not valid in the object's current state */
 
 /* ------------------------------------------------------------------ enums */
-typedef enum { MMFD_LCDE = 0, MMFD_NCDE = 1, MMFD_NSE = 2 } mmfd_pde;
+/* MMFD_LWE: the linear wave equation d_t^2 phi = div(K grad phi) (Eq. (LWE)), three-level. */
+typedef enum { MMFD_LCDE = 0, MMFD_NCDE = 1, MMFD_NSE = 2, MMFD_LWE = 3 } mmfd_pde;
 typedef enum { MMFD_D2Q5 = 0, MMFD_D2Q9 = 1, MMFD_D3Q7 = 2, MMFD_D3Q19 = 3 } mmfd_lattice;
 /* Storage of the level buffers.  BF16: each value stored as bf16(v - ref[field]) and
  * read back as ref[field] + v; all arithmetic in FP32.  FP64: arithmetic in FP64. */
@@ -69,6 +70,12 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        D2Q9/D3Q19: used as given (mmfd_desc_init sets 1/3).  D2Q5/D3Q7:
  *                        ignored for the LCDE (derived from K, u, the scheme moments).
  *  K[3][3], u[3]         LCDE: diffusion tensor alpha D0 and constant velocity (Eq. (LCDE)).
+ *                        LWE: the wave tensor alpha D0 of Eq. (LWE) (u must be zero).  The EDF
+ *                        is the linear one of Eq. (TforMMFD-0) with second moment K phi / A_22
+ *                        (Eq. (ME-NCDE-W-1)): on D2Q9 / D3Q19 C = K / A_22 - c_s^2 I, on
+ *                        D2Q5 / D3Q7 c_salpha^2 = K_alphaalpha / A_22.  The scheme must be
+ *                        three-level with A_10 = A_11 = A_21 = 0 and A_20 = -1 (Sec. III.B (3)),
+ *                        e.g. mmfd_wave_coefficients; no source terms.
  *  lambda_bar            LCDE quadratic EDF parameter of Eq. (TforMMFD-0) (default 1).
  *  flux[3][4]            NCDE: B_alpha(phi) = sum_p flux[alpha][p] phi^p.
  *  diff[4]               NCDE: isotropic D(phi) = sum_p diff[p] phi^p (div(D grad phi)).
@@ -250,6 +257,10 @@ int mmfd_solve_three_level(const double targets[5], double a[3], double ahat[3])
  * step on when level t - dt holds the initial moments and level t one LBGK tau = 1 step of them
  * (a = (1, 0, 0)).  Any output pointer may be NULL.  MMFD_ERR_ARG if s_minus is outside (0, 2). */
 int mmfd_trt_coefficients(double s_minus, double a[3], double ahat[3], double abar[3], double abarhat[3]);
+/* Sec. III.C, special case (4): the wave-equation scheme a = (gamma, 2 (1 - gamma), gamma),
+ * ahat = (0, -1, 0), with A_22 = gamma (so that alpha = gamma beta c_s^2).  MMFD_ERR_ARG if gamma
+ * is not finite and positive. */
+int mmfd_wave_coefficients(double gamma, double a[3], double ahat[3]);
 /* ---- autotuner --------------------------------------------------------------------------
  * Not from the paper: a build choice.  The step kernels take two tuning parameters, the temporal
  * depth (time steps per launch, where blocking is available) and the work-item height (rows in

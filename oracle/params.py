@@ -191,6 +191,39 @@ def effective_diffusion(lattice: str, levels: int, dt: float, K, u, a: Triple,
     return Keff
 
 
+def wave_coefficients(gamma):
+    """Sec. III.C case (4): a = (gamma, 2 (1 - gamma), gamma), ahat = (0, -1, 0)."""
+    return (gamma, 2 * (1 - gamma), gamma), (0 * gamma, 0 * gamma - 1, 0 * gamma)
+
+
+def problem_lwe(lattice: str, n, dt: float, dx, K, a: Triple, ahat: Triple, d0=None) -> Problem:
+    """Linear wave equation d_t^2 phi = div(K grad phi) (Eq. (LWE), K = alpha D0), three-level.
+
+    Eq. (ME-NCDE-W-1): d_t^2 phi = A_22 div div M_2 with M_2 = beta c_s^2 D0 phi, so the EDF's
+    second moment is K phi / A_22: on D2Q9 / D3Q19 C = K / A_22 - c_s^2 I (u = 0 in
+    Eq. (TforMMFD-0)); on D2Q5 / D3Q7 the linear EDF (C = 0) with c_salpha^2 = K_alphaalpha / A_22.
+    """
+    dim = LATTICE_DIM[lattice]
+    c = lattice_c(dt, dx, dim)
+    A = three_level_moments(a, ahat)
+    A22 = float(A[(2, 2)])
+    K = np.asarray(K, dtype=float)
+    Cmat = np.zeros((3, 3))
+    if lattice in ("D2Q9", "D3Q19"):
+        d0v = list(d0) if d0 is not None else [1.0 / 3.0] * dim
+        d0v = (d0v + [0.0] * 3)[:3]
+        for i in range(dim):
+            for j in range(dim):
+                Cmat[i, j] = K[i, j] / A22
+            Cmat[i, i] -= d0v[i] * c[i] ** 2
+    else:
+        d0v = [0.0, 0.0, 0.0]
+        for i in range(dim):
+            d0v[i] = K[i, i] / A22 / c[i] ** 2
+    return Problem(lattice=lattice, pde="LCDE", levels=3, n=n, c=c, d0=d0v, a=a, ahat=ahat,
+                   u=(0.0, 0.0, 0.0), Cmat=Cmat.ravel(), dt=dt)
+
+
 def problem_ncde(lattice: str, levels: int, n, dt: float, dx, flux_poly, diff_poly, a: Triple,
                  ahat: Triple = (0.0, 0.0, 0.0), d0=None) -> Problem:
     """NCDE  d_t phi + div B(phi) = div(D(phi) grad phi), D isotropic (Eq. (NCDE0)).

@@ -121,6 +121,18 @@ int mmfd_trt_coefficients(double s_minus, double a[3], double ahat[3], double ab
     return MMFD_OK;
 }
 
+int mmfd_wave_coefficients(double gamma, double a[3], double ahat[3]) {
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) return set_error(MMFD_ERR_ARG, "gamma must be finite and positive");
+    if (!a || !ahat) return set_error(MMFD_ERR_ARG, "null argument");
+    a[0] = gamma;
+    a[1] = 2.0 * (1.0 - gamma);
+    a[2] = gamma;
+    ahat[0] = 0.0;
+    ahat[1] = -1.0;
+    ahat[2] = 0.0;
+    return MMFD_OK;
+}
+
 static void fill_info(const Resolved& r, mmfd_info_t* o) {
     std::memset(o, 0, sizeof(*o));
     o->nf = r.nf;

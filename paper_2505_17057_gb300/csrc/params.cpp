@@ -141,9 +141,14 @@ static int fail(std::string* msg, int code, const char* why) {
     return code;
 }
 
-int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
+int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
     std::memset(&r, 0, sizeof(r));
-    if (d.pde < PDE_LCDE || d.pde > PDE_NSE) return fail(msg, MMFD_ERR_ARG, "unknown pde");
+    if (d_in.pde < PDE_LCDE || d_in.pde > MMFD_LWE) return fail(msg, MMFD_ERR_ARG, "unknown pde");
+    // the wave equation (Eq. (LWE)) is a linear-EDF scheme like the LCDE: its own mapping of K
+    // onto the EDF, the LCDE's kernels
+    const bool wave = d_in.pde == MMFD_LWE;
+    mmfd_desc d = d_in;
+    if (wave) d.pde = PDE_LCDE;
     if (d.lattice < LAT_D2Q5 || d.lattice > LAT_D3Q19) return fail(msg, MMFD_ERR_ARG, "unknown lattice");
     if (d.levels != 2 && d.levels != 3) return fail(msg, MMFD_ERR_ARG, "levels must be 2 or 3");
     if (d.storage < ST_F64 || d.storage > ST_BF16) return fail(msg, MMFD_ERR_ARG, "unknown storage");
@@ -190,6 +195,19 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
         if (std::fabs(Ab00 - 1.0) > 1e-12) return fail(msg, MMFD_ERR_ARG, "momentum coefficients violate Abar_00 = 1");
     }
     scheme_moments(d.levels, r.a, r.ahat, r.A10, r.A20, r.A21, r.A22);
+    if (wave) {
+        // Sec. III.B (3): A_20 = -1 and A_lm = 0 except (2, 0), (2, 2) among the moments the
+        // second-order equation sees, so that d_t^2 phi = A_22 div div M_2 (Eq. (ME-NCDE-W))
+        if (d.levels != 3) return fail(msg, MMFD_ERR_ARG, "the wave equation needs a three-level scheme");
+        const double A11 = r.a[2] - r.a[0] + r.ahat[2] - r.ahat[0];
+        if (std::fabs(r.A10) > 1e-12 || std::fabs(A11) > 1e-12 || std::fabs(r.A21) > 1e-12 ||
+            std::fabs(r.A20 + 1.0) > 1e-12 || !(std::fabs(r.A22) > 0.0))
+            return fail(msg, MMFD_ERR_ARG,
+                        "wave equation: coefficients must give A_10 = A_11 = A_21 = 0, A_20 = -1, A_22 != 0");
+        for (int a = 0; a < 3; ++a)
+            if (d.u[a] != 0.0) return fail(msg, MMFD_ERR_ARG, "wave equation: u must be zero");
+        if (d.source != MMFD_SRC_NONE) return fail(msg, MMFD_ERR_UNSUPPORTED, "wave equation: no source terms");
+    }
 
     for (int a = 0; a < 3; ++a) r.c[a] = a < dim ? d.dx[a] / d.dt : 0.0;
 
@@ -201,7 +219,7 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
             for (int b = 0; b < dim; ++b)
                 if (!finite(d.K[a][b]) || std::fabs(d.K[a][b] - d.K[b][a]) > 1e-14 * (1 + std::fabs(d.K[a][b])))
                     return fail(msg, MMFD_ERR_ARG, "K must be finite and symmetric");
-        if (r.A10 == 0.0 || r.A22 == 0.0) return fail(msg, MMFD_ERR_ARG, "A_10 and A_22 must be nonzero for a CDE");
+        if (!wave && (r.A10 == 0.0 || r.A22 == 0.0)) return fail(msg, MMFD_ERR_ARG, "A_10 and A_22 must be nonzero for a CDE");
     }
     if (axis) {
         // Linear EDF (C = 0) with direction-dependent c_salpha^2 chosen so that the recovered
@@ -216,7 +234,9 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
                         "off-diagonal diffusion cannot be represented on an axis lattice (set MMFD_FLAG_DROP_OFFDIAG)");
         double sum = 0.0;
         for (int a = 0; a < dim; ++a) {
-            const double cs2 = (-r.A10 * d.K[a][a] / d.dt + (r.A21 - r.A20) * d.u[a] * d.u[a]) / r.A22;
+            // LCDE: Eq. (ME-NCDE-3-2-1); wave: second moment K phi / A_22 (Eq. (ME-NCDE-W-1))
+            const double cs2 = wave ? d.K[a][a] / r.A22
+                                    : (-r.A10 * d.K[a][a] / d.dt + (r.A21 - r.A20) * d.u[a] * d.u[a]) / r.A22;
             r.cs2[a] = cs2;
             r.d0[a] = cs2 / (r.c[a] * r.c[a]);
             if (!(r.d0[a] > 0.0) || !finite(r.d0[a])) return fail(msg, MMFD_ERR_ARG, "derived d_0 must be positive");
@@ -233,7 +253,8 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
             // C = c_s^2 (beta D0 - I) + lambda_bar u u with c_s^2 beta D0 = -A_10 K / (A_22 dt)
             for (int a = 0; a < dim; ++a)
                 for (int b = 0; b < dim; ++b)
-                    r.Cmat[a][b] = -r.A10 * d.K[a][b] / (r.A22 * d.dt) + d.lambda_bar * d.u[a] * d.u[b];
+                    r.Cmat[a][b] = wave ? d.K[a][b] / r.A22
+                                        : -r.A10 * d.K[a][b] / (r.A22 * d.dt) + d.lambda_bar * d.u[a] * d.u[b];
             for (int a = 0; a < dim; ++a) r.Cmat[a][a] -= r.cs2[a];
         }
     }
@@ -456,9 +477,16 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg) {
                     if (d.levels == 2) {
                         m = std::abs(A[0]);
                     } else {
-                        // roots of lambda^2 - p1 lambda - p0 (Eq. (3-level))
-                        const std::complex<double> disc = std::sqrt(A[0] * A[0] + 4.0 * A[1]);
-                        m = std::max(std::abs(0.5 * (A[0] + disc)), std::abs(0.5 * (A[0] - disc)));
+                        // roots of lambda^2 - p1 lambda - p0 (Eq. (3-level)); a vanishing
+                        // discriminant is the double root p1 / 2 (the wave scheme's constant mode:
+                        // the quadratic formula would put it at 1 +- O(sqrt(eps)))
+                        const std::complex<double> d2 = A[0] * A[0] + 4.0 * A[1];
+                        if (std::abs(d2) <= 1e-13 * std::max(1.0, std::norm(A[0]))) {
+                            m = std::abs(0.5 * A[0]);
+                        } else {
+                            const std::complex<double> disc = std::sqrt(d2);
+                            m = std::max(std::abs(0.5 * (A[0] + disc)), std::abs(0.5 * (A[0] - disc)));
+                        }
                     }
                     if (m > lmax) lmax = m;
                 }

@@ -31,7 +31,7 @@ MMFD_ERR_TIMEOUT = -8
 MMFD_ERR_CUDA = -9
 MMFD_ERR_STATE = -10
 
-MMFD_LCDE, MMFD_NCDE, MMFD_NSE = 0, 1, 2
+MMFD_LCDE, MMFD_NCDE, MMFD_NSE, MMFD_LWE = 0, 1, 2, 3
 MMFD_D2Q5, MMFD_D2Q9, MMFD_D3Q7, MMFD_D3Q19 = 0, 1, 2, 3
 MMFD_FP64, MMFD_FP32, MMFD_BF16 = 0, 1, 2
 MMFD_HOST, MMFD_DEVICE = 0, 1
@@ -44,7 +44,7 @@ MMFD_FLAG_TWO_SETS = 0x8
 MMFD_RED_SUM, MMFD_RED_MAXABS, MMFD_RED_NONFINITE = 0, 1, 2
 MMFD_SRC_NONE, MMFD_SRC_S, MMFD_SRC_SU, MMFD_SRC_SM = 0, 1, 2, 3
 
-PDE = {"LCDE": MMFD_LCDE, "NCDE": MMFD_NCDE, "NSE": MMFD_NSE}
+PDE = {"LCDE": MMFD_LCDE, "NCDE": MMFD_NCDE, "NSE": MMFD_NSE, "LWE": MMFD_LWE}
 LATTICE = {"D2Q5": MMFD_D2Q5, "D2Q9": MMFD_D2Q9, "D3Q7": MMFD_D3Q7, "D3Q19": MMFD_D3Q19}
 STORAGE = {"fp64": MMFD_FP64, "fp32": MMFD_FP32, "bf16": MMFD_BF16}
 SOURCE = {"none": MMFD_SRC_NONE, "s": MMFD_SRC_S, "su": MMFD_SRC_SU, "sm": MMFD_SRC_SM}
@@ -124,6 +124,7 @@ SIGNATURES = {
     "mmfd_destroy": (C.c_int, [_VP]),
     "mmfd_solve_three_level": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mmfd_trt_coefficients": (C.c_int, [C.c_double] + [C.POINTER(C.c_double)] * 4),
+    "mmfd_wave_coefficients": (C.c_int, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mmfd_describe": (C.c_int, [C.POINTER(mmfd_desc), C.POINTER(mmfd_info_t)]),
     "mmfd_selftest_wait_timeout": (C.c_int, [_VP, C.c_longlong]),
     "mmfd_strerror": (C.c_char_p, [C.c_int]),
@@ -205,6 +206,13 @@ def mmfd_trt_coefficients(s_minus: float) -> dict:
     out = [(C.c_double * 3)() for _ in range(4)]
     check(lib.mmfd_trt_coefficients(float(s_minus), *out), "mmfd_trt_coefficients")
     return dict(zip(("a", "ahat", "abar", "abarhat"), (tuple(o) for o in out)))
+
+
+def mmfd_wave_coefficients(gamma: float) -> dict:
+    """Keyword arguments a, ahat of make_desc for the wave-equation scheme."""
+    a, ah = (C.c_double * 3)(), (C.c_double * 3)()
+    check(lib.mmfd_wave_coefficients(float(gamma), a, ah), "mmfd_wave_coefficients")
+    return {"a": tuple(a), "ahat": tuple(ah)}
 
 
 def mmfd_create(d: mmfd_desc) -> int:

@@ -221,3 +221,32 @@ def test_source_descriptor_validation(mm):
     info = _describe(mm, pde="LCDE", levels=3, K=K, u=[0.1, 0], source="su", storage="fp64",
                      targets=[0, -1, -1, 0.25, 0.5], **base)
     assert info.bytes_per_lu == 8 * 3 + 8 * 2
+
+
+def test_wave_descriptor(mm):
+    c3 = mm.mmfd_wave_coefficients(3 / 8)
+    assert c3 == {"a": (3 / 8, 5 / 4, 3 / 8), "ahat": (0.0, -1.0, 0.0)}
+    with pytest.raises(mm.MMFDError):
+        mm.mmfd_wave_coefficients(0.0)
+    K = np.diag([0.5, 0.3])
+    base = dict(pde="LWE", levels=3, n=[20, 18], dt=0.5, dx=[1.0, 1.0], K=K, flags=mm.MMFD_FLAG_ALLOW_UNSTABLE)
+    for lat, gamma in [("D2Q5", 3 / 8), ("D2Q9", 3 / 8), ("D2Q9", 1 / 2)]:
+        co = mm.mmfd_wave_coefficients(gamma)
+        info = _describe(mm, lattice=lat, **co, **base)
+        prob = P.problem_lwe(lat, [20, 18], 0.5, [1.0, 1.0], K, co["a"], co["ahat"])
+        assert abs(info.A22 - gamma) < 1e-15 and abs(info.A20 + 1) < 1e-15 and abs(info.A10) < 1e-15
+        assert np.allclose(list(info.d0)[:2], prob.d0[:2], rtol=1e-14)
+        assert np.allclose(np.array([list(r) for r in info.Cmat]).ravel(), prob.Cmat, atol=1e-14)
+        # the constant mode is a double root 1; the oracle's quadratic formula resolves it only to
+        # O(sqrt(eps)), the library takes it exactly
+        assert abs(info.max_lambda - F.max_amplification(prob)) < 1e-7
+        assert info.max_lambda <= 1 + 1e-12
+    co = mm.mmfd_wave_coefficients(3 / 8)
+    for bad, code in [(dict(levels=2), mm.MMFD_ERR_ARG), (dict(u=[0.1, 0.0]), mm.MMFD_ERR_ARG),
+                      (dict(a=(0.6, 1.0, 0.4), ahat=(0.0, -1.0, 0.0)), mm.MMFD_ERR_ARG),
+                      (dict(source="s"), mm.MMFD_ERR_UNSUPPORTED)]:
+        kw = dict(base, lattice="D2Q9", **co)
+        kw.update(bad)
+        with pytest.raises(mm.MMFDError) as e:
+            _describe(mm, **kw)
+        assert e.value.code == code, bad

@@ -1,0 +1,90 @@
+"""GPU parity of the wave-equation scheme (Sec. III.C case (4), Eq. (LWE)): the three-level
+CUDA path through the C ABI against the oracle on the same seeded inputs (FP64 1e-12, FP32 1e-5
+relative to max |value|) on every lattice and on the direct and marching kernels, and Example 3's
+three cases run to an exact periodic standing wave on the GPU.
+"""
+import numpy as np
+import pytest
+
+import gpu_cases as G
+from oracle import oracle as orc
+from oracle import params as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_17057_gb300 import mmfd
+    return mmfd
+
+
+def wave_case(lat, n, storage, gamma=0.45):
+    dim = G.dims(lat)
+    dt, dx = 0.5, [1.0, 1.1, 0.9][:dim]
+    K = np.diag([0.35, 0.3, 0.25][:dim])
+    if lat in ("D2Q9", "D3Q19"):
+        K = K + 0.02 * (1 - np.eye(dim))
+    a, ah = P.wave_coefficients(gamma)
+    kw = dict(pde="LWE", lattice=lat, levels=3, n=n, dt=dt, dx=dx, K=K, a=a, ahat=ah, storage=storage)
+    prob = P.problem_lwe(lat, list(n) + [1] * (3 - len(n)), dt, dx, K, a, ah)
+    return kw, prob
+
+
+@pytest.mark.parametrize("lat", ["D2Q5", "D2Q9", "D3Q7", "D3Q19"])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_wave_matches_oracle(mm, lat, storage, tol):
+    rng = np.random.default_rng(G.RNG_SEED + 110)
+    sizes = [[300, 70], [67, 45]] if G.dims(lat) == 2 else [[150, 21, 9], [40, 21, 9]]
+    kernels = set()
+    for n in sizes:
+        kw, prob = wave_case(lat, n, storage)
+        L0 = [rng.standard_normal(prob.shape)]
+        L1 = [rng.standard_normal(prob.shape)]
+        s = mm.Solver(mm.make_desc(**kw))
+        try:
+            kernels.add(s.get_info().kernel.decode())
+            s.set_fields(L0)
+            s.set_fields(L1, level=1)
+            st0, st1 = s.fields(0), s.fields(1)
+            s.step(6)
+            out = s.fields(0)
+        finally:
+            s.close()
+        ref, _ = orc.run(prob, st0, st1, nsteps=6)
+        assert G.rel_err(out, ref) < tol, (n, G.rel_err(out, ref))
+    assert len(kernels) == 2, kernels
+
+
+def _example3_gpu(mm, case, nx):
+    import test_oracle_wave as TW
+    prob, dx, dt = TW.example3_problem(case, nx)
+    lat, beta, gamma = TW.CASES[case]
+    kw = dict(pde="LWE", lattice=lat, levels=3, n=[nx, nx], dt=dt, dx=[dx, dx], K=0.5 * np.eye(2),
+              storage="fp64", **mm.mmfd_wave_coefficients(gamma))
+    x = np.arange(nx) * dx
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    exact = lambda t: np.cos(2 * np.pi * (X + Y)) * np.cos(2 * np.pi * t)
+    steps = int(round(1.0 / dt))
+    s = mm.Solver(mm.make_desc(**kw))
+    try:
+        s.set_fields([exact(0.0)])
+        s.set_fields([exact(-dt)], level=1)
+        s.step(steps)
+        out = s.fields(0)[0]
+    finally:
+        s.close()
+    ref = exact(steps * dt)
+    return float(np.abs(out - ref).sum() / np.abs(ref).sum()), TW.standing_wave_gre(case, nx)
+
+
+@pytest.mark.parametrize("case", [1, 2, 3])
+def test_example3_standing_wave_on_gpu(mm, case):
+    res = [_example3_gpu(mm, case, nx) for nx in (20, 40, 160)]
+    for gpu, oracle in res[:2]:
+        assert abs(gpu - oracle) < 1e-9 * oracle
+    orders = [np.log2(res[0][0] / res[1][0]), np.log2(res[1][0] / res[2][0]) / 2]
+    assert all(o >= 1.8 for o in orders), (res, orders)
