@@ -504,10 +504,58 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
 
     // store the completed output row yo from acc
     EdgeStore<2, ST> es;
-    auto store_row = [&](int yo, int xb, const T (&acc)[LN][NF]) {
+    // Source terms (SRC != 0) of the output row being stored, add[k] for node xb + k.
+    // SRC == 1 (a source S; M_1F = 0 or S u folded): the source rows y0+i-3 .. y0+i feeding the two
+    // output rows stored in iteration i sit in a rolling register window; the two new rows are
+    // loaded at the top of the iteration, before the stage wait and the pushes, so that their
+    // latency is hidden.  SRC == 2 (S and M_1F fields) reads its rows in the epilogue.
+    [[maybe_unused]] T swin[LEVELS - 1][4][6];
+    auto src_load = [&](int y0, int i, int xb) {
+        if constexpr (SRC == 1) {
+#pragma unroll
+            for (int l = 0; l < LEVELS - 1; ++l) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) swin[l][r][c] = swin[l][r + 2][c];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int row = y0 + i - 1 + r;   // rows past the ghost row ny feed no stored output
+                    if (xb < g.nx && row <= g.ny) {
+                        ld_src6<T>(sa.s[l] + g.at(0, row, 0), xb, g.nx, swin[l][2 + r]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) swin[l][2 + r][c] = T(0);
+                    }
+                }
+            }
+        }
+    };
+    // the output row whose source rows are window rows W0 .. W0 + 2 (y - 1, y, y + 1)
+    auto src_window = [&](auto w0c, T (&add)[4]) {
+        constexpr int W0 = decltype(w0c)::value;
+        constexpr int NP = lat_npair(LAT);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) add[k] = T(0);
+        if constexpr (SRC == 1) {
+#pragma unroll
+        for (int l = 0; l < LEVELS - 1; ++l) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T acc = sa.w.W0[l] * swin[l][W0 + 1][k + 1];
+                static_for<0, NP>([&](auto pc) {
+                    constexpr int P = decltype(pc)::value;
+                    constexpr int EX = pair_e(LAT, P, 0), EY = pair_e(LAT, P, 1);
+                    acc += sa.w.Wp[l][P] * swin[l][W0 + 1 + EY][k + 1 + EX] +
+                           sa.w.Wm[l][P] * swin[l][W0 + 1 - EY][k + 1 - EX];
+                });
+                add[k] += acc;
+            }
+        }
+        }
+    };
+    auto store_row = [&](int yo, int xb, const T (&acc)[LN][NF], const T (&add)[4]) {
         const long long nb = (long long)yo * g.nx;
-        [[maybe_unused]] T add[4];
-        if constexpr (SRC != 0) source_quad<LAT, SRC, LEVELS, T>(g, sa, yo, 0, xb, add);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             S* fo = out + (size_t)f * g.fs;
@@ -536,6 +584,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
         const int nrows = (hrows + 2 + RPS - 1) / RPS * RPS;       // staged input rows
         const int xb = x0 + lane * LN;
         static_assert(LN == 4, "the edge store covers four nodes per lane");
+        static_assert(SRC != 1 || RPS == 2, "the source window holds the rows of two output rows");
         es.init(g, xb, true);
 #pragma unroll
         for (int k = 0; k < LN; ++k)
@@ -543,6 +592,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
             for (int f = 0; f < NF; ++f) acc0[k][f] = acc1[k][f] = acc2[k][f] = acc3[k][f] = T(0);
         for (int i = 0; i < nrows; i += RPS) {
             const int s = cs;
+            if constexpr (SRC == 1) src_load(y0, i, xb);
             const bool ok = mbar_wait_bounded(&full[s], cphase);
             if (__any_sync(0xffffffffu, !ok)) {
                 failed = true;
@@ -560,9 +610,18 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
             }
             // input row i (y0 - 1 + i) completes output row y0 + i - 2 (all lanes take part in
             // the store; lanes beyond nx write nothing)
-            if (i >= 2) store_row(y0 + i - 2, xb, acc0);
+            [[maybe_unused]] T add[4] = {T(0), T(0), T(0), T(0)};
+            if (i >= 2) {
+                if constexpr (SRC == 1) src_window(std::integral_constant<int, 0>{}, add);
+                if constexpr (SRC == 2) source_quad<LAT, SRC, LEVELS, T>(g, sa, y0 + i - 2, 0, xb, add);
+                store_row(y0 + i - 2, xb, acc0, add);
+            }
             if constexpr (RPS == 2) {
-                if (i >= 1 && i - 1 < hrows) store_row(y0 + i - 1, xb, acc1);
+                if (i >= 1 && i - 1 < hrows) {
+                    if constexpr (SRC == 1) src_window(std::integral_constant<int, 1>{}, add);
+                    if constexpr (SRC == 2) source_quad<LAT, SRC, LEVELS, T>(g, sa, y0 + i - 1, 0, xb, add);
+                    store_row(y0 + i - 1, xb, acc1, add);
+                }
             }
 #pragma unroll
             for (int k = 0; k < LN; ++k)
