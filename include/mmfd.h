@@ -40,8 +40,12 @@ extern "C" {
 /* MMFD_LWE: the linear wave equation d_t^2 phi = div(K grad phi) (Eq. (LWE)), three-level. */
 typedef enum { MMFD_LCDE = 0, MMFD_NCDE = 1, MMFD_NSE = 2, MMFD_LWE = 3 } mmfd_pde;
 typedef enum { MMFD_D2Q5 = 0, MMFD_D2Q9 = 1, MMFD_D3Q7 = 2, MMFD_D3Q19 = 3 } mmfd_lattice;
-/* Storage of the level buffers.  BF16: each value stored as bf16(v - ref[field]) and
- * read back as ref[field] + v; all arithmetic in FP32.  FP64: arithmetic in FP64. */
+/* Storage of the level buffers.  FP32 and BF16 levels hold offsets v - ref[field] from a reference
+ * state (BF16: bf16(v - ref[field])); values are read back as ref[field] + offset.  The LCDE, wave
+ * and NSE updates are affine in the stored scalar / density with coefficients summing to one, so
+ * their kernels step the offsets directly in FP32 (no precision spent on the common value); the
+ * NCDE's FP32 levels hold values (ref ignored) and its BF16 levels are stepped on values.  FP64:
+ * values, arithmetic in FP64. */
 typedef enum { MMFD_FP64 = 0, MMFD_FP32 = 1, MMFD_BF16 = 2 } mmfd_storage;
 enum { MMFD_HOST = 0, MMFD_DEVICE = 1 };
 enum { MMFD_DT_F64 = 0, MMFD_DT_F32 = 1 };          /* element type of user buffers */
@@ -95,7 +99,8 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        [1] level t - dt (three-level), each (a_{-1}, a_0, a_1).  With a = d2 and
  *                        abar = bar_d2 this is the TRT MesoFD scheme of Eq. (2-1b) (even set d2,
  *                        odd set d1; momentum: even set bar_d1, odd set bar_d2).
- *  storage, ref[4]       storage type; BF16 offsets per field (default ref = {rho0 or 0, 0, ..}).
+ *  storage, ref[4]       storage type; FP32 / BF16 reference state per field (default ref = {rho0
+ *                        for the NSE density, 0 otherwise}); NSE velocity references must be 0.
  *  flags                 MMFD_FLAG_*.
  *  temporal_depth        time steps fused per kernel launch (temporal blocking): 1 = none;
  *                        T >= 2 asks for T; 0 asks for the deepest available.  Blocking is

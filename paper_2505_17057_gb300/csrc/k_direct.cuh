@@ -70,17 +70,17 @@ __device__ __forceinline__ void direct_node(const Geom& g, const void* __restric
         const S* in = static_cast<const S*>(l == 0 ? in0v : in1v);
         if constexpr (PDE == PDE_LCDE) {
             // f_j^eq = phi ubar_j (Eq. (TforMMFD-0)): the update is a fixed linear stencil.
-            T s = cf.W0[l] * Tr::load(in + c0, cf.ref[0]);
+            T s = cf.W0[l] * kload<ST, PDE>(in + c0, cf.ref[0]);
             static_for<0, NP>([&](auto pc) {
                 constexpr int P = decltype(pc)::value;
                 const long long off = pair_offset<LAT>(g, P);
-                s += cf.Wp[l][P] * Tr::load(in + c0 + off, cf.ref[0]) + cf.Wm[l][P] * Tr::load(in + c0 - off, cf.ref[0]);
+                s += cf.Wp[l][P] * kload<ST, PDE>(in + c0 + off, cf.ref[0]) + cf.Wm[l][P] * kload<ST, PDE>(in + c0 - off, cf.ref[0]);
             });
             acc[0] += s;
         } else {
             T f[NF];
 #pragma unroll
-            for (int i = 0; i < NF; ++i) f[i] = Tr::load(in + i * g.fs + c0, cf.ref[i]);
+            for (int i = 0; i < NF; ++i) f[i] = kload<ST, PDE>(in + i * g.fs + c0, cf.ref[i]);
             Basis<LAT, PDE, T> b0;
             b0.init(f, cf);
             acc[0] += cf.a0[l] * b0.A() + cf.ap[l] * b0.rest(cf);
@@ -94,8 +94,8 @@ __device__ __forceinline__ void direct_node(const Geom& g, const void* __restric
                 T fp[NF], fm[NF];
 #pragma unroll
                 for (int i = 0; i < NF; ++i) {
-                    fp[i] = Tr::load(in + i * g.fs + c0 + off, cf.ref[i]);
-                    fm[i] = Tr::load(in + i * g.fs + c0 - off, cf.ref[i]);
+                    fp[i] = kload<ST, PDE>(in + i * g.fs + c0 + off, cf.ref[i]);
+                    fm[i] = kload<ST, PDE>(in + i * g.fs + c0 - off, cf.ref[i]);
                 }
                 Basis<LAT, PDE, T> bp, bm;
                 bp.init(fp, cf);
@@ -122,7 +122,7 @@ __device__ __forceinline__ void direct_node(const Geom& g, const void* __restric
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
         const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, node, i) : 0u;
-        store_with_ghosts<D>(out + i * g.fs, g, x, y, z, Tr::pack(acc[i], cf.ref[i], rnd));
+        store_with_ghosts<D>(out + i * g.fs, g, x, y, z, kpack<ST, PDE>(acc[i], cf.ref[i], rnd));
     }
 }
 

@@ -21,8 +21,9 @@
 
 namespace mmfd {
 
-// Four consecutive values of storage type S from shared memory (aligned) into T.
-template <int ST>
+// Four consecutive values of storage type S from shared memory (aligned) into T (offsets, or
+// values for the NCDE's BF16 levels: see kload).
+template <int ST, int PDE>
 __device__ __forceinline__ void lds4(const unsigned char* p, typename Storage<ST>::T ref, typename Storage<ST>::T v[4]) {
     if constexpr (ST == ST_F32) {
         const float4 q = *reinterpret_cast<const float4*>(p);
@@ -33,10 +34,14 @@ __device__ __forceinline__ void lds4(const unsigned char* p, typename Storage<ST
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     } else {
         const uint2 q = *reinterpret_cast<const uint2*>(p);
-        v[0] = ref + __uint_as_float(q.x << 16);
-        v[1] = ref + __uint_as_float(q.x & 0xffff0000u);
-        v[2] = ref + __uint_as_float(q.y << 16);
-        v[3] = ref + __uint_as_float(q.y & 0xffff0000u);
+        v[0] = __uint_as_float(q.x << 16);
+        v[1] = __uint_as_float(q.x & 0xffff0000u);
+        v[2] = __uint_as_float(q.y << 16);
+        v[3] = __uint_as_float(q.y & 0xffff0000u);
+        if constexpr (!offset_arith<PDE>()) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] += ref;
+        }
     }
 }
 
@@ -405,14 +410,14 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
 #pragma unroll
                 for (int k4 = 0; k4 < LN; k4 += 4) {
                     T v4[4];
-                    lds4<ST>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
+                    lds4<ST, PDE>(base + (size_t)(ALIGN + lane * LN + k4) * ES, cf.ref[f], v4);
                     raw[1 + k4][f] = v4[0];
                     raw[2 + k4][f] = v4[1];
                     raw[3 + k4][f] = v4[2];
                     raw[4 + k4][f] = v4[3];
                 }
-                raw[0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
-                raw[LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
+                raw[0][f] = kload<ST, PDE>(sp + ALIGN + lane * LN - 1, cf.ref[f]);
+                raw[LN + 1][f] = kload<ST, PDE>(sp + ALIGN + lane * LN + LN, cf.ref[f]);
             }
             static_for<0, LN + 2>([&](auto cc) {
                 constexpr int C = decltype(cc)::value - 1;  // node offset -1 .. LN
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                     if constexpr (SRC != 0) {
                         if (f == 0) v += add[k];
                     }
-                    sv[k] = Tr::pack(v, cf.ref[f], rnd);
+                    sv[k] = kpack<ST, PDE>(v, cf.ref[f], rnd);
                 }
                 es.put(fo, g, xb + k4, yo, 0, sv);
             }

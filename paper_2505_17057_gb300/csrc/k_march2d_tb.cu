@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k, 0) : 0u;
-                sv[k] = Tr::pack(raw[1 + k], cf.ref[0], rnd);
+                sv[k] = kpack<ST, PDE>(raw[1 + k], cf.ref[0], rnd);
             }
             es.put(out, g, xb, yo, 0, sv);
         }
@@ -203,13 +203,13 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
     auto load_row = [&](const unsigned char* base, T (&raw)[LN + 2]) {
         const S* sp = reinterpret_cast<const S*>(base);
         T v4[4];
-        lds4<ST>(base + (size_t)(ALIGN + lane * LN) * ES, cf.ref[0], v4);
+        lds4<ST, PDE>(base + (size_t)(ALIGN + lane * LN) * ES, cf.ref[0], v4);
         raw[1] = v4[0];
         raw[2] = v4[1];
         raw[3] = v4[2];
         raw[4] = v4[3];
-        raw[0] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[0]);
-        raw[LN + 1] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[0]);
+        raw[0] = kload<ST, PDE>(sp + ALIGN + lane * LN - 1, cf.ref[0]);
+        raw[LN + 1] = kload<ST, PDE>(sp + ALIGN + lane * LN + LN, cf.ref[0]);
     };
 
     for (int item = wid; item < nitems && !failed; item += wstride) {

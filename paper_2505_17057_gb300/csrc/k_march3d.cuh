@@ -141,13 +141,13 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
                         const unsigned char* rowp = slot(s, l * NF + f) + (size_t)(warp + dy) * ROWB;
                         const S* sp = reinterpret_cast<const S*>(rowp);
                         T v4[4];
-                        lds4<ST>(rowp + (size_t)(ALIGN + lane * LN) * ES, cf.ref[f], v4);
+                        lds4<ST, PDE>(rowp + (size_t)(ALIGN + lane * LN) * ES, cf.ref[f], v4);
                         raw[dy][1][f] = v4[0];
                         raw[dy][2][f] = v4[1];
                         raw[dy][3][f] = v4[2];
                         raw[dy][4][f] = v4[3];
-                        raw[dy][0][f] = Tr::load(sp + ALIGN + lane * LN - 1, cf.ref[f]);
-                        raw[dy][LN + 1][f] = Tr::load(sp + ALIGN + lane * LN + LN, cf.ref[f]);
+                        raw[dy][0][f] = kload<ST, PDE>(sp + ALIGN + lane * LN - 1, cf.ref[f]);
+                        raw[dy][LN + 1][f] = kload<ST, PDE>(sp + ALIGN + lane * LN + LN, cf.ref[f]);
                     }
                 static_for<0, 3>([&](auto dyc) {
                     constexpr int DY = decltype(dyc)::value - 1;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
                         if constexpr (SRC != 0) {
                             if (f == 0) v += add[n];
                         }
-                        sv[n] = Tr::pack(v, cf.ref[f], rnd);
+                        sv[n] = kpack<ST, PDE>(v, cf.ref[f], rnd);
                     }
                     S* fo = out + (size_t)f * g.fs;
                     es.put(fo, g, xb, y, zo, sv);

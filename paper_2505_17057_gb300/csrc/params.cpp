@@ -275,10 +275,17 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
         if (!(r.w[j] >= 0.0)) return fail(msg, MMFD_ERR_ARG, "lattice weights must be non-negative (App. A)");
     }
 
-    // ---- BF16 offsets
+    // ---- storage offsets: FP32 and BF16 levels hold v - ref.  FP64 levels, and FP32 levels of the
+    // NCDE (whose update is nonlinear in phi and runs on values), hold values.  The NSE velocity
+    // reference must be zero: the update runs on the stored offsets, and it is affine in the
+    // density only.
     for (int f = 0; f < 4; ++f) {
         double v = d.ref[f];
         if (std::isnan(v)) v = (d.pde == PDE_NSE && f == 0) ? d.rho0 : 0.0;
+        if (!finite(v)) return fail(msg, MMFD_ERR_ARG, "non-finite storage reference");
+        if (d.storage == ST_F64 || (d.storage == ST_F32 && d.pde == PDE_NCDE)) v = 0.0;
+        if (d.pde == PDE_NSE && f >= 1 && f < r.nf && v != 0.0)
+            return fail(msg, MMFD_ERR_ARG, "NSE velocity references must be zero");
         r.ref[f] = v;
     }
 

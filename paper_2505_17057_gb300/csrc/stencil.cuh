@@ -10,34 +10,63 @@
 namespace mmfd {
 
 // ------------------------------------------------------------------ storage traits
+// FP32 and BF16 levels hold offsets v - ref[field] from a reference state (FP64 levels hold v).
+// load / pack convert between stored offsets and values; raw / pack_raw move the offsets as they
+// are (the kernels' offset arithmetic, see kload below).
 template <int ST> struct Storage;
 template <> struct Storage<ST_F64> {
     using S = double;
     using T = double;
+    __device__ static T raw(const S* p) { return *p; }
+    __device__ static S pack_raw(T v, unsigned) { return v; }
     __device__ static T load(const S* p, T) { return *p; }
     __device__ static S pack(T v, T, unsigned) { return v; }
 };
 template <> struct Storage<ST_F32> {
     using S = float;
     using T = float;
-    __device__ static T load(const S* p, T) { return *p; }
-    __device__ static S pack(T v, T, unsigned) { return v; }
+    __device__ static T raw(const S* p) { return *p; }
+    __device__ static S pack_raw(T v, unsigned) { return v; }
+    __device__ static T load(const S* p, T ref) { return ref + *p; }
+    __device__ static S pack(T v, T ref, unsigned) { return v - ref; }
 };
 template <> struct Storage<ST_BF16> {
     using S = __nv_bfloat16;
     using T = float;
-    __device__ static T load(const S* p, T ref) { return ref + __bfloat162float(*p); }
-    // round-to-nearest-even of the offset (rnd == 0), or stochastic rounding with the
-    // 16 random low bits `rnd` added before truncation.
-    __device__ static S pack(T v, T ref, unsigned rnd) {
-        float d = v - ref;
+    __device__ static T raw(const S* p) { return __bfloat162float(*p); }
+    // round-to-nearest-even (rnd == 0), or stochastic rounding with the 16 random low bits
+    // `rnd` added before truncation.
+    __device__ static S pack_raw(T d, unsigned rnd) {
         if (rnd == 0u) return __float2bfloat16_rn(d);
         unsigned b = __float_as_uint(d);
         if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(d);  // inf / nan
         b += (rnd & 0xffffu);
         return __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
+    __device__ static T load(const S* p, T ref) { return ref + raw(p); }
+    __device__ static S pack(T v, T ref, unsigned rnd) { return pack_raw(v - ref, rnd); }
 };
+
+// Offset arithmetic.  The LCDE (and wave) update and the He-Luo NSE update are affine in the
+// stored scalar / density with coefficients summing to A_00 = 1 (and the momentum sees the
+// density only through differences), so they run on the stored offsets directly: the level t+dt
+// offset comes out of the same stencil applied to the level-t offsets, with no reference added
+// or subtracted and no precision lost to a large common value.  The NCDE update is nonlinear in
+// phi and works on values: BF16 levels add the reference on load (FP32 NCDE levels are stored
+// without an offset).  NSE velocities have zero reference (checked on the host).
+template <int PDE>
+__host__ __device__ constexpr bool offset_arith() { return PDE != PDE_NCDE; }
+
+template <int ST, int PDE>
+__device__ __forceinline__ typename Storage<ST>::T kload(const typename Storage<ST>::S* p, typename Storage<ST>::T ref) {
+    if constexpr (ST == ST_BF16 && !offset_arith<PDE>()) return Storage<ST>::load(p, ref);
+    else return Storage<ST>::raw(p);
+}
+template <int ST, int PDE>
+__device__ __forceinline__ typename Storage<ST>::S kpack(typename Storage<ST>::T v, typename Storage<ST>::T ref, unsigned rnd) {
+    if constexpr (ST == ST_BF16 && !offset_arith<PDE>()) return Storage<ST>::pack(v, ref, rnd);
+    else return Storage<ST>::pack_raw(v, rnd);
+}
 
 // SplitMix64 finaliser as a counter-based hash (stochastic rounding bits).
 __device__ __forceinline__ unsigned sr_bits(unsigned long long seed, long long step, long long node, int f) {

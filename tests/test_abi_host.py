@@ -250,3 +250,19 @@ def test_wave_descriptor(mm):
         with pytest.raises(mm.MMFDError) as e:
             _describe(mm, **kw)
         assert e.value.code == code, bad
+
+
+def test_storage_reference_rules(mm):
+    # NSE velocities have zero reference (their update is not affine in u); non-finite references
+    # are rejected; FP64 levels hold values whatever the reference
+    base = dict(pde="NSE", lattice="D2Q9", levels=2, n=[16, 16], dt=1.0, dx=[1, 1], a=(1, 0, 0), abar=(1, 0, 0))
+    for st in ("fp32", "bf16"):
+        mm.mmfd_describe(mm.make_desc(**base, storage=st, ref=[1.0, 0.0, 0.0]))
+        with pytest.raises(mm.MMFDError) as e:
+            mm.mmfd_describe(mm.make_desc(**base, storage=st, ref=[1.0, 0.01, 0.0]))
+        assert e.value.code == mm.MMFD_ERR_ARG
+    mm.mmfd_describe(mm.make_desc(**base, storage="fp64", ref=[1.0, 0.01, 0.0]))
+    with pytest.raises(mm.MMFDError) as e:
+        mm.mmfd_describe(mm.make_desc(pde="LCDE", lattice="D2Q9", levels=2, n=[16, 16], dt=1.0, dx=[1, 1],
+                                      K=np.eye(2) * 0.01, storage="fp32", ref=[float("inf")]))
+    assert e.value.code == mm.MMFD_ERR_ARG
