@@ -1,0 +1,139 @@
+"""Accuracy of the GPU path on the benchmark configurations, measured on the device: errors
+against closed-form solutions and between the storage precisions (FP64, FP32, BF16-offset).
+
+    python -m paper_2505_17057_gb300.accuracy [--quick] [--case NAME ...]
+
+prints one JSON line per case.  The closed forms are the analytic Taylor-Green decay (the NSE
+workloads; velocity error, GRE = sum |u - u*| / sum |u*| over both components) and the exact
+solution of the periodic linear CDE for the trigonometric interpolant of the initial field (the
+64^2 CDE workload).  Where no closed form exists (NCDE, 3D) the FP64 GPU run of the same
+configuration is the reference.  The FP64 GPU path itself is checked against the FP64 CPU oracle
+by the test suite (1e-12), so its error against a closed form is the scheme's discretisation
+error.  --quick runs reduced sizes and step counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+from . import configs, inputs, mmfd
+
+
+def _run(desc_kw, fields, steps, storage, fields_m1=None, flags=0, **extra):
+    kw = dict(desc_kw)
+    kw["storage"] = storage
+    if storage != "fp64" and "ref" not in kw and kw["pde"] != "NSE":
+        kw["ref"] = [float(np.mean(fields[0]))]
+    s = mmfd.Solver(mmfd.make_desc(**kw, flags=flags, **extra))
+    try:
+        s.set_fields(fields)
+        if fields_m1 is not None:
+            s.set_fields(fields_m1, level=1)
+        m0 = s.reduce(mmfd.MMFD_RED_SUM)[0]
+        s.step(steps)
+        out = s.fields(0)
+        m1 = s.reduce(mmfd.MMFD_RED_SUM)[0]
+    finally:
+        s.close()
+    # change of sum(phi) (or sum(rho)) relative to sum |phi0|: exact conservation gives rounding only
+    return out, (m1 - m0) / max(float(np.abs(fields[0]).sum()), 1e-300)
+
+
+def _gre(a, b):
+    return float(sum(np.abs(x - y).sum() for x, y in zip(a, b)) / sum(np.abs(y).sum() for y in b))
+
+
+def _maxrel(a, b):
+    return float(max(np.abs(x - y).max() for x, y in zip(a, b)) / max(np.abs(y).max() for y in b))
+
+
+def tgv(n=4096, re=100.0, steps=5000):
+    """Taylor-Green vortex (D2Q9 He-Luo NSE, LBGK tau = 1): velocity GRE / max error against the
+    analytic decay after `steps` steps, per storage."""
+    desc, fields, _ = configs.tgv2d_4096(n=n, re=re, storage="fp64")
+    u0 = re * configs.NU_LBGK / n
+    _, ue, ve = inputs.taylor_green_2d(n, n, u0, configs.NU_LBGK, float(steps))
+    res = {"case": f"tgv2d_{n}", "re": re, "steps": steps, "reference": "analytic Taylor-Green decay"}
+    outs = {}
+    for st, extra in [("fp64", {}), ("fp32", {}), ("bf16", {}), ("bf16_sr", {"seed": 5})]:
+        storage = "bf16" if st.startswith("bf16") else st
+        flags = mmfd.MMFD_FLAG_STOCHASTIC_ROUND if st == "bf16_sr" else 0
+        out, _ = _run(desc, fields, steps, storage, flags=flags, **extra)
+        outs[st] = out
+        res[st] = {"gre_u": _gre(out[1:], [ue, ve]), "max_u": _maxrel(out[1:], [ue, ve])}
+    for st in ("fp32", "bf16", "bf16_sr"):
+        res[st]["gre_ratio_to_fp64"] = res[st]["gre_u"] / res["fp64"]["gre_u"]
+        res[st]["max_rel_vs_fp64"] = _maxrel(outs[st][1:], outs["fp64"][1:])
+    return res
+
+
+def cde2d_64():
+    """The 64^2 linear CDE (Gaussian hill, 200 steps, FP64) on D2Q5 and D2Q9 against the exact
+    solution of the PDE for the periodic interpolant of the initial field."""
+    res = {"case": "cde2d_64", "reference": "exact periodic LCDE solution (Fourier)"}
+    for lat in ("D2Q5", "D2Q9"):
+        desc, fields, steps = configs.cde2d_64(lat)
+        flags = mmfd.MMFD_FLAG_DROP_OFFDIAG if lat == "D2Q5" else 0
+        out, mass = _run(desc, fields, steps, "fp64", flags=flags)
+        phi0 = fields[0]
+        K = np.asarray(desc["K"], dtype=float)
+        if lat == "D2Q5":
+            K = np.diag(np.diag(K))     # the axis lattice carries diag(K) only
+        u = desc["u"]
+        ky = 2 * np.pi * np.fft.fftfreq(phi0.shape[0])
+        kx = 2 * np.pi * np.fft.fftfreq(phi0.shape[1])
+        KY, KX = np.meshgrid(ky, kx, indexing="ij")
+        expo = 1j * (KX * u[0] + KY * u[1]) + K[0, 0] * KX ** 2 + 2 * K[0, 1] * KX * KY + K[1, 1] * KY ** 2
+        exact = np.real(np.fft.ifftn(np.fft.fftn(phi0) * np.exp(-expo * steps * desc["dt"])))
+        res[lat] = {"gre": _gre(out, [exact]), "max_rel": _maxrel(out, [exact]), "mass_drift": mass}
+    return res
+
+
+def ncde2d(n=1024, steps=10000):
+    """The three-level NCDE workload: FP32 and BF16 (stochastic rounding) against the FP64 GPU run."""
+    desc, fields, _ = configs.ncde2d_1024(n=n, storage="fp64")
+    ref, m64 = _run(desc, fields, steps, "fp64")
+    res = {"case": f"ncde2d_{n}", "steps": steps, "reference": "FP64 GPU run", "fp64": {"mass_drift": m64}}
+    for st, flags in [("fp32", 0), ("bf16_sr", mmfd.MMFD_FLAG_STOCHASTIC_ROUND)]:
+        out, mass = _run(desc, fields, steps, "bf16" if st == "bf16_sr" else st, flags=flags, seed=7)
+        res[st] = {"max_rel_vs_fp64": _maxrel(out, ref), "gre_vs_fp64": _gre(out, ref), "mass_drift": mass}
+    return res
+
+
+def three_d(kind="cde3d", n=512, steps=1000):
+    """The 3D workloads: FP32 and BF16-offset against the FP64 GPU run."""
+    maker = configs.cde3d_512 if kind == "cde3d" else configs.nse3d_512
+    desc, fields, _ = maker(n=n, storage="fp64")
+    ref, m64 = _run(desc, fields, steps, "fp64")
+    res = {"case": f"{kind}_{n}", "steps": steps, "reference": "FP64 GPU run", "fp64": {"mass_drift": m64}}
+    for st in ("fp32", "bf16"):
+        out, mass = _run(desc, fields, steps, st)
+        res[st] = {"max_rel_vs_fp64": _maxrel(out, ref), "gre_vs_fp64": _gre(out, ref), "mass_drift": mass}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--case", nargs="*", default=["cde2d", "tgv100", "tgv1000", "ncde2d", "cde3d", "nse3d"])
+    args = ap.parse_args()
+    q = args.quick
+    runs = {
+        "cde2d": lambda: cde2d_64(),
+        "tgv100": lambda: tgv(512 if q else 4096, 100.0, 1000 if q else 5000),
+        "tgv1000": lambda: tgv(512 if q else 4096, 1000.0, 1000 if q else 5000),
+        "ncde2d": lambda: ncde2d(256 if q else 1024, 1000 if q else 10000),
+        "cde3d": lambda: three_d("cde3d", 128 if q else 512, 200 if q else 1000),
+        "nse3d": lambda: three_d("nse3d", 128 if q else 512, 200 if q else 1000),
+    }
+    import torch
+    torch.cuda.init()
+    for c in args.case:
+        print(json.dumps(runs[c]()), flush=True)
+
+
+if __name__ == "__main__":
+    main()
