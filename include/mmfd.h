@@ -105,7 +105,8 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *  temporal_depth        time steps fused per kernel launch (temporal blocking): 1 = none;
  *                        T >= 2 asks for T; 0 asks for the deepest available.  Blocking is
  *                        available for 2D two-level LCDE / NCDE grids with nx >= 128 and
- *                        ny >= 2T, up to T = 2 (FP64), 4 (FP32), 5 (BF16) -- the x ghost
+ *                        ny >= 2T, and for 3D two-level LCDE grids (D3Q7 / D3Q19) with
+ *                        nx >= 128, up to T = 2 (FP64), 4 (FP32), 5 (BF16) -- the x ghost
  *                        columns of the padded layout hold that many levels.  Larger requests
  *                        are clamped, other configurations run unblocked; mmfd_get_info reports
  *                        the depth in use.  mmfd_step(n) runs n / T blocked launches and the

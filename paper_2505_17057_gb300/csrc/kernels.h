@@ -51,6 +51,9 @@ LaunchFn find_march3d(int lat, int pde, int levels, int st);
 // It reads the level through the same 2-row-box tensor maps as k_march2d.
 LaunchFn find_march2d_tb(int lat, int pde, int levels, int st, int depth);
 int march2d_tb_max_depth(int st);
+// Temporally blocked 3D kernel (two-level LCDE on D3Q7 / D3Q19; nullptr elsewhere): depths as in
+// 2D.  It reads the level through tensor maps of one-row boxes ((128 + 2 x 16 B) x 1 x 1).
+LaunchFn find_march3d_tb(int lat, int pde, int levels, int st, int depth);
 // The same with source terms in the store epilogue (src as for find_direct_src; LCDE / NCDE).
 LaunchFn find_march3d_src(int lat, int pde, int levels, int st, int src);
 // Rows of the x-y tile a 3D march CTA stages per plane (the TMA box is 128+halo x rows+2 x 1).

@@ -220,6 +220,7 @@ int solver_step(Solver* s, long long nsteps) {
         solver_launch_args(s, a);
         if (blocked) {
             // the blocked kernel (two-level solvers) writes level t + depth dt into next()
+            solver_blocked_maps(s, a);
             a.ex.step = s->steps_done + s->depth;
             cudaError_t e = s->fn_block(a);
             if (e != cudaSuccess) return cuda_fail(e, "blocked step kernel");
@@ -321,12 +322,22 @@ int solver_error_norms(Solver* s, int field, const void* ref, int where, int dty
     return MMFD_OK;
 }
 
+void solver_blocked_maps(Solver* s, LaunchArgs& a) {
+    if (s->r.dim == 3) {
+        s->launch_maps.m[0] = s->tbmaps[s->cur];
+        a.maps = &s->launch_maps;
+    }
+}
+
 void solver_use_depth(Solver* s, int depth) {
-    LaunchFn fb = depth >= 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth) : nullptr;
+    LaunchFn fb = nullptr;
+    if (depth >= 2)
+        fb = s->r.dim == 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth)
+                           : find_march3d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth);
     if (fb) {
         s->fn_block = fb;
         s->depth = depth;
-        s->kernel_name = "k_march2d_tb";
+        s->kernel_name = s->r.dim == 2 ? "k_march2d_tb" : "k_march3d_tb";
     } else {
         s->fn_block = nullptr;
         s->depth = 1;
@@ -403,6 +414,20 @@ int solver_pick_kernels(Solver* s) {
             s->use_tma = true;
             s->kernel_name = srcv ? "k_march3d_src" : "k_march3d";
             s->H = 0;
+            // temporal blocking (two-level LCDE): the blocked kernel streams one-row boxes of the
+            // level, with rows and planes wrapped periodically, so any ny and nz will do
+            if (!srcv && s->desc.temporal_depth != 1 &&
+                find_march3d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
+                bool ok = true;
+                for (int b = 0; b < s->nlev && ok; ++b)
+                    ok = encode_field_map(&s->tbmaps[b], s->lev[b], s->r.st, s->g, 128 + 2 * (16 / s->g.es), 1, 1) == 0;
+                if (ok) {
+                    s->max_depth = march2d_tb_max_depth(s->r.st);
+                    int want = s->desc.temporal_depth == 0 ? s->max_depth : s->desc.temporal_depth;
+                    if (want > s->max_depth) want = s->max_depth;
+                    solver_use_depth(s, want);
+                }
+            }
             return MMFD_OK;
         }
     }

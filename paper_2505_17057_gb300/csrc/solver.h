@@ -37,6 +37,7 @@ struct Solver {
     bool fields_set = false;
     bool use_tma = false;                        // kernel family consumes tensor maps
     CUtensorMap tmaps[3][4];                     // per level buffer, per field
+    CUtensorMap tbmaps[3];                       // 3D blocked kernel: one-row boxes of field 0 per buffer
     TmapSet launch_maps;                         // assembled per launch (inputs of this step)
     int H = 0;                                   // rows / planes per CTA
     void* srcbuf[2] = {nullptr, nullptr};        // source levels (compute type, ghosted layout)
@@ -71,6 +72,8 @@ int solver_check_flag(Solver* s);
 void solver_launch_args(Solver* s, LaunchArgs& a);
 // Switch to temporal depth `depth` (1 = unblocked; must not exceed max_depth).
 void solver_use_depth(Solver* s, int depth);
+// The input maps of the blocked kernel (after solver_launch_args; the 3D one reads one-row boxes).
+void solver_blocked_maps(Solver* s, LaunchArgs& a);
 // Time the candidate configurations and keep the fastest (mmfd_autotune).
 int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out);
 
