@@ -76,6 +76,8 @@ KERNEL_SOURCES = {
                   "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     "k_march2d_src": ["k_march2d_src.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
                       "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+    "k_march3d_tb": ["k_march3d_tb.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
+                     "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
 }
 
 
