@@ -64,15 +64,14 @@ __device__ __forceinline__ void tb3_push(const Coef<T>& cf, const T (&raw)[3][6]
         // plane of the input, the z parts to the planes below (plus) and above (minus) it
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const T vp = raw[1 + EY][k + 1 + EX];
-            const T vm = raw[1 - EY][k + 1 - EX];
+            const T vp = raw[1 + EY][k + 1 + EX];   // phi(x + e) for the node's own plane ...
+            const T vm = raw[1 - EY][k + 1 - EX];   // ... and phi(x - e)
             if constexpr (EZ == 0) {
                 accC[k] += cf.Wp[0][P] * vp + cf.Wm[0][P] * vm;
             } else {
-                // input plane z feeds node (x - e) of plane z - 1 through the plus term and node
-                // (x + e) of plane z + 1 through the minus term
-                accP[k] += cf.Wp[0][P] * raw[1 + EY][k + 1 + EX];
-                accN[k] += cf.Wm[0][P] * raw[1 - EY][k + 1 - EX];
+                // with e_z = 1 the input plane z is x + e for plane z - 1 and x - e for plane z + 1
+                accP[k] += cf.Wp[0][P] * vp;
+                accN[k] += cf.Wm[0][P] * vm;
             }
         }
     });

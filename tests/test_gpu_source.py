@@ -10,6 +10,7 @@ import pytest
 
 import gpu_cases as G
 from oracle import oracle as orc
+from oracle import params as P
 
 pytestmark = pytest.mark.gpu
 
@@ -240,3 +241,41 @@ def test_march_source_matches_direct(mm, monkeypatch, storage, tol, lat, n):
         assert np.all(np.abs(a - b) <= G.bf16_ulp(b) + 1e-6 * np.abs(b))
     else:
         assert np.abs(a - b).max() <= tol * np.abs(b).max()
+
+
+@pytest.mark.parametrize("n", [[1, 7], [5, 1], [1, 1], [2, 3, 1], [1, 1, 3]])
+def test_source_degenerate_grids(mm, n):
+    # grids one node wide in some direction: every neighbour is a periodic image of the node
+    rng = np.random.default_rng(G.RNG_SEED + 106)
+    lat = "D2Q9" if len(n) == 2 else "D3Q19"
+    kw, prob = source_case(lat, "LCDE", 3, n, "fp64", "sm")
+    out, ref = run_both(mm, kw, prob, rng, 3)
+    assert G.rel_err(out, ref) < 1e-12
+
+
+def test_source_full_size_on_samples(mm):
+    # the benchmark workload (Example 1's CDE with a time-dependent source at 4096^2, FP32) in the
+    # bench's launch configuration: one step against the FP64 oracle on sampled nodes
+    from paper_2505_17057_gb300 import configs
+    import test_gpu_fullsize as FS
+    kw, f0, fm1, source = configs.srccde2d_4096(n=4096, storage="fp32")
+    s = mm.Solver(mm.make_desc(**kw))
+    try:
+        assert s.get_info().kernel.decode() == "k_march2d_src"
+        s.set_fields(f0)
+        s.set_fields(fm1, level=1)
+        st0, st1 = s.fields(0), s.fields(1)
+        S0, Sm1 = [np.float32(x).astype(np.float64) for x in source(0)], [np.float32(x).astype(np.float64) for x in source(-1)]
+        s.set_source(source(-1), level=1)
+        s.set_source(source(0))
+        s.step(1)
+        out = s.fields(0)[0]
+    finally:
+        s.close()
+    a, ah = kw["a"], kw["ahat"]
+    prob = P.problem_lcde("D2Q9", 3, kw["n"], kw["dt"], kw["dx"], kw["K"], kw["u"], a, ah)
+    prob.source, prob.b, prob.bhat = "su", kw["b"], kw["bhat"]
+    nodes = FS.sample_nodes(st0[0].shape, np.random.default_rng(99))
+    ref = orc.step_nodes(prob, st0, st1, nodes, src=(S0, Sm1))[:, 0]
+    got = out.reshape(-1)[nodes]
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-5

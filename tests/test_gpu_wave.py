@@ -88,3 +88,40 @@ def test_example3_standing_wave_on_gpu(mm, case):
         assert abs(gpu - oracle) < 1e-9 * oracle
     orders = [np.log2(res[0][0] / res[1][0]), np.log2(res[1][0] / res[2][0]) / 2]
     assert all(o >= 1.8 for o in orders), (res, orders)
+
+
+def test_wave_bf16_one_step(mm):
+    rng = np.random.default_rng(G.RNG_SEED + 111)
+    kw, prob = wave_case("D2Q9", [260, 33], "bf16")
+    L0 = [1.0 + 0.3 * rng.standard_normal(prob.shape)]
+    L1 = [1.0 + 0.3 * rng.standard_normal(prob.shape)]
+    s = mm.Solver(mm.make_desc(**kw, ref=[1.0]))
+    try:
+        s.set_fields(L0)
+        s.set_fields(L1, level=1)
+        st0, st1 = s.fields(0), s.fields(1)
+        s.step(1)
+        out = s.fields(0)[0]
+    finally:
+        s.close()
+    ref = orc.step(prob, st0, st1)[0]
+    tol = G.bf16_ulp(ref - 1.0) + 2e-6 * (1 + np.abs(ref))
+    assert np.all(np.abs(out - ref) <= tol)
+
+
+@pytest.mark.parametrize("n", [[1, 7], [5, 1], [1, 1, 3], [4, 1, 2]])
+def test_wave_degenerate_grids(mm, n):
+    rng = np.random.default_rng(G.RNG_SEED + 112)
+    lat = "D2Q9" if len(n) == 2 else "D3Q19"
+    kw, prob = wave_case(lat, n, "fp64")
+    L0, L1 = [rng.standard_normal(prob.shape)], [rng.standard_normal(prob.shape)]
+    s = mm.Solver(mm.make_desc(**kw))
+    try:
+        s.set_fields(L0)
+        s.set_fields(L1, level=1)
+        s.step(4)
+        out = s.fields(0)
+    finally:
+        s.close()
+    ref, _ = orc.run(prob, L0, L1, nsteps=4)
+    assert G.rel_err(out, ref) < 1e-12
