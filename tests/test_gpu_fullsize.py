@@ -94,3 +94,55 @@ def test_full_size_blocked_matches_unblocked(mm):
     _, _, plain = solve_one(mm, kw, fields, 4, 1)
     err = np.abs(blocked[0] - plain[0]).max() / np.abs(plain[0]).max()
     assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("lat,n", [("D2Q9", [65536, 32800]), ("D3Q7", [1300, 1300, 1300])])
+def test_more_than_2_31_nodes(mm, lat, n):
+    # node counts past 2^31 (every index in the kernels is 64-bit): one LCDE step of a single
+    # Fourier mode phi0 = cos(theta . x), whose exact result is |lambda| cos(theta . x + arg lambda)
+    # with the scheme's amplification factor lambda(theta) (Eq. (TforMMFD-3)), at sampled nodes
+    # spread over the whole index range
+    import torch
+    from oracle import fourier as F
+    dim = len(n)
+    K = np.diag([0.02, 0.015, 0.01][:dim])
+    u = [0.05, 0.03, 0.02][:dim]
+    kw = dict(pde="LCDE", lattice=lat, levels=2, n=n, dt=1.0, dx=[1.0] * dim, K=K, u=u,
+              targets=[0, -1, -1, 0, 0.5], storage="fp32")
+    prob = P.problem_lcde(lat, 2, n, 1.0, [1.0] * dim, K, u, P.two_level_from_a0(0.0))
+    modes = [3, 5, 2][:dim]
+    theta = [2 * np.pi * m / nn for m, nn in zip(modes, n)]     # lattice axes x, y[, z]
+    E, _, _ = orc.lattice(lat, prob.d0, prob.c)
+    ub = F.ubar(prob)
+    lam = sum(a * sum(ub[j] * np.exp(1j * k * sum(theta[ax] * E[j][ax] for ax in range(dim)))
+                      for j in range(E.shape[0]))
+              for k, a in zip((-1, 0, 1), prob.a))
+    nodes = int(np.prod(n))
+    assert nodes > 2 ** 31
+    dev = torch.device("cuda")
+    # phase of node (x, y[, z]) with x fastest, built plane by plane on the device
+    field = torch.empty(nodes, dtype=torch.float32, device=dev)
+    plane = n[0] * n[1]
+    x = torch.arange(n[0], device=dev, dtype=torch.float64)
+    y = torch.arange(n[1], device=dev, dtype=torch.float64)
+    ph_xy = (theta[0] * x[None, :] + theta[1] * y[:, None]).reshape(-1)
+    for z in range(n[2] if dim == 3 else 1):
+        pz = theta[2] * z if dim == 3 else 0.0
+        field[z * plane:(z + 1) * plane] = torch.cos(ph_xy + pz).to(torch.float32)
+    shape = (n[1], n[0]) if dim == 2 else (n[2], n[1], n[0])
+    s = mm.Solver(mm.make_desc(**kw))
+    try:
+        s.set_fields([field.view(shape)])
+        s.step(1)
+        out = s.fields(0, device=True, dtype=np.float32)[0].reshape(-1)
+    finally:
+        s.close()
+    del field
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([rng.integers(0, nodes, 20000), [0, nodes - 1, 2 ** 31 - 1, 2 ** 31, 2 ** 31 + 1]]))
+    got = out[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+    xs = idx % n[0]
+    ys = (idx // n[0]) % n[1]
+    ph = theta[0] * xs + theta[1] * ys + (theta[2] * (idx // plane) if dim == 3 else 0.0)
+    ref = np.abs(lam) * np.cos(ph + np.angle(lam))
+    assert np.abs(got - ref).max() < 2e-6, np.abs(got - ref).max()
