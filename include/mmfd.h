@@ -273,7 +273,7 @@ int mmfd_wave_coefficients(double gamma, double a[3], double ahat[3]);
  * 2D, planes in 3D, streamed per warp or CTA item; 0 = the launcher's occupancy-based choice).
  * mmfd_autotune times candidate pairs on this solver's own grid -- depths 1 .. the deepest the
  * solver allows when it was created with temporal_depth = 0, else the depth in use; heights 0,
- * 16, 32, 64, 128 (2D) or 0, 8, 16, 32, 64 (3D marching kernels) -- and keeps the fastest for
+ * 4, 8, 16, 32, 64, 128 (2D) or 0, 8, 16, 32, 64 (3D marching kernels) -- and keeps the fastest for
  * later mmfd_step calls.  Trial launches read the current level(s) and write only the spare
  * buffer, so the solver's fields and step count are unchanged; the call synchronises the
  * solver's stream.  Any solver can be tuned, before or after its fields are set.

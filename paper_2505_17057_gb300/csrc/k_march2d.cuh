@@ -695,10 +695,11 @@ cudaError_t launch_march2d_t(const LaunchArgs& a) {
     const int strips = (a.g.nx + COLS - 1) / COLS;
     int H = a.H;
     if (H <= 0) {
-        // rows per item: maximise (useful rows / streamed rows) x (fill of the resident warp slots)
+        // rows per item: maximise (useful rows / streamed rows) x (fill of the resident warp slots);
+        // small grids take short items so that every resident warp gets one
         const long long wslots = (long long)resident * NW;
         double best = -1.0;
-        for (int h = 8; h <= 256; ++h) {
+        for (int h = 2; h <= 256; ++h) {
             const long long items = (long long)strips * ((a.g.ny + h - 1) / h);
             const long long rounds = (items + wslots - 1) / wslots;
             const double fill = (double)items / (double)(rounds * wslots);
