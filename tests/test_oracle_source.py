@@ -184,3 +184,51 @@ def test_example1_second_order(case):
     orders = [np.log2(gre[i] / gre[i + 1]) for i in range(2)]
     assert all(o >= 1.8 for o in orders), (gre, orders)
     assert gre[-1] < 2e-2
+
+
+# ----------------------------------------------------------------------------- NCDE, manufactured
+
+def ncde_manufactured_gre(n, T=0.5, A=0.5):
+    """The three-level NCDE of the ncde2d workload (B(phi) = phi^2/2 (1, 1), D(phi) = 0.01 (1 + phi^2),
+    (a) = (7/8, 0, 1/8), (ahat) = (1/8, 0, -1/8)) with the source S that makes
+        phi = 1 + A e^{-t} sin(x + y)
+    exact on the periodic [0, 2 pi)^2; b_{-1} = 3/2, bhat_{-1} = -1/2, M_1F = 0.  With s = x + y,
+    g = A e^{-t} sin s, phi_s = A e^{-t} cos s:
+        S = d_t phi + div B - div (D grad phi) = -g + 2 phi phi_s - 2 (0.02 phi phi_s^2 - 0.01 (1 + phi^2) g).
+    GRE at t = T, with dt = 0.4 dx^2 / (2 D_max) (diffusive scaling)."""
+    dx = 2 * np.pi / n
+    dmax = 0.01 * (1 + (1 + A) ** 2)
+    dt = 0.4 * dx * dx / (2 * dmax)
+    steps = int(round(T / dt))
+    dt = T / steps
+    prob = P.problem_ncde("D2Q9", 3, [n, n], dt, [dx, dx], [[0, 0, 0.5, 0], [0, 0, 0.5, 0]], [0.01, 0, 0.01],
+                          (7 / 8, 0, 1 / 8), (1 / 8, 0, -1 / 8))
+    prob.source, prob.b, prob.bhat = "s", (1.5, 0, 0), (-0.5, 0, 0)
+    x = np.arange(n) * dx
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    sn, cs = np.sin(X + Y), np.cos(X + Y)
+
+    def exact(t):
+        return 1 + A * np.exp(-t) * sn
+
+    def S(m):
+        t = m * dt
+        g = A * np.exp(-t) * sn
+        ph = 1 + g
+        phs = A * np.exp(-t) * cs
+        return [-g + 2 * ph * phs - 2 * (0.02 * ph * phs ** 2 - 0.01 * (1 + ph ** 2) * g)]
+
+    out, _ = orc.run_source(prob, [exact(0.0)], [exact(-dt)], steps, S)
+    ref = exact(steps * dt)
+    return float(np.abs(out[0] - ref).sum() / np.abs(ref).sum())
+
+
+def test_ncde_manufactured_second_order():
+    # pins the NCDE's absolute values (flux, nonlinear diffusion, three-level scheme, sources) to a
+    # closed form: second-order convergence to the manufactured solution.  Diffusive scaling puts the
+    # convective CFL max|phi| dt/dx at 0.9 for n = 64 and 0.23 for n = 256, so the asymptotic range
+    # starts near n = 64 (measured: GRE 1.2e-2, 2.6e-3, 6.5e-4; orders 2.2, 2.0)
+    gre = [ncde_manufactured_gre(n) for n in (64, 128, 256)]
+    orders = [np.log2(gre[i] / gre[i + 1]) for i in range(2)]
+    assert all(o >= 1.9 for o in orders), (gre, orders)
+    assert gre[-1] < 1e-3, gre
