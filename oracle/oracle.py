@@ -314,6 +314,43 @@ def run(prob: Problem, level_n, level_nm1=None, nsteps: int = 1, form: str = "mm
     return _unpack(bn), (_unpack(bm) if prob.levels == 3 else None)
 
 
+def theta_operator_symbol(prob: Problem, form: str = "mmfd") -> np.ndarray:
+    """Eigenvalues ell of the difference operator L of the two-level LCDE scheme on the grid.
+
+    The explicit update Eq. (2-2-2) without sources is phi + L phi: the zeroth-order term is
+    sum_k a_k phi = phi (A_00 = 1) and L collects the central differences of Eq. (2-2-1).  For the
+    LCDE L is linear and shift-invariant on the periodic grid, i.e. circulant: L phi = h * phi
+    (circular convolution) with the impulse response h = L delta_0, so L is diagonalised by the
+    DFT with eigenvalues DFT(h) (numpy axis order)."""
+    if prob.pde != "LCDE" or prob.levels != 2:
+        raise ValueError("the theta-scheme is defined here for the two-level LCDE")
+    delta = np.zeros(prob.shape)
+    delta[(0,) * len(prob.shape)] = 1.0
+    h = step(prob, [delta], form=form)[0] - delta
+    return np.fft.fftn(h)
+
+
+def theta_run(prob: Problem, level_n, nsteps: int, theta: float, form: str = "mmfd") -> List[np.ndarray]:
+    """nsteps steps of the two-level theta-scheme Eq. (GCN) for the LCDE without sources.
+
+    Eq. (GCN) weights the difference terms of level t - dt by theta and those of the new level t
+    by theta_1 = 1 - theta: phi^{n+1} = phi^n + theta L phi^n + theta_1 L phi^{n+1}, i.e. the
+    linear system (I - theta_1 L) phi^{n+1} = (I + theta L) phi^n.  theta = 1 is the explicit
+    scheme Eq. (2-2-2), theta = 0 the implicit one Eq. (2-2-3).  Each step solves the system
+    exactly in the DFT basis of the circulant L (theta_operator_symbol)."""
+    if not 0.0 <= theta <= 1.0:
+        raise ValueError("theta must lie in [0, 1]")
+    ell = theta_operator_symbol(prob, form)
+    den = 1.0 - (1.0 - theta) * ell
+    if np.abs(den).min() == 0.0:
+        raise ValueError("I - (1 - theta) L is singular on this grid")
+    mult = (1.0 + theta * ell) / den
+    phi = np.asarray(level_n[0], dtype=np.float64)
+    for _ in range(int(nsteps)):
+        phi = np.real(np.fft.ifftn(np.fft.fftn(phi) * mult))
+    return [phi]
+
+
 def lbgk_tau1_run(prob: Problem, level_n, nsteps: int) -> List[np.ndarray]:
     """Collide-and-stream LBGK with tau = 1 on explicit populations (independent check)."""
     b = _pack(level_n, prob.nf, prob.shape)
