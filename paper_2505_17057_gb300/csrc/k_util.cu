@@ -39,8 +39,10 @@ __device__ __forceinline__ void ld4_st(const void* base, long long i, double ref
     using S = typename Tr::S;
     const S* p = static_cast<const S*>(base) + i;
     if constexpr (ST == ST_F32) {
+        // FP32 levels hold v - ref: the value is ref + stored, in FP32 as Storage<ST_F32>::load
         const float4 a = *reinterpret_cast<const float4*>(p);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        const float r = (float)ref;
+        v[0] = (double)(r + a.x); v[1] = (double)(r + a.y); v[2] = (double)(r + a.z); v[3] = (double)(r + a.w);
     } else if constexpr (ST == ST_F64) {
         const double2 a = *reinterpret_cast<const double2*>(p);
         const double2 b = *reinterpret_cast<const double2*>(p + 2);

@@ -168,9 +168,12 @@ def test_conservation_gpu(mm):
         s.close()
 
 
-def test_reductions_match_numpy(mm):
+@pytest.mark.parametrize("nx,storage", [(123, "fp32"), (128, "fp32"), (128, "bf16"), (128, "fp64")])
+def test_reductions_match_numpy(mm, nx, storage):
+    # nx = 128 takes the reduction's four-wide vector loads, nx = 123 the scalar ones; FP32 and
+    # BF16 levels hold offsets from the density's reference rho0 = 1, which both must add back
     rng = np.random.default_rng(13)
-    kw, prob = G.case("D2Q9", "NSE", 2, [123, 77], "fp32")
+    kw, prob = G.case("D2Q9", "NSE", 2, [nx, 77], storage)
     d = mm.make_desc(**kw)
     s = mm.Solver(d)
     s.set_fields(G.random_level(prob, rng))
