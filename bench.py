@@ -78,6 +78,11 @@ KERNEL_SOURCES = {
                       "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     "k_march3d_tb": ["k_march3d_tb.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
                      "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+    # one theta-scheme step: the right-hand side (k_march2d) and the Jacobi sweeps (k_march2d_src),
+    # their count and coefficients resolved in params.cpp and issued by solver.cpp
+    "k_march2d_theta": ["k_march2d_src.cu", "k_march2d.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh",
+                        "mmfd_internal.h", "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp",
+                        "solver.cpp"],
 }
 
 
@@ -353,7 +358,8 @@ def run_ours(args):
         desc_kw, fields, fields_m1, source = configs.srccde2d_4096(n=n, storage=args.storage)
     else:
         maker = {"tgv2d": configs.tgv2d_4096, "cde3d": configs.cde3d_512, "nse3d": configs.nse3d_512,
-                 "ncde2d": configs.ncde2d_1024, "lcde2d": configs.lcde2d_8192}[kind]
+                 "ncde2d": configs.ncde2d_1024, "lcde2d": configs.lcde2d_8192,
+                 "theta2d": configs.theta2d_4096}[kind]
         desc_kw, fields, _ = maker(n=n, storage=args.storage)
     dim = 3 if kind.endswith("3d") else 2
     stream = torch.cuda.Stream()
@@ -428,7 +434,11 @@ def run_ours(args):
         achieved = alg_bytes / avg_launch_s / 1e9
         effective = bytes_per_lu * nodes * depth / avg_launch_s / 1e9
         kernel_name = info.kernel.decode()
-        traffic = traffic_from_profile(kernel_name, args.workload)
+        # theta-scheme: one step is the right-hand side plus info.sweeps Jacobi sweeps; its events,
+        # bytes and traffic are those of the whole step (1 + sweeps launches of two HBM streams)
+        theta = info.sweeps > 0
+        launches_per_step = (1 + info.sweeps) if theta else 1
+        traffic = traffic_from_profile("k_march2d_theta" if theta else kernel_name, args.workload)
 
         # end to end through the public API: every step uploads the level from pinned host memory,
         # advances it, and reads back the FP64 field sums (the step's diagnostic result)
@@ -478,18 +488,24 @@ def run_ours(args):
                    "pde": {"NSE": "NSE (He-Luo)"}.get(desc_kw["pde"], desc_kw["pde"]),
                    "levels": desc_kw["levels"], "storage": args.storage, "temporal_depth": depth,
                    **({"source": "su, set from device memory before every step"} if has_src else {}),
+                   **({"theta": desc_kw["theta"], "dt": desc_kw["dt"], "jacobi_sweeps": info.sweeps}
+                      if theta else {}),
                    "autotuned": tuned,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": kernel_name, "peak_kind": peak_kind,
+                     "kernel": (kernel_name + " + k_march2d (one theta step)") if theta else kernel_name,
+                     "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
-                     "effective_gbs": effective},
+                     "effective_gbs": effective,
+                     **({"launches_per_step": launches_per_step,
+                         "note": "per theta step: alg bytes, time and traffic of its 1 + sweeps launches"}
+                        if theta else {})},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
-        "gpu_launches": args.steps * (2 if has_src else 1),
+        "gpu_launches": args.steps * (2 if has_src else launches_per_step),
     }
     if args.serve > 0:
         with torch.cuda.stream(stream):

@@ -58,6 +58,7 @@ enum { MMFD_SRC_NONE = 0, MMFD_SRC_S = 1, MMFD_SRC_SU = 2, MMFD_SRC_SM = 3 };
 #define MMFD_FLAG_DROP_OFFDIAG 0x2u     /* axis lattices: drop K_xy (solve with diag(K)) */
 #define MMFD_FLAG_STOCHASTIC_ROUND 0x4u /* BF16 storage: stochastic instead of nearest rounding */
 #define MMFD_FLAG_TWO_SETS 0x8u         /* multiple-parameter-set scheme, Eq. (2-2-1b): see mmfd_desc */
+#define MMFD_FLAG_THETA 0x10u           /* two-level theta-scheme, Eq. (GCN): see mmfd_desc */
 
 typedef int (*mmfd_alloc_fn)(size_t bytes, void** ptr, void* ctx);
 typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
@@ -125,6 +126,18 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        b = (3/2, 0, 0), bhat = (-1/2, 0, 0) (three-level, as in Sec. III.C and
  *                        Example 1).  The source fields are set with mmfd_set_source.  A solver
  *                        with sources runs unblocked (temporal_depth 1).
+ *  theta                 with MMFD_FLAG_THETA: the two-level theta-scheme of Eq. (GCN), theta in
+ *                        [0, 1] (mmfd_desc_init sets 1/2, Crank-Nicolson).  theta weights the
+ *                        difference terms of the old level and 1 - theta those of the new one:
+ *                        with phi + L phi the explicit update Eq. (2-2-2), every step solves
+ *                            (I - (1 - theta) L) phi^{n+1} = (I + theta L) phi^n.
+ *                        theta = 1 is Eq. (2-2-2), theta = 0 the implicit Eq. (2-2-3).  LCDE,
+ *                        two-level, FP64 or FP32 storage, no source terms.  The system is solved
+ *                        by a Jacobi iteration started from phi^n, with a sweep count fixed at
+ *                        create time so that the iteration error is below the storage type's
+ *                        rounding (mmfd_info_t.sweeps); MMFD_ERR_UNSUPPORTED when the
+ *                        iteration would not contract.  The stability check uses Eq. (Tcond1-1).
+ *                        Runs unblocked; the server does not take such requests.
  */
 typedef struct {
     int pde, lattice, levels;
@@ -153,6 +166,7 @@ typedef struct {
     void* alloc_ctx;
     int source;
     double b[3], bhat[3];
+    double theta;
 } mmfd_desc;
 
 /* Derived constants of a created solver (read-only view, for checking and reporting). */
@@ -166,11 +180,13 @@ typedef struct {
     double Cmat[3][3];           /* LCDE: EDF C per unit phi (Eq. (TforMMFD-0)) */
     double m2[5];                /* NCDE: second-moment target polynomial M2(phi) */
     double max_lambda;           /* max |amplification| found by the create-time check (-1: not checked) */
-    double bytes_per_lu;         /* compulsory HBM bytes per lattice update */
+    double bytes_per_lu;         /* compulsory HBM bytes per lattice update (theta-scheme: per step,
+                                    the right-hand side and every Jacobi sweep) */
     long long device_bytes;      /* device memory held by the level buffers */
     int temporal_depth;          /* depth in use */
     long long steps_done;        /* time levels advanced so far */
     char kernel[32];             /* name of the step kernel family in use */
+    int sweeps;                  /* theta-scheme: Jacobi sweeps per step (0: explicit scheme) */
 } mmfd_info_t;
 
 typedef struct mmfd_solver mmfd_solver;

@@ -18,6 +18,9 @@ Workload recipe (seeded, synthetic; the paper uses analytic test problems, no da
                   phi0 = 1 + 0.5 Sx Sy Sz (16-mode seeded cosine series), 1k steps.
   nse3d_512       512^3 He-Luo NSE on D3Q19, LBGK tau = 1, rho0 = 1, divergence-free seeded
                   velocity with max |u| = 0.05, 1k steps.
+  theta2d_4096    lcde2d_8192's LCDE and initial field on 4096^2, two-level theta-scheme (Eq. (GCN))
+                  with theta = 1/2 (Crank-Nicolson) at dt = 8, a step at which the explicit scheme
+                  (theta = 1) is unstable on this grid; FP32.
   srccde2d_4096   Example 1 (isotropic CDE with the time-dependent source R) scaled to 4096^2 on the
                   periodic [0, 2]^2: D2Q9 three-level Case 3 (a = (7/8, 0, 1/8), ahat = (1/8, 0, -1/8)),
                   b_{-1} = 3/2, bhat_{-1} = -1/2, F_j = w_j R (1 + c_j.u/c_s^2), u = (0.1, 0.1),
@@ -33,7 +36,7 @@ import numpy as np
 from . import inputs
 
 CONFIG_INDEX = {"cde2d_64": 0, "ncde2d_1024": 1, "lcde2d_8192": 1, "tgv2d_4096": 2, "cde3d_512": 3, "nse3d_512": 3,
-                "serve": 4, "srccde2d_4096": 1}
+                "serve": 4, "srccde2d_4096": 1, "theta2d_4096": 1}
 
 NU_LBGK = 1.0 / 6.0          # -(Abar_22 / Abar_10) dt c_s^2 with a_0 = 0, c_s^2 = 1/3
 THREE_LEVEL_A = (7 / 8, 0.0, 1 / 8)
@@ -69,6 +72,16 @@ def lcde2d_8192(n: int = 8192, storage: str = "fp32"):
     desc = dict(pde="LCDE", lattice="D2Q9", levels=2, n=[n, n], dt=1.0, dx=[1.0, 1.0],
                 K=[[0.02, 0.005], [0.005, 0.01]], u=[0.1, 0.05], targets=[0, -1, -1, 0, 0.5],
                 storage=storage, ref=[1.0])
+    return desc, [phi0], 1000
+
+
+def theta2d_4096(n: int = 4096, storage: str = "fp32", theta: float = 0.5, dt: float = 8.0):
+    rng = inputs.rng_for(CONFIG_INDEX["theta2d_4096"])
+    modes = inputs.draw_fourier_modes_2d(rng, 32, 8, 0.1, 0.5)
+    phi0 = 1.0 + inputs.fourier_field_2d(modes, n, n)
+    desc = dict(pde="LCDE", lattice="D2Q9", levels=2, n=[n, n], dt=dt, dx=[1.0, 1.0],
+                K=[[0.02, 0.005], [0.005, 0.01]], u=[0.1, 0.05], targets=[0, -1, -1, 0, 0.5],
+                storage=storage, ref=[1.0], theta=theta)
     return desc, [phi0], 1000
 
 

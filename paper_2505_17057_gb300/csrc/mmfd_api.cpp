@@ -102,6 +102,7 @@ int mmfd_desc_init(mmfd_desc* d) {
     for (int f = 0; f < 4; ++f) d->ref[f] = NAN;
     d->temporal_depth = 1;
     d->seed = 0x4D4D4644ull;
+    d->theta = 0.5;
     return MMFD_OK;
 }
 
@@ -156,6 +157,7 @@ static void fill_info(const Resolved& r, mmfd_info_t* o) {
     o->max_lambda = r.max_lambda;
     o->bytes_per_lu = bytes_per_lu(r);
     o->temporal_depth = 1;
+    o->sweeps = r.theta_on ? r.sweeps : 0;
 }
 
 int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out) {

@@ -8,6 +8,7 @@
 // the second-order moment equation Eq. (ME-NCDE-3-2-1); stability symbol Eq. (TforMMFD-3).
 #include "params.h"
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -450,6 +451,59 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
         for (size_t i = 0; i < sizeof(SrcCoef<double>) / sizeof(double); ++i) sdst[i] = (float)ssrc[i];
     }
 
+    // ---- two-level theta-scheme (Eq. (GCN)).  With phi + L phi the explicit update above (E = I + L,
+    // the collapsed stencil of level t), a step solves (I - theta_1 L) x = (I + theta L) phi^n,
+    // theta_1 = 1 - theta.  The right-hand side is the stencil (1 - theta) I + theta E; the
+    // system is solved by Jacobi sweeps on its diagonal d = 1 + theta_1 (1 - W0):
+    //     x <- rhs / d + (theta_1 / d) (E - W0 I) x,
+    // i.e. an LCDE stencil without a centre weight plus a centre-only source term rhs / d.  The
+    // sweep contracts by at most rho = theta_1 sum_p (|Wp| + |Wm|) / d per step.
+    r.theta_on = (d.flags & MMFD_FLAG_THETA) != 0 ? 1 : 0;
+    r.theta = 1.0;
+    r.sweeps = 0;
+    double th_dg = 1.0, th_w0 = 0.0;
+    if (r.theta_on) {
+        if (!(d.theta >= 0.0 && d.theta <= 1.0)) return fail(msg, MMFD_ERR_ARG, "theta must lie in [0, 1]");
+        if (d_in.pde != PDE_LCDE) return fail(msg, MMFD_ERR_UNSUPPORTED, "the theta-scheme is built for the LCDE");
+        if (d.levels != 2) return fail(msg, MMFD_ERR_UNSUPPORTED, "the theta-scheme is a two-level scheme");
+        if (d.source != MMFD_SRC_NONE) return fail(msg, MMFD_ERR_UNSUPPORTED, "theta-scheme: no source terms");
+        if (d.storage == ST_BF16)
+            return fail(msg, MMFD_ERR_UNSUPPORTED, "theta-scheme: FP64 or FP32 storage (the iteration stalls at BF16 rounding)");
+        r.theta = d.theta;
+        const double th = d.theta, th1 = 1.0 - d.theta;
+        double woff = 0.0;
+        for (int p = 0; p < NP; ++p) woff += std::fabs(c.Wp[0][p]) + std::fabs(c.Wm[0][p]);
+        const double dg = 1.0 + th1 * (1.0 - c.W0[0]);
+        if (!(dg > 0.0) || !(th1 * woff / dg < 1.0))
+            return fail(msg, MMFD_ERR_UNSUPPORTED, "theta-scheme: the Jacobi iteration does not contract");
+        th_dg = dg;
+        th_w0 = c.W0[0];
+        Coef<double>& R = r.thr_d;
+        Coef<double>& J = r.thj_d;
+        R = c;
+        J = c;
+        R.W0[0] = th1 + th * c.W0[0];
+        J.W0[0] = 0.0;
+        R.W0[1] = J.W0[1] = 0.0;
+        for (int p = 0; p < kMaxPair; ++p) {
+            R.Wp[0][p] = th * c.Wp[0][p];
+            R.Wm[0][p] = th * c.Wm[0][p];
+            J.Wp[0][p] = th1 * c.Wp[0][p] / dg;
+            J.Wm[0][p] = th1 * c.Wm[0][p] / dg;
+            R.Wp[1][p] = R.Wm[1][p] = J.Wp[1][p] = J.Wm[1][p] = 0.0;
+        }
+        std::memset(&r.ths_d, 0, sizeof(r.ths_d));
+        r.ths_d.W0[0] = 1.0 / dg;
+        const double* srcs[3] = {reinterpret_cast<const double*>(&r.thr_d), reinterpret_cast<const double*>(&r.thj_d),
+                                 reinterpret_cast<const double*>(&r.ths_d)};
+        float* dsts[3] = {reinterpret_cast<float*>(&r.thr_f), reinterpret_cast<float*>(&r.thj_f),
+                          reinterpret_cast<float*>(&r.ths_f)};
+        const size_t counts[3] = {sizeof(Coef<double>) / sizeof(double), sizeof(Coef<double>) / sizeof(double),
+                                  sizeof(SrcCoef<double>) / sizeof(double)};
+        for (int b = 0; b < 3; ++b)
+            for (size_t i = 0; i < counts[b]; ++i) dsts[b][i] = (float)srcs[b][i];
+    }
+
     // ---- create-time stability check (LCDE: exact symbol on the grid's wave numbers)
     r.max_lambda = -1.0;
     if (d.pde == PDE_LCDE) {
@@ -467,6 +521,13 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
             }
         }
         double lmax = 0.0;
+        // theta-scheme: per Fourier mode the sweeps start from phi^n, whose error is
+        // ell / (1 - theta_1 ell) phi_hat^n, and multiply it by g = theta_1 (A - W0) / d each; the
+        // sweep count takes every mode's error below the storage type's rounding
+        const double th_eps = d.storage == ST_F64 ? 1e-15 : 6e-8;
+        int th_k = 1;
+        bool sampled = false;
+        for (int a = 0; a < dim; ++a) sampled = sampled || d.n[a] > 96;
         for (double tz : th[2])
             for (double ty : th[1])
                 for (double tx : th[0]) {
@@ -481,7 +542,18 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
                         A[l] = s;
                     }
                     double m;
-                    if (d.levels == 2) {
+                    if (r.theta_on) {
+                        // Eq. (Tcond1-1): lambda = (1 + theta ell) / (1 - theta_1 ell), ell = A - 1
+                        const std::complex<double> ell = A[0] - 1.0;
+                        const std::complex<double> den = 1.0 - (1.0 - r.theta) * ell;
+                        m = std::abs(den) > 0.0 ? std::abs((1.0 + r.theta * ell) / den) : HUGE_VAL;
+                        const double e0 = std::abs(den) > 0.0 ? std::abs(ell) / std::abs(den) : HUGE_VAL;
+                        const double gm = (1.0 - r.theta) * std::abs(A[0] - th_w0) / th_dg;
+                        if (e0 > th_eps && gm > 0.0) {
+                            const double kk = std::ceil(std::log(th_eps / e0) / std::log(gm));
+                            th_k = (int)std::min(1e6, std::max((double)th_k, kk));
+                        }
+                    } else if (d.levels == 2) {
                         m = std::abs(A[0]);
                     } else {
                         // roots of lambda^2 - p1 lambda - p0 (Eq. (3-level)); a vanishing
@@ -500,11 +572,21 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
         r.max_lambda = lmax;
         if (lmax > 1.0 + 1e-12 && !(d.flags & MMFD_FLAG_ALLOW_UNSTABLE))
             return fail(msg, MMFD_ERR_UNSTABLE, "max |lambda| > 1 on the grid's wave numbers");
+        if (r.theta_on) {
+            // theta = 1: one sweep (x = rhs).  On sampled wave numbers one sweep more as margin.
+            int k = r.theta == 1.0 ? 1 : th_k + (sampled ? 1 : 0);
+            if (k > 20000)
+                return fail(msg, MMFD_ERR_UNSUPPORTED, "theta-scheme: the Jacobi iteration would need more than 20000 sweeps");
+            r.sweeps = k;
+        }
     }
     return MMFD_OK;
 }
 
 double bytes_per_lu(const Resolved& r) {
+    // theta-scheme: the right-hand side reads the level and writes rhs; each Jacobi sweep reads
+    // the iterate and rhs and writes the next iterate
+    if (r.theta_on) return (double)storage_bytes(r.st) * (2.0 + 3.0 * r.sweeps);
     // levels read and the one written; source levels (compute type) read once per step
     const double src = r.src ? (double)(r.st == ST_F64 ? 8 : 4) * r.nsrc * (r.levels - 1) : 0.0;
     return (double)storage_bytes(r.st) * r.nf * (r.levels - 1 + 1) + src;

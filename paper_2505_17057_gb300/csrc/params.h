@@ -27,6 +27,16 @@ struct Resolved {
     double b[3], bhat[3];
     SrcCoef<double> sd;
     SrcCoef<float> sf;
+    // two-level theta-scheme (Eq. (GCN)): right-hand side (I + theta L) phi^n as an LCDE stencil
+    // (thr), Jacobi sweep x <- x_rhs / d + ((1 - theta) / d) (E - W0 I) x as an LCDE stencil (thj)
+    // plus a centre-only source block (ths) with weight 1 / d, d = 1 + (1 - theta)(1 - W0)
+    int theta_on;
+    double theta;
+    int sweeps;
+    Coef<double> thr_d, thj_d;
+    Coef<float> thr_f, thj_f;
+    SrcCoef<double> ths_d;
+    SrcCoef<float> ths_f;
 };
 
 // Returns MMFD_OK or an error code; *msg gets a human-readable reason on error.

@@ -579,11 +579,13 @@ int mmfd_submit(mmfd_server* h, const mmfd_desc* d, const void* const* init, int
         s->st.rejected++;
         return set_error(rc, msg);
     }
-    if (q->r->src) {
+    if (q->r->src || q->r->theta_on) {
+        const bool src = q->r->src != 0;
         delete q->r;
         delete q;
         s->st.rejected++;
-        return set_error(MMFD_ERR_UNSUPPORTED, "the server does not take requests with source terms");
+        return set_error(MMFD_ERR_UNSUPPORTED, src ? "the server does not take requests with source terms"
+                                                   : "the server does not take theta-scheme requests");
     }
     q->desc = *d;
     q->g = make_geom(*q->r);

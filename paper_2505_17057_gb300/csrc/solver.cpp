@@ -60,6 +60,13 @@ int solver_init_device(Solver* s) {
         s->src_i0 = s->src_i1 = 0;
         s->src_fresh = true;
     }
+    if (s->r.theta_on) {
+        // same element size and ghosted layout as a level (FP64 / FP32 storage only)
+        rc = dev_alloc(s, s->level_bytes, &s->rhs);
+        if (rc != MMFD_OK) return rc;
+        cudaError_t e = cudaMemsetAsync(s->rhs, 0, s->level_bytes, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
     rc = dev_alloc(s, 256, reinterpret_cast<void**>(&s->d_flag));
     if (rc != MMFD_OK) return rc;
     cudaError_t e = cudaMemsetAsync(s->d_flag, 0, 256, s->stream);
@@ -81,6 +88,8 @@ void solver_free_device(Solver* s) {
         dev_free(s, s->srcbuf[i]);
         s->srcbuf[i] = nullptr;
     }
+    dev_free(s, s->rhs);
+    s->rhs = nullptr;
     dev_free(s, s->d_red);
     s->d_red = nullptr;
     dev_free(s, s->d_flag);
@@ -200,6 +209,13 @@ void solver_launch_args(Solver* s, LaunchArgs& a) {
     a.src[0] = s->r.src ? s->srcbuf[s->src_i0] : nullptr;
     a.src[1] = s->r.src ? s->srcbuf[s->src_i1] : nullptr;
     a.src_coef = s->r.st == ST_F64 ? static_cast<const void*>(&s->r.sd) : static_cast<const void*>(&s->r.sf);
+    if (s->r.theta_on) {
+        // theta-scheme: the step kernel fn is the Jacobi sweep (rhs enters as a centre-only source)
+        const bool f64 = s->r.st == ST_F64;
+        a.coef = f64 ? static_cast<const void*>(&s->r.thj_d) : static_cast<const void*>(&s->r.thj_f);
+        a.src[0] = a.src[1] = s->rhs;
+        a.src_coef = f64 ? static_cast<const void*>(&s->r.ths_d) : static_cast<const void*>(&s->r.ths_f);
+    }
     if (s->use_tma) {
         const int nf = s->g.nf;
         for (int f = 0; f < nf; ++f) {
@@ -212,6 +228,28 @@ void solver_launch_args(Solver* s, LaunchArgs& a) {
 
 int solver_step(Solver* s, long long nsteps) {
     if (!s->fields_set) return set_error(MMFD_ERR_STATE, "set the fields before stepping");
+    if (s->r.theta_on) {
+        // Eq. (GCN): rhs = ((1 - theta) I + theta E) phi^n, then r.sweeps Jacobi sweeps from
+        // x = phi^n, each into the spare level buffer
+        const bool f64 = s->r.st == ST_F64;
+        for (long long n = 0; n < nsteps; ++n) {
+            LaunchArgs a;
+            solver_launch_args(s, a);
+            a.out = s->rhs;
+            a.coef = f64 ? static_cast<const void*>(&s->r.thr_d) : static_cast<const void*>(&s->r.thr_f);
+            a.src[0] = a.src[1] = nullptr;
+            cudaError_t e = s->fn_rhs(a);
+            if (e != cudaSuccess) return cuda_fail(e, "theta-scheme right-hand side kernel");
+            for (int k = 0; k < s->r.sweeps; ++k) {
+                solver_launch_args(s, a);
+                e = s->fn(a);
+                if (e != cudaSuccess) return cuda_fail(e, "theta-scheme sweep kernel");
+                s->cur = s->next();
+            }
+            s->steps_done += 1;
+        }
+        return MMFD_OK;
+    }
     long long done = 0;
     while (done < nsteps) {
         const long long left = nsteps - done;
@@ -341,7 +379,8 @@ void solver_use_depth(Solver* s, int depth) {
     } else {
         s->fn_block = nullptr;
         s->depth = 1;
-        if (s->r.src) s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d_src" : "k_march3d_src") : "k_direct_src";
+        if (s->r.src || s->r.theta_on)
+            s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d_src" : "k_march3d_src") : "k_direct_src";
         else s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
     }
 }
@@ -356,11 +395,17 @@ int solver_pick_kernels(Solver* s) {
     const char* force = std::getenv("MMFD_FORCE_KERNEL");
     const bool want_direct = force && std::strcmp(force, "direct") == 0;
     // source terms: kernel variant 1 (S only, M_1F = 0 or S u folded) or 2 (S and M_1F fields);
-    // such solvers run unblocked
-    const int srcv = s->r.src == 0 ? 0 : (s->r.src == MMFD_SRC_SM ? 2 : 1);
+    // such solvers run unblocked.  The theta-scheme's Jacobi sweep is variant 1 (its right-hand
+    // side enters as a centre-only source) and its right-hand side a plain step.
+    const int srcv = s->r.theta_on ? 1 : s->r.src == 0 ? 0 : (s->r.src == MMFD_SRC_SM ? 2 : 1);
+    s->fn_rhs = nullptr;
     if (s->r.dim == 2 && s->g.nx >= 128 && !want_direct) {
         s->fn = srcv ? find_march2d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
                      : find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        if (s->r.theta_on) {
+            s->fn_rhs = find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+            if (!s->fn_rhs) s->fn = nullptr;
+        }
         if (s->fn) {
             const int es = s->g.es;
             const int boxw = 128 + 2 * (16 / es);
@@ -397,6 +442,10 @@ int solver_pick_kernels(Solver* s) {
     if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct) {
         s->fn = srcv ? find_march3d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
                      : find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        if (s->r.theta_on) {
+            s->fn_rhs = find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+            if (!s->fn_rhs) s->fn = nullptr;
+        }
         if (s->fn) {
             const int es = s->g.es;
             const int boxw = 128 + 2 * (16 / es);
@@ -434,7 +483,9 @@ int solver_pick_kernels(Solver* s) {
     s->fn = srcv ? find_direct_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
                  : find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
     s->kernel_name = srcv ? "k_direct_src" : "k_direct";
-    if (!s->fn) return set_error(MMFD_ERR_UNSUPPORTED, "no kernel for this lattice/PDE/levels/storage");
+    if (s->r.theta_on) s->fn_rhs = find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+    if (!s->fn || (s->r.theta_on && !s->fn_rhs))
+        return set_error(MMFD_ERR_UNSUPPORTED, "no kernel for this lattice/PDE/levels/storage");
     return MMFD_OK;
 }
 

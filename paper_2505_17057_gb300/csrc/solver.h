@@ -44,6 +44,8 @@ struct Solver {
     size_t src_bytes = 0;
     int src_i0 = 0, src_i1 = 0;                  // buffers holding the sources at t_n and t_{n-1}
     bool src_fresh = true;                       // no step since creation or set_fields(level 0)
+    void* rhs = nullptr;                         // theta-scheme: right-hand side (I + theta L) phi^n
+    LaunchFn fn_rhs = nullptr;                   // theta-scheme: kernel writing rhs (plain LCDE step)
 
     int prev() const { return nlev == 2 ? 1 - cur : (cur + 2) % 3; }
     int next() const { return nlev == 2 ? 1 - cur : (cur + 1) % 3; }

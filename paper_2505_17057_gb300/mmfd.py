@@ -41,6 +41,7 @@ MMFD_FLAG_ALLOW_UNSTABLE = 0x1
 MMFD_FLAG_DROP_OFFDIAG = 0x2
 MMFD_FLAG_STOCHASTIC_ROUND = 0x4
 MMFD_FLAG_TWO_SETS = 0x8
+MMFD_FLAG_THETA = 0x10
 MMFD_RED_SUM, MMFD_RED_MAXABS, MMFD_RED_NONFINITE = 0, 1, 2
 MMFD_SRC_NONE, MMFD_SRC_S, MMFD_SRC_SU, MMFD_SRC_SM = 0, 1, 2, 3
 
@@ -68,6 +69,7 @@ class mmfd_desc(C.Structure):
         ("seed", C.c_ulonglong), ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p),
         ("source", C.c_int), ("b", C.c_double * 3), ("bhat", C.c_double * 3),
+        ("theta", C.c_double),
     ]
 
 
@@ -79,7 +81,7 @@ class mmfd_info_t(C.Structure):
         ("c", C.c_double * 3), ("d0", C.c_double * 3), ("cs2", C.c_double * 3), ("w", C.c_double * 19),
         ("Cmat", (C.c_double * 3) * 3), ("m2", C.c_double * 5), ("max_lambda", C.c_double),
         ("bytes_per_lu", C.c_double), ("device_bytes", C.c_longlong), ("temporal_depth", C.c_int),
-        ("steps_done", C.c_longlong), ("kernel", C.c_char * 32),
+        ("steps_done", C.c_longlong), ("kernel", C.c_char * 32), ("sweeps", C.c_int),
     ]
 
 
@@ -294,13 +296,15 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
               rho0: float = 1.0, a=None, ahat=None, abar=None, abarhat=None, targets=None, targets_bar=None,
               d0=None, flags: int = 0, ref=None, temporal_depth: int = 1, seed: Optional[int] = None,
               stream: Optional[int] = None, sets: Optional[dict] = None, source: str = "none",
-              b=None, bhat=None) -> mmfd_desc:
+              b=None, bhat=None, theta: Optional[float] = None) -> mmfd_desc:
     """Fill an mmfd_desc (plain field assignment; every derived constant is computed by the library).
 
     sets: the multiple-parameter-set scheme (MMFD_FLAG_TWO_SETS): a dict with "d2", "d1" and,
     for the NSE momentum, "bar_d2", "bar_d1", each a pair of triples (level t, level t - dt).
     source: "none", "s" (M_1F = 0), "su" (M_1F = S u) or "sm" (M_1F given); b, bhat: the source
     coefficient triples (None: the library's defaults).
+    theta: the two-level theta-scheme of Eq. (GCN) with this theta (MMFD_FLAG_THETA); None: the
+    explicit scheme.
     """
     d = mmfd_desc_init()
     d.pde = PDE[pde]
@@ -367,6 +371,9 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
     for i in range(3):
         d.b[i] = float(b[i]) if b is not None else 0.0
         d.bhat[i] = float(bhat[i]) if bhat is not None else 0.0
+    if theta is not None:
+        d.flags |= MMFD_FLAG_THETA
+        d.theta = float(theta)
     if seed is not None:
         d.seed = int(seed)
     if stream is not None:

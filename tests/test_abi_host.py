@@ -266,3 +266,68 @@ def test_storage_reference_rules(mm):
         mm.mmfd_describe(mm.make_desc(pde="LCDE", lattice="D2Q9", levels=2, n=[16, 16], dt=1.0, dx=[1, 1],
                                       K=np.eye(2) * 0.01, storage="fp32", ref=[float("inf")]))
     assert e.value.code == mm.MMFD_ERR_ARG
+
+
+def _theta_sweeps_from_oracle(prob, theta, eps):
+    """Jacobi sweeps that take every mode's initial error ell / (1 - theta_1 ell) below eps when
+    each sweep multiplies it by g = theta_1 (E - W0) / d, d = 1 + theta_1 (1 - W0); E and W0 from
+    the oracle's explicit step (impulse response)."""
+    delta = np.zeros(prob.shape)
+    delta[(0,) * len(prob.shape)] = 1.0
+    h = orc.step(prob, [delta])[0]
+    W0 = h[(0,) * len(prob.shape)]
+    E = np.fft.fftn(h)
+    th1 = 1.0 - theta
+    ell = E - 1.0
+    g = np.abs(th1 * (E - W0) / (1.0 + th1 * (1.0 - W0)))
+    b = np.abs(ell) / np.abs(1.0 - th1 * ell)
+    m = (b > eps) & (g > 0)
+    return max(1, int(np.ceil((np.log(eps / b[m]) / np.log(g[m])).max()))) if m.any() else 1
+
+
+def test_theta_descriptor(mm):
+    # the two-level theta-scheme (Eq. (GCN)): validation, the create-time check against
+    # Eq. (Tcond1-1), and the Jacobi sweep count against the oracle's own symbol
+    K = [[0.03, 0.004], [0.004, 0.02]]
+    u = [0.15, -0.1]
+    for lat in ("D2Q5", "D2Q9"):
+        KK = np.diag(np.diag(K)) if lat == "D2Q5" else K
+        for dt in (1.0, 3.0):
+            prob = P.problem_lcde(lat, 2, [24, 20], dt, [1, 1], KK, u, P.two_level_from_a0(0.0))
+            for theta in (0.0, 0.4, 0.5, 0.8):
+                for st, es, eps in (("fp64", 8, 1e-15), ("fp32", 4, 6e-8)):
+                    info = _describe(mm, pde="LCDE", lattice=lat, levels=2, n=[24, 20], dt=dt, dx=[1, 1], K=KK, u=u,
+                                     a=P.two_level_from_a0(0.0), storage=st, theta=theta,
+                                     flags=mm.MMFD_FLAG_ALLOW_UNSTABLE)
+                    lam = np.abs(F.theta_lambda(prob, theta, prob.shape)).max()
+                    assert abs(info.max_lambda - lam) < 1e-12, (lat, dt, theta)
+                    k = _theta_sweeps_from_oracle(prob, theta, eps)
+                    assert k <= info.sweeps <= k + 1, (lat, dt, theta, st, k, info.sweeps)
+                    assert info.bytes_per_lu == es * (2 + 3 * info.sweeps)
+    # theta = 1 is the explicit scheme: one sweep (x = rhs); no flag: no sweeps
+    base = dict(pde="LCDE", lattice="D2Q9", levels=2, n=[32, 32], dt=1.0, dx=[1, 1], K=K, u=u)
+    assert _describe(mm, **base, theta=1.0).sweeps == 1
+    assert _describe(mm, **base).sweeps == 0
+    # Theorem 2: heavily diffusive D2Q5 (a_0 = -2): theta <= 1/2 passes the check, the explicit end fails
+    heavy = dict(pde="LCDE", lattice="D2Q5", levels=2, n=[16, 16], dt=1.0, dx=[1, 1], K=[[0.3, 0], [0, 0.25]],
+                 u=[0.2, 0.1], a=P.two_level_from_a0(-2.0), storage="fp64")
+    for theta in (0.0, 0.25, 0.5):
+        assert _describe(mm, **heavy, theta=theta).max_lambda <= 1 + 1e-12
+    with pytest.raises(mm.MMFDError) as e:
+        _describe(mm, **heavy, theta=1.0)
+    assert e.value.code == mm.MMFD_ERR_UNSTABLE
+    # what the theta-scheme is not built for
+    for bad, code in [(dict(theta=1.5), mm.MMFD_ERR_ARG), (dict(theta=-0.1), mm.MMFD_ERR_ARG),
+                      (dict(theta=float("nan")), mm.MMFD_ERR_ARG),
+                      (dict(theta=0.5, storage="bf16"), mm.MMFD_ERR_UNSUPPORTED),
+                      (dict(theta=0.5, source="s"), mm.MMFD_ERR_UNSUPPORTED),
+                      (dict(theta=0.5, levels=3, targets=[0, -1, -1, 0.25, 0.5]), mm.MMFD_ERR_UNSUPPORTED)]:
+        kw = dict(base)
+        kw.update(bad)
+        with pytest.raises(mm.MMFDError) as e:
+            _describe(mm, **kw)
+        assert e.value.code == code, bad
+    with pytest.raises(mm.MMFDError) as e:
+        _describe(mm, pde="NCDE", lattice="D2Q9", levels=2, n=[16, 16], dt=1.0, dx=[1, 1],
+                  flux=[[0, 0.1, 0, 0], [0, 0.1, 0, 0]], diff=[0.1, 0, 0, 0], theta=0.5)
+    assert e.value.code == mm.MMFD_ERR_UNSUPPORTED
