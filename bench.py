@@ -78,9 +78,10 @@ KERNEL_SOURCES = {
                       "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     "k_march3d_tb": ["k_march3d_tb.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
                      "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
-    # one theta-scheme step: the right-hand side (k_march2d) and the Jacobi sweeps (k_march2d_src),
+    # one theta-scheme step: the right-hand side (k_march2d) and the Jacobi sweeps (k_march2d_tb
+    # fusing several per launch, k_march2d_src for single ones),
     # their count and coefficients resolved in params.cpp and issued by solver.cpp
-    "k_march2d_theta": ["k_march2d_src.cu", "k_march2d.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh",
+    "k_march2d_theta": ["k_march2d_src.cu", "k_march2d.cu", "k_march2d_tb.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh",
                         "mmfd_internal.h", "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp",
                         "solver.cpp"],
 }
@@ -381,7 +382,9 @@ def run_ours(args):
             tuned = {"temporal_depth": t.temporal_depth, "rows_per_item": t.rows_per_item,
                      "candidates": t.candidates, "ms_per_step": t.ms_per_step}
         info = s.get_info()
-        depth = max(1, info.temporal_depth)
+        # steps per timed launch group: a theta-scheme solver's depth counts fused Jacobi sweeps,
+        # one step each
+        depth = 1 if info.sweeps > 0 else max(1, info.temporal_depth)
         nodes = n ** dim
         bytes_per_lu = info.bytes_per_lu
 
@@ -431,13 +434,21 @@ def run_ours(args):
         avg_launch_s = statistics.mean(launch_ms) / 1e3
         # a launch reads and writes the stored level once, whatever its temporal depth
         alg_bytes = bytes_per_lu * nodes
-        achieved = alg_bytes / avg_launch_s / 1e9
         effective = bytes_per_lu * nodes * depth / avg_launch_s / 1e9
         kernel_name = info.kernel.decode()
-        # theta-scheme: one step is the right-hand side plus info.sweeps Jacobi sweeps; its events,
-        # bytes and traffic are those of the whole step (1 + sweeps launches of two HBM streams)
+        # theta-scheme: one step is the right-hand side plus info.sweeps Jacobi sweeps, fused jd
+        # per launch; its events, bytes and traffic are those of the whole step.  Compulsory bytes:
+        # the right-hand side reads the level and writes rhs, each sweep launch reads the iterate
+        # and rhs and writes the next iterate; the effective figure counts every sweep as unfused.
         theta = info.sweeps > 0
-        launches_per_step = (1 + info.sweeps) if theta else 1
+        jd = max(1, info.temporal_depth)
+        sweep_launches = info.sweeps // jd + (1 if info.sweeps % jd else 0)
+        launches_per_step = (1 + sweep_launches) if theta else 1
+        if theta:
+            es = {"fp32": 4, "fp64": 8}[args.storage]
+            alg_bytes = es * (2 + 3 * sweep_launches) * nodes
+            effective = bytes_per_lu * nodes / avg_launch_s / 1e9
+        achieved = alg_bytes / avg_launch_s / 1e9
         traffic = traffic_from_profile("k_march2d_theta" if theta else kernel_name, args.workload)
 
         # end to end through the public API: every step uploads the level from pinned host memory,
@@ -486,10 +497,11 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "grid": [n] * dim, "lattice": desc_kw["lattice"],
                    "pde": {"NSE": "NSE (He-Luo)"}.get(desc_kw["pde"], desc_kw["pde"]),
-                   "levels": desc_kw["levels"], "storage": args.storage, "temporal_depth": depth,
+                   "levels": desc_kw["levels"], "storage": args.storage,
+                   "temporal_depth": jd if theta else depth,
                    **({"source": "su, set from device memory before every step"} if has_src else {}),
-                   **({"theta": desc_kw["theta"], "dt": desc_kw["dt"], "jacobi_sweeps": info.sweeps}
-                      if theta else {}),
+                   **({"theta": desc_kw["theta"], "dt": desc_kw["dt"], "jacobi_sweeps": info.sweeps,
+                       "sweeps_per_launch": jd} if theta else {}),
                    "autotuned": tuned,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},

@@ -113,7 +113,9 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        the depth in use.  mmfd_step(n) runs n / T blocked launches and the
  *                        remaining n % T steps unblocked.  With BF16 storage a blocked solver
  *                        rounds the state to BF16 once per T steps (the intermediate levels
- *                        stay in FP32).
+ *                        stay in FP32).  For a theta-scheme solver (MMFD_FLAG_THETA) the depth
+ *                        counts Jacobi sweeps fused per launch instead (2D grids with nx >= 128,
+ *                        up to 2 for FP64 and 4 for FP32); every mmfd_step is one time step.
  *  seed                  BF16 stochastic-rounding seed.
  *  stream                cudaStream_t (NULL = legacy default stream).
  *  alloc/free_fn/ctx     device allocator for the level buffers (NULL = cudaMalloc/cudaFree).
@@ -137,7 +139,8 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        create time so that the iteration error is below the storage type's
  *                        rounding (mmfd_info_t.sweeps); MMFD_ERR_UNSUPPORTED when the
  *                        iteration would not contract.  The stability check uses Eq. (Tcond1-1).
- *                        Runs unblocked; the server does not take such requests.
+ *                        temporal_depth fuses sweeps (see there); the server does not take such
+ *                        requests.
  */
 typedef struct {
     int pde, lattice, levels;

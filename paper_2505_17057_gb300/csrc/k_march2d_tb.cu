@@ -14,6 +14,14 @@
 // x-edges are read from the ghost columns, which every writer of a blocked solver keeps up to
 // date to depth TT (Geom::gx).  Intermediate levels stay in the compute type (they are never
 // stored), so for BF16 storage the state is rounded once per TT steps.
+//
+// JAC: TT Jacobi sweeps of the two-level theta-scheme (Eq. (GCN)) instead of TT steps.  A sweep
+// is the LCDE stencil of the coefficient block (no centre weight) plus jw times the right-hand
+// side rhs, which does not change between sweeps: when level t completes row r - 1 - t (r the
+// input row), rhs of that row is added before the row moves on to level t + 1.  The TT rhs rows
+// in use sit in a register window that takes one new row per input row, fetched a row early.  rhs has the
+// level's ghosted layout with its x ghosts current, so the columns the wavefront needs are valid;
+// lanes whose columns leave the padded row (they feed no stored node) take zero.
 #include "k_march2d.cuh"
 
 namespace mmfd {
@@ -86,10 +94,12 @@ __device__ __forceinline__ void tb_push_row(const Coef<T>& cf, const T (&raw)[LN
     });
 }
 
-template <int LAT, int PDE, int ST, int TT, int NW, int NSTAGE>
+template <int LAT, int PDE, int ST, int TT, int NW, int NSTAGE, bool JAC>
 __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ TmapSet maps, Geom g,
                                                         void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
-                                                        StepExtra ex, int H, int nitems, int* __restrict__ err) {
+                                                        StepExtra ex, int H, int nitems, int* __restrict__ err,
+                                                        const typename Storage<ST>::S* __restrict__ rhs,
+                                                        typename Storage<ST>::T jw) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
@@ -105,6 +115,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
     constexpr size_t kRingBytes = (size_t)NSTAGE * SLOT;
     static_assert(TT >= 2 && TT <= 5, "the 8-column strip overlap supports 2 .. 5 levels");
     static_assert(TT <= ALIGN, "ghost columns of 16 bytes hold at most 16 / sizeof(S) levels");
+    static_assert(!JAC || (PDE == PDE_LCDE && ST != ST_BF16), "Jacobi sweeps: LCDE, FP32 / FP64 levels");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -168,6 +179,38 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
     bool failed = false;
     const bool store_lane = lane >= 1 && lane <= 30;
 
+    // the lane's LN right-hand-side values of row y (periodic in y).  Columns off the padded row
+    // [-ox, py - ox) take zero; a vector that straddles its ends (the ghost columns are narrower
+    // than a lane's four nodes in FP64) is read node by node.
+    [[maybe_unused]] auto rhs_row = [&](int y, int xb, T (&rv)[LN]) {
+        if constexpr (JAC) {
+        int yw = y % g.ny;
+        if (yw < 0) yw += g.ny;
+        const S* row = rhs + g.at(0, yw, 0);
+        if (xb >= -g.ox && xb + LN <= g.py - g.ox) {
+            if constexpr (sizeof(S) == 4) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(row + xb));
+                rv[0] = q.x; rv[1] = q.y; rv[2] = q.z; rv[3] = q.w;
+            } else {
+                const double2 q0 = __ldg(reinterpret_cast<const double2*>(row + xb));
+                const double2 q1 = __ldg(reinterpret_cast<const double2*>(row + xb + 2));
+                rv[0] = q0.x; rv[1] = q0.y; rv[2] = q1.x; rv[3] = q1.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < LN; ++k) {
+                const int x = xb + k;
+                rv[k] = (x >= -g.ox && x < g.py - g.ox) ? __ldg(row + x) : T(0);
+            }
+        }
+        }
+    };
+
+    // Jacobi right-hand side: rwin[t] holds row r - 1 - t for the current input row r (the row
+    // level t completes), rnext row r, loaded one input row before it is needed
+    [[maybe_unused]] T rwin[TT][LN];
+    [[maybe_unused]] T rnext[LN];
+
     // input row i of the item at (xb, y0): push it through the TT levels and store the completed
     // level-TT row y0 - 2 TT + i if it is one of the item's output rows
     EdgeStore<2, ST> es;
@@ -186,6 +229,20 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
                 accC[t][k] = accN[t][k];
                 accN[t][k] = T(0);
             }
+            if constexpr (JAC) {
+#pragma unroll
+                for (int k = 0; k < LN; ++k) raw[1 + k] += jw * rwin[t][k];
+            }
+        }
+        if constexpr (JAC) {
+            // advance the window to input row i + 1 and fetch the row input row i + 2 starts with
+#pragma unroll
+            for (int t = TT - 1; t > 0; --t)
+#pragma unroll
+                for (int k = 0; k < LN; ++k) rwin[t][k] = rwin[t - 1][k];
+#pragma unroll
+            for (int k = 0; k < LN; ++k) rwin[0][k] = rnext[k];
+            rhs_row(y0 - TT + i + 1, xb, rnext);
         }
         const int yo = y0 - 2 * TT + i;
         if (i >= 2 * TT && i < hrows + 2 * TT) {   // warp-uniform; lanes 0 and 31 hold no output
@@ -224,6 +281,11 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
         for (int t = 0; t < TT; ++t)
 #pragma unroll
             for (int k = 0; k < LN; ++k) accP[t][k] = accC[t][k] = accN[t][k] = T(0);
+        if constexpr (JAC) {
+#pragma unroll
+            for (int t = 0; t < TT; ++t) rhs_row(y0 - TT - 1 - t, xb, rwin[t]);
+            rhs_row(y0 - TT, xb, rnext);
+        }
         for (int i = 0; i < nrows; i += RPS) {
             const bool ok = mbar_wait_bounded(&full[cs], cphase);
             if (__any_sync(0xffffffffu, !ok)) {
@@ -261,15 +323,16 @@ constexpr size_t tb_smem() {
     return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * SLOT;
 }
 
-template <int LAT, int PDE, int ST, int TT>
+template <int LAT, int PDE, int ST, int TT, bool JAC>
 cudaError_t launch_tb(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
+    using S = typename Storage<ST>::S;
     constexpr int NW = 4;
     constexpr int ES = ST == ST_F64 ? 8 : (ST == ST_F32 ? 4 : 2);
     constexpr int PER = ((2 * (128 + 2 * (16 / ES)) * ES + 127) / 128) * 128;
     constexpr int NSTAGE = 8192 / PER < 3 ? 3 : (8192 / PER > 12 ? 12 : 8192 / PER);
     constexpr size_t smem = tb_smem<ST, NW, NSTAGE>();
-    auto kern = k_march2d_tb<LAT, PDE, ST, TT, NW, NSTAGE>;
+    auto kern = k_march2d_tb<LAT, PDE, ST, TT, NW, NSTAGE, JAC>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -302,21 +365,34 @@ cudaError_t launch_tb(const LaunchArgs& a) {
     const int nitems = strips * ((a.g.ny + H - 1) / H);
     const int blocks_needed = (nitems + NW - 1) / NW;
     const int grid = blocks_needed < resident ? blocks_needed : resident;
+    const S* rhs = nullptr;
+    T jw = T(0);
+    if constexpr (JAC) {
+        rhs = static_cast<const S*>(a.src[0]);
+        jw = static_cast<const SrcCoef<T>*>(a.src_coef)->W0[0];
+    }
     kern<<<grid, NW * 32, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
-                                             nitems, a.err);
+                                             nitems, a.err, rhs, jw);
     return cudaGetLastError();
 }
 
-template <int LAT, int PDE, int ST>
+template <int LAT, int PDE, int ST, bool JAC = false>
 LaunchFn pick_depth(int depth) {
-    if (depth == 2) return launch_tb<LAT, PDE, ST, 2>;
+    if (depth == 2) return launch_tb<LAT, PDE, ST, 2, JAC>;
     if constexpr (ST != ST_F64) {
-        if (depth == 3) return launch_tb<LAT, PDE, ST, 3>;
-        if (depth == 4) return launch_tb<LAT, PDE, ST, 4>;
+        if (depth == 3) return launch_tb<LAT, PDE, ST, 3, JAC>;
+        if (depth == 4) return launch_tb<LAT, PDE, ST, 4, JAC>;
     }
     if constexpr (ST == ST_BF16) {
-        if (depth == 5) return launch_tb<LAT, PDE, ST, 5>;
+        if (depth == 5) return launch_tb<LAT, PDE, ST, 5, JAC>;
     }
+    return nullptr;
+}
+
+template <int LAT>
+LaunchFn pick_jac(int st, int depth) {
+    if (st == ST_F64) return pick_depth<LAT, PDE_LCDE, ST_F64, true>(depth);
+    if (st == ST_F32) return pick_depth<LAT, PDE_LCDE, ST_F32, true>(depth);
     return nullptr;
 }
 
@@ -339,6 +415,13 @@ LaunchFn find_march2d_tb(int lat, int pde, int levels, int st, int depth) {
         if (pde == PDE_LCDE) return pick_st<LAT_D2Q9, PDE_LCDE>(st, depth);
         if (pde == PDE_NCDE) return pick_st<LAT_D2Q9, PDE_NCDE>(st, depth);
     }
+    return nullptr;
+}
+
+LaunchFn find_march2d_tb_jacobi(int lat, int st, int depth) {
+    if (depth < 2) return nullptr;
+    if (lat == LAT_D2Q5) return pick_jac<LAT_D2Q5>(st, depth);
+    if (lat == LAT_D2Q9) return pick_jac<LAT_D2Q9>(st, depth);
     return nullptr;
 }
 

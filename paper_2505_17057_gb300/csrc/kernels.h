@@ -51,6 +51,10 @@ LaunchFn find_march3d(int lat, int pde, int levels, int st);
 // It reads the level through the same 2-row-box tensor maps as k_march2d.
 LaunchFn find_march2d_tb(int lat, int pde, int levels, int st, int depth);
 int march2d_tb_max_depth(int st);
+// The same kernel advancing `depth` Jacobi sweeps of the two-level LCDE theta-scheme per launch
+// (FP32 / FP64 levels): the coefficient block is the sweep's stencil, src[0] the right-hand
+// side and src_coef's W0[0] its weight.
+LaunchFn find_march2d_tb_jacobi(int lat, int st, int depth);
 // Temporally blocked 3D kernel (two-level LCDE on D3Q7 / D3Q19; nullptr elsewhere): depths as in
 // 2D.  It reads the level through tensor maps of one-row boxes ((128 + 2 x 16 B) x 1 x 1).
 LaunchFn find_march3d_tb(int lat, int pde, int levels, int st, int depth);

@@ -240,11 +240,27 @@ int solver_step(Solver* s, long long nsteps) {
             a.src[0] = a.src[1] = nullptr;
             cudaError_t e = s->fn_rhs(a);
             if (e != cudaSuccess) return cuda_fail(e, "theta-scheme right-hand side kernel");
-            for (int k = 0; k < s->r.sweeps; ++k) {
+            // sweeps fused `depth` per launch by the blocked kernel (a shallower blocked launch,
+            // with the launcher's own work-item height, or a single sweep for the remainder)
+            int left = s->r.sweeps;
+            while (left > 0) {
                 solver_launch_args(s, a);
-                e = s->fn(a);
+                LaunchFn f = s->fn;
+                int did = 1;
+                if (s->fn_block && s->depth > 1 && left >= 2) {
+                    did = left >= s->depth ? s->depth : left;
+                    f = did == s->depth ? s->fn_block : find_march2d_tb_jacobi(s->r.lat, s->r.st, did);
+                    if (did != s->depth) a.H = 0;
+                    if (!f) {
+                        f = s->fn;
+                        did = 1;
+                        a.H = s->H;
+                    }
+                }
+                e = f(a);
                 if (e != cudaSuccess) return cuda_fail(e, "theta-scheme sweep kernel");
                 s->cur = s->next();
+                left -= did;
             }
             s->steps_done += 1;
         }
@@ -369,7 +385,9 @@ void solver_blocked_maps(Solver* s, LaunchArgs& a) {
 
 void solver_use_depth(Solver* s, int depth) {
     LaunchFn fb = nullptr;
-    if (depth >= 2)
+    if (depth >= 2 && s->r.theta_on)
+        fb = s->r.dim == 2 ? find_march2d_tb_jacobi(s->r.lat, s->r.st, depth) : nullptr;
+    else if (depth >= 2)
         fb = s->r.dim == 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth)
                            : find_march3d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth);
     if (fb) {
@@ -429,6 +447,14 @@ int solver_pick_kernels(Solver* s) {
             // (The blocked kernel stages two rows per box, as the solver's maps for these PDEs do.)
             int maxd = march2d_tb_max_depth(s->r.st);
             while (maxd >= 2 && s->g.ny < 2 * maxd) --maxd;
+            if (s->r.theta_on && s->desc.temporal_depth != 1 && maxd >= 2 &&
+                find_march2d_tb_jacobi(s->r.lat, s->r.st, 2)) {
+                // theta-scheme: Jacobi sweeps fused per launch
+                s->max_depth = maxd;
+                int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
+                if (want > maxd) want = maxd;
+                solver_use_depth(s, want);
+            }
             if (!srcv && s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
                 find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
                 s->max_depth = maxd;

@@ -10,6 +10,8 @@ basis.  Tolerances as elsewhere: FP64 1e-12, FP32 1e-5 relative to the field's m
 - theta = 1 gives the explicit solver's result bit for bit;
 - the full-size workload (theta2d_4096): a plane wave is multiplied per step by Eq. (Tcond1-1)'s
   lambda (checked on sampled nodes) and the mass is conserved;
+- the Jacobi sweeps fused per launch by the blocked 2D kernel (depths 2 .. 4, with blocked and
+  single-sweep remainders) against the oracle;
 - the solve server refuses theta-scheme requests; the autotuner keeps the result.
 """
 import numpy as np
@@ -96,6 +98,40 @@ def test_theta_parity(mm, lat, n, storage, dt, theta, kernel):
     want = orc.theta_run(prob, L0, 4, theta)
     tol = 1e-12 if storage == "fp64" else 1e-5
     assert G.rel_err(got, want) <= tol, (lat, n, storage, theta, G.rel_err(got, want))
+
+
+# Jacobi sweeps fused per launch by the 2D blocked kernel: (case, temporal_depth asked, depth in
+# use).  The sweep counts (10, 12, 19, 10, 15, 8) leave a blocked remainder, none, a single-sweep
+# remainder, ...; ny = 8 is the smallest grid the depth-4 wavefront allows.
+BLOCKED = [
+    (("D2Q9", [300, 130], "fp32", 2.4, 0.5), 4, 4),
+    (("D2Q5", [257, 64], "fp32", 1.6, 0.0), 3, 3),
+    (("D2Q9", [300, 130], "fp64", 2.4, 0.5), 0, 2),
+    (("D2Q9", [128, 8], "fp32", 2.4, 0.5), 4, 4),
+    (("D2Q5", [200, 33], "fp64", 1.6, 0.7), 2, 2),
+    (("D2Q9", [131, 70], "fp32", 2.4, 0.7), 0, 4),
+]
+
+
+@pytest.mark.parametrize("case,asked,depth", BLOCKED)
+def test_theta_blocked_sweeps_parity(mm, case, asked, depth):
+    lat, n, storage, dt, theta = case
+    rng = np.random.default_rng(G.RNG_SEED + 1)
+    kw, prob = theta_case(lat, n, storage, dt, theta)
+    L0 = smooth_level(prob, rng)
+    s = mm.Solver(mm.make_desc(**kw, temporal_depth=asked))
+    try:
+        info = s.get_info()
+        assert info.kernel.decode() == "k_march2d_tb" and info.temporal_depth == depth
+        s.set_fields(L0)
+        s.step(4)
+        got = s.fields()
+        assert s.get_info().steps_done == 4
+    finally:
+        s.close()
+    want = orc.theta_run(prob, L0, 4, theta)
+    tol = 1e-12 if storage == "fp64" else 1e-5
+    assert G.rel_err(got, want) <= tol, (case, asked, G.rel_err(got, want))
 
 
 def test_theta_beyond_the_explicit_limit(mm):
@@ -185,11 +221,11 @@ def test_theta_autotune_keeps_the_result(mm):
     rng = np.random.default_rng(9)
     kw, prob = theta_case("D2Q9", [520, 300], "fp32", 2.4, 0.5)
     L0 = smooth_level(prob, rng)
-    s = mm.Solver(mm.make_desc(**kw))
+    s = mm.Solver(mm.make_desc(**kw, temporal_depth=0))
     try:
         s.set_fields(L0)
         t = s.autotune(None)
-        assert t.temporal_depth == 1
+        assert 1 <= t.temporal_depth <= 4
         s.set_fields(L0)
         s.step(3)
         got = s.fields()
