@@ -96,15 +96,16 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def traffic_from_profile(kernel: str, workload: str, depth: int = 1):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source and
+    at this temporal depth."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
     e = d.get(f"{workload}:{kernel}")
-    if not e or e.get("source_sha") != kernel_source_sha(kernel):
+    if not e or e.get("source_sha") != kernel_source_sha(kernel) or e.get("temporal_depth", 1) != depth:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -449,7 +450,8 @@ def run_ours(args):
             alg_bytes = es * (2 + 3 * sweep_launches) * nodes
             effective = bytes_per_lu * nodes / avg_launch_s / 1e9
         achieved = alg_bytes / avg_launch_s / 1e9
-        traffic = traffic_from_profile("k_march2d_theta" if theta else kernel_name, args.workload)
+        traffic = traffic_from_profile("k_march2d_theta" if theta else kernel_name, args.workload,
+                                       jd if theta else depth)
 
         # end to end through the public API: every step uploads the level from pinned host memory,
         # advances it, and reads back the FP64 field sums (the step's diagnostic result)
