@@ -507,19 +507,33 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
     // ---- create-time stability check (LCDE: exact symbol on the grid's wave numbers)
     r.max_lambda = -1.0;
     if (d.pde == PDE_LCDE) {
-        std::vector<double> th[3];
+        // Wave numbers per axis over the whole band: all of them up to 96 nodes, else the 16
+        // smallest of either sign (where convection-driven growth lives) and a uniform sweep of
+        // 64.  The weights are real, so the symbol at -xi is the conjugate of that at xi: the
+        // last axis takes only [0, pi].  The phase of pair p is a product of per-axis phasors.
+        const int last = dim - 1;
+        std::vector<std::complex<double>> ph[3];
         for (int a = 0; a < 3; ++a) {
             const long long n = a < dim ? d.n[a] : 1;
-            const double two_pi = 6.283185307179586;
+            std::vector<long long> ms;
             if (n <= 96) {
-                for (long long m = 0; m < n; ++m) th[a].push_back(two_pi * m / n);
+                for (long long m = 0; m < n; ++m) ms.push_back(m);
             } else {
-                // the grid's smallest wave numbers (where convection-driven growth lives) and a
-                // uniform sweep through the rest of the band
-                for (long long m = 0; m <= 16; ++m) th[a].push_back(two_pi * m / n);
-                for (int m = 1; m <= 64; ++m) th[a].push_back(two_pi * (double)((long long)((double)m * n / 128.0)) / n);
+                for (long long m = 0; m <= 16; ++m) {
+                    ms.push_back(m);
+                    if (m > 0) ms.push_back(n - m);
+                }
+                for (int m = 1; m < 64; ++m) ms.push_back((long long)((double)m * n / 64.0));
+            }
+            for (long long m : ms) {
+                if (a == last && 2 * m > n) continue;
+                ph[a].push_back(std::polar(1.0, 6.283185307179586 * (double)m / (double)n));
             }
         }
+        int pe[kMaxPair][3];
+        for (int p = 0; p < NP; ++p)
+            for (int a = 0; a < 3; ++a) pe[p][a] = a < dim ? pair_e(d.lattice, p, a) : 0;
+        const int nl = d.levels == 3 ? 2 : 1;
         double lmax = 0.0;
         // theta-scheme: per Fourier mode the sweeps start from phi^n, whose error is
         // ell / (1 - theta_1 ell) phi_hat^n, and multiply it by g = theta_1 (A - W0) / d each; the
@@ -528,18 +542,28 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
         int th_k = 1;
         bool sampled = false;
         for (int a = 0; a < dim; ++a) sampled = sampled || d.n[a] > 96;
-        for (double tz : th[2])
-            for (double ty : th[1])
-                for (double tx : th[0]) {
-                    std::complex<double> A[2];
-                    for (int l = 0; l < 2; ++l) {
-                        std::complex<double> s(c.W0[l], 0.0);
-                        for (int p = 0; p < NP; ++p) {
-                            const double ph = pair_e(d.lattice, p, 0) * tx + pair_e(d.lattice, p, 1) * ty +
-                                              (dim == 3 ? pair_e(d.lattice, p, 2) * tz : 0.0);
-                            s += c.Wp[l][p] * std::polar(1.0, ph) + c.Wm[l][p] * std::polar(1.0, -ph);
+        for (const std::complex<double>& qz : ph[2])
+            for (const std::complex<double>& qy : ph[1])
+                for (const std::complex<double>& qx : ph[0]) {
+                    const std::complex<double> q[3] = {qx, qy, qz};
+                    std::complex<double> e[kMaxPair];
+                    for (int p = 0; p < NP; ++p) {
+                        std::complex<double> v(1.0, 0.0);
+                        for (int a = 0; a < 3; ++a) {
+                            if (pe[p][a] == 1) v *= q[a];
+                            else if (pe[p][a] == -1) v *= std::conj(q[a]);
                         }
-                        A[l] = s;
+                        e[p] = v;
+                    }
+                    // W_p e^{i phase} + W_m e^{-i phase}
+                    std::complex<double> A[2] = {0.0, 0.0};
+                    for (int l = 0; l < nl; ++l) {
+                        double re = c.W0[l], im = 0.0;
+                        for (int p = 0; p < NP; ++p) {
+                            re += (c.Wp[l][p] + c.Wm[l][p]) * e[p].real();
+                            im += (c.Wp[l][p] - c.Wm[l][p]) * e[p].imag();
+                        }
+                        A[l] = std::complex<double>(re, im);
                     }
                     double m;
                     if (r.theta_on) {
