@@ -61,11 +61,12 @@ struct Req {
     LaunchFn solo = nullptr;
     LaunchFn solo_tb = nullptr;
     int solo_depth = 1;
-    CUtensorMap tmaps[3][4];
+    CUtensorMap tmaps[3][4] = {};   // march solos only (the direct kernel takes none)
 };
 
-// A request this large (and at least 128 columns wide) is stepped with the single-solve march
-// kernel (2D or 3D); smaller ones are packed into the batched kernel of their class.
+// A request this large is stepped with its own single-solve launches (the march kernel, 2D or
+// 3D, when it is at least 128 columns wide, else the direct kernel); smaller ones are packed
+// into the batched kernel of their class.
 constexpr long long kSoloNodes = 1ll << 16;
 
 struct ClassTables {
@@ -178,7 +179,8 @@ int admit(Server* s, Req* q) {
     q->init.clear();
     q->init.shrink_to_fit();
     q->solo = nullptr;
-    if (q->g.nx >= 128 && (long long)q->g.nx * q->g.ny * q->g.nz >= kSoloNodes) {
+    const bool large = (long long)q->g.nx * q->g.ny * q->g.nz >= kSoloNodes;
+    if (large && q->g.nx >= 128) {
         LaunchFn fn = q->g.dim == 2 ? find_march2d(q->r->lat, q->r->pde, q->r->levels, q->r->st)
                                     : find_march3d(q->r->lat, q->r->pde, q->r->levels, q->r->st);
         bool ok = fn != nullptr;
@@ -201,6 +203,10 @@ int admit(Server* s, Req* q) {
             }
         }
     }
+    // a large request too narrow for the march kernels runs its own one-node-per-thread
+    // launches: they take the coefficients as a kernel parameter, where the batched kernel reads
+    // them from its device table at every use
+    if (large && !q->solo) q->solo = find_direct(q->r->lat, q->r->pde, q->r->levels, q->r->st);
     q->cur = 0;
     q->state = RQ_ACTIVE;
     q->t_admit = now_s();
