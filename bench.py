@@ -79,11 +79,10 @@ KERNEL_SOURCES = {
     "k_march3d_tb": ["k_march3d_tb.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
                      "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     # one theta-scheme step: the right-hand side (k_march2d) and the Jacobi sweeps (k_march2d_tb
-    # fusing several per launch, k_march2d_src for single ones),
-    # their count and coefficients resolved in params.cpp and issued by solver.cpp
+    # fusing several per launch, k_march2d_src for single ones), issued by solver.cpp; the traffic
+    # entry also records the sweep count it was taken at
     "k_march2d_theta": ["k_march2d_src.cu", "k_march2d.cu", "k_march2d_tb.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh",
-                        "mmfd_internal.h", "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp",
-                        "solver.cpp"],
+                        "mmfd_internal.h", "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "solver.cpp"],
 }
 
 
@@ -96,9 +95,9 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel: str, workload: str, depth: int = 1):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source and
-    at this temporal depth."""
+def traffic_from_profile(kernel: str, workload: str, depth: int = 1, sweeps: int = 0):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source, at
+    this temporal depth and (theta-scheme) with this many Jacobi sweeps per step."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -106,6 +105,8 @@ def traffic_from_profile(kernel: str, workload: str, depth: int = 1):
         d = json.load(fh)
     e = d.get(f"{workload}:{kernel}")
     if not e or e.get("source_sha") != kernel_source_sha(kernel) or e.get("temporal_depth", 1) != depth:
+        return None
+    if e.get("sweeps", 0) != sweeps:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -451,7 +452,7 @@ def run_ours(args):
             effective = bytes_per_lu * nodes / avg_launch_s / 1e9
         achieved = alg_bytes / avg_launch_s / 1e9
         traffic = traffic_from_profile("k_march2d_theta" if theta else kernel_name, args.workload,
-                                       jd if theta else depth)
+                                       jd if theta else depth, info.sweeps)
 
         # end to end through the public API: every step uploads the level from pinned host memory,
         # advances it, and reads back the FP64 field sums (the step's diagnostic result)
