@@ -6,7 +6,8 @@ against closed-form solutions and between the storage precisions (FP64, FP32, BF
 prints one JSON line per case.  The closed forms are the analytic Taylor-Green decay (the NSE
 workloads; velocity error, GRE = sum |u - u*| / sum |u*| over both components) and the exact
 solution of the periodic linear CDE for the trigonometric interpolant of the initial field (the
-64^2 CDE workload).  Where no closed form exists (NCDE, 3D) the FP64 GPU run of the same
+64^2 CDE workload, and the heat equation for the Crank-Nicolson case).  Where no closed form
+exists (NCDE, 3D) the FP64 GPU run of the same
 configuration is the reference.  The FP64 GPU path itself is checked against the FP64 CPU oracle
 by the test suite (1e-12), so its error against a closed form is the scheme's discretisation
 error.  --quick runs reduced sizes and step counts.
@@ -115,10 +116,36 @@ def three_d(kind="cde3d", n=512, steps=1000):
     return res
 
 
+def theta_cn(ns=(64, 128, 256), kx=0.3, ky=0.2, t_end=1.0):
+    """Crank-Nicolson (the theta-scheme of Eq. (GCN) with theta = 1/2) on D2Q9 with u = 0 and
+    K = diag(kx, ky) on [0, 2 pi)^2, dt proportional to dx (n/4 steps to t_end, up to ~50x the
+    explicit scheme's diffusive limit), FP64: max error against the exact heat-equation solution
+    sin(x) sin(2y) exp(-(kx + 4 ky) t), and the observed order between successive grids."""
+    res = {"case": "theta_cn_d2q9", "reference": "exact heat-equation solution", "runs": []}
+    errs = []
+    for n in ns:
+        dx = 2 * math.pi / n
+        steps = n // 4
+        dt = t_end / steps
+        desc = dict(pde="LCDE", lattice="D2Q9", levels=2, n=[n, n], dt=dt, dx=[dx, dx], K=[[kx, 0.0], [0.0, ky]],
+                    u=[0.0, 0.0], targets=[0, -1, -1, 0, 0.5], theta=0.5)
+        g = np.arange(n) * dx
+        Y, X = np.meshgrid(g, g, indexing="ij")
+        phi0 = np.sin(X) * np.sin(2 * Y)
+        out, mass = _run(desc, [phi0], steps, "fp64")
+        err = float(np.abs(out[0] - phi0 * math.exp(-(kx + 4 * ky) * t_end)).max())
+        errs.append(err)
+        info = mmfd.mmfd_describe(mmfd.make_desc(**desc, storage="fp64"))
+        res["runs"].append({"n": n, "steps": steps, "dt_over_explicit_limit": dt / (dx * dx / (2 * (kx + ky))),
+                            "jacobi_sweeps": info.sweeps, "max_err": err, "mass_drift": mass})
+    res["orders"] = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--case", nargs="*", default=["cde2d", "tgv100", "tgv1000", "ncde2d", "cde3d", "nse3d"])
+    ap.add_argument("--case", nargs="*", default=["cde2d", "tgv100", "tgv1000", "ncde2d", "cde3d", "nse3d", "theta"])
     args = ap.parse_args()
     q = args.quick
     runs = {
@@ -128,6 +155,7 @@ def main():
         "ncde2d": lambda: ncde2d(256 if q else 1024, 1000 if q else 10000),
         "cde3d": lambda: three_d("cde3d", 128 if q else 512, 200 if q else 1000),
         "nse3d": lambda: three_d("nse3d", 128 if q else 512, 200 if q else 1000),
+        "theta": lambda: theta_cn((64, 128) if q else (64, 128, 256)),
     }
     import torch
     torch.cuda.init()

@@ -49,3 +49,27 @@ def test_3d_storages_against_fp64(acc, kind):
     assert abs(r["fp64"]["mass_drift"]) < 1e-13, r
     assert r["fp32"]["max_rel_vs_fp64"] < 1e-4, r
     assert r["bf16"]["max_rel_vs_fp64"] < 0.5, r
+
+
+def test_crank_nicolson_against_the_exact_solution(acc):
+    # the theta-scheme on the GPU (Jacobi sweeps) at time steps far beyond the explicit limit:
+    # second order against the exact solution, with the errors the oracle's exact solve of the
+    # same steps makes (test_oracle_theta pins that solve)
+    import math
+    import numpy as np
+    from oracle import oracle as orc
+    from oracle import params as P
+    r = acc.theta_cn()
+    assert all(1.9 <= o <= 2.1 for o in r["orders"]), r
+    kx, ky = 0.3, 0.2
+    for run in r["runs"]:
+        n, steps = run["n"], run["steps"]
+        dx = 2 * math.pi / n
+        prob = P.problem_lcde("D2Q9", 2, [n, n], 1.0 / steps, [dx, dx], [[kx, 0], [0, ky]], [0, 0],
+                              P.two_level_from_a0(0.0))
+        g = np.arange(n) * dx
+        Y, X = np.meshgrid(g, g, indexing="ij")
+        phi0 = np.sin(X) * np.sin(2 * Y)
+        want = np.abs(orc.theta_run(prob, [phi0], steps, 0.5)[0] - phi0 * math.exp(-(kx + 4 * ky))).max()
+        assert abs(run["max_err"] - want) <= 1e-3 * want and abs(run["mass_drift"]) < 1e-13, (run, want)
+    assert r["runs"][-1]["dt_over_explicit_limit"] > 20, r

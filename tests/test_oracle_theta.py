@@ -136,6 +136,25 @@ def test_crank_nicolson_converges_at_second_order():
     assert all(1.9 <= o <= 2.2 for o in orders), (errs, orders)
 
 
+def test_crank_nicolson_d2q9_converges_at_second_order():
+    # the same heat problem on D2Q9 (quadratic EDF, d_0 = 1/3): not the five-point scheme, but
+    # still second order with dt proportional to dx
+    kx, ky, T = 0.3, 0.2, 1.0
+    errs = []
+    for n in (32, 64, 128):
+        dx = 2 * np.pi / n
+        steps = n // 4
+        prob = P.problem_lcde("D2Q9", 2, [n, n], T / steps, [dx, dx], [[kx, 0], [0, ky]], [0.0, 0.0],
+                              P.two_level_from_a0(0.0))
+        g = np.arange(n) * dx
+        Y, X = np.meshgrid(g, g, indexing="ij")
+        phi0 = np.sin(X) * np.sin(2 * Y)
+        got = orc.theta_run(prob, [phi0], steps, 0.5)[0]
+        errs.append(np.abs(got - phi0 * np.exp(-(kx + 4 * ky) * T)).max())
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.9 <= o <= 2.1 for o in orders), (errs, orders)
+
+
 def test_theta_conserves_mass():
     prob = aniso_problem("D2Q9", (40, 30))
     phi = rand_field(prob)
