@@ -14,6 +14,8 @@ basis.  Tolerances as elsewhere: FP64 1e-12, FP32 1e-5 relative to the field's m
   single-sweep remainders) against the oracle;
 - the solve server refuses theta-scheme requests; the autotuner keeps the result.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -233,3 +235,36 @@ def test_theta_autotune_keeps_the_result(mm):
         s.close()
     want = orc.theta_run(prob, L0, 3, 0.5)
     assert G.rel_err(got, want) <= 1e-5
+
+
+def _random_cases(count, seed=20250603):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        lat = ["D2Q5", "D2Q9", "D3Q7", "D3Q19"][rng.integers(4)]
+        storage = ["fp32", "fp64"][rng.integers(2)]
+        if lat.startswith("D2"):
+            n = [int(rng.integers(128, 700)), int(rng.integers(8, 160))]
+        else:
+            n = [int(rng.integers(128, 220)), int(rng.integers(3, 24)), int(rng.integers(3, 12))]
+        out.append((lat, n, storage, float(rng.choice([0.8, 1.6, 2.4] if lat != "D2Q5" and lat != "D3Q7" else [0.8, 1.6])),
+                    float(rng.uniform(0.0, 0.9)), int(rng.integers(0, 5))))
+    return out
+
+
+@pytest.mark.parametrize("lat,n,storage,dt,theta,depth", _random_cases(16))
+def test_theta_random_shapes(mm, lat, n, storage, dt, theta, depth):
+    # seeded random lattices, storages, ragged grids, theta, time steps and fused-sweep depths
+    rng = np.random.default_rng(zlib.crc32(repr((lat, n, storage, theta)).encode()))
+    kw, prob = theta_case(lat, n, storage, dt, theta)
+    L0 = smooth_level(prob, rng)
+    s = mm.Solver(mm.make_desc(**kw, temporal_depth=depth))
+    try:
+        s.set_fields(L0)
+        s.step(3)
+        got = s.fields()
+    finally:
+        s.close()
+    want = orc.theta_run(prob, L0, 3, theta)
+    tol = 1e-12 if storage == "fp64" else 1e-5
+    assert G.rel_err(got, want) <= tol, (lat, n, storage, dt, theta, depth, G.rel_err(got, want))
