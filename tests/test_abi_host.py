@@ -331,3 +331,20 @@ def test_theta_descriptor(mm):
         _describe(mm, pde="NCDE", lattice="D2Q9", levels=2, n=[16, 16], dt=1.0, dx=[1, 1],
                   flux=[[0, 0.1, 0, 0], [0, 0.1, 0, 0]], diff=[0.1, 0, 0, 0], theta=0.5)
     assert e.value.code == mm.MMFD_ERR_UNSUPPORTED
+
+
+def test_theta_check_at_the_eq_tcond1_3_bound(mm):
+    # the create-time check accepts theta just inside theta* = 1/2 + min (-A / (A^2 + B^2))
+    # (Eq. (Tcond1-3), from the oracle's A and B) and refuses it just outside
+    prob = P.problem_lcde("D2Q5", 2, [16, 16], 1.0, [1, 1], [[0.3, 0], [0, 0.25]], [0.2, 0.1],
+                          P.two_level_from_a0(-2.0))
+    A, B = F.theta_AB(prob, prob.shape)
+    q = A * A + B * B
+    m = q > 1e-14
+    ts = 0.5 + float((-A[m] / q[m]).min())
+    heavy = dict(pde="LCDE", lattice="D2Q5", levels=2, n=[16, 16], dt=1.0, dx=[1, 1], K=[[0.3, 0], [0, 0.25]],
+                 u=[0.2, 0.1], a=P.two_level_from_a0(-2.0), storage="fp64")
+    assert _describe(mm, **heavy, theta=ts - 1e-3).max_lambda <= 1 + 1e-12
+    with pytest.raises(mm.MMFDError) as e:
+        _describe(mm, **heavy, theta=ts + 1e-3)
+    assert e.value.code == mm.MMFD_ERR_UNSTABLE

@@ -174,3 +174,36 @@ def test_theorem2_at_a_large_time_step():
         out = orc.theta_run(prob, [phi], 50, theta)[0]
         assert np.linalg.norm(out) <= n0 * (1 + 1e-12), theta
     assert np.linalg.norm(orc.theta_run(prob, [phi], 50, 1.0)[0]) > 1e3 * n0
+
+
+def theta_star(prob):
+    """The stability bound of Eq. (Tcond1-3) for A <= 0: |lambda| <= 1 on every mode iff
+    theta <= theta* = 1/2 + min over modes with A^2 + B^2 > 0 of (-A) / (A^2 + B^2)."""
+    A, B = F.theta_AB(prob, prob.shape)
+    q = A * A + B * B
+    m = q > 1e-14
+    assert (A[m] <= 1e-14).all()      # condition (a)
+    return 0.5 + float((-A[m] / q[m]).min())
+
+
+def heavy_problem():
+    return P.problem_lcde("D2Q5", 2, [16, 16], 1.0, [1, 1], [[0.3, 0], [0, 0.25]], [0.2, 0.1],
+                          P.two_level_from_a0(-2.0))
+
+
+def test_theta_bound_just_inside_and_outside():
+    # conditional stability for theta > 1/2 (Theorem 2 (2)): bounded just inside theta*, and just
+    # outside the oracle's growth rate per step tends to max |lambda| of Eq. (Tcond1-1)
+    prob = heavy_problem()
+    ts = theta_star(prob)
+    assert 0.5 < ts < 1.0, ts
+    phi = rand_field(prob)
+    n0 = np.linalg.norm(phi)
+    inside = orc.theta_run(prob, [phi], 400, ts - 0.01)[0]
+    assert np.linalg.norm(inside) <= n0 * (1 + 1e-10)
+    th = ts + 0.01
+    lam = np.abs(F.theta_lambda(prob, th, prob.shape)).max()
+    assert lam > 1.0
+    a = orc.theta_run(prob, [phi], 300, th)[0]
+    b = orc.theta_run(prob, [a], 1, th)[0]
+    assert abs(np.linalg.norm(b) / np.linalg.norm(a) - lam) <= 1e-6 * lam
