@@ -1,0 +1,48 @@
+"""Host logic of bench.py that decides what a JSON line may claim (no GPU): a committed ncu
+traffic figure is reported only for the kernel sources, temporal depth and sweep count it was
+taken on, and every kernel family the solver can name has its source list."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _entries():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        return json.load(fh)
+
+
+def test_source_lists_name_existing_files():
+    csrc = os.path.join(ROOT, "paper_2505_17057_gb300", "csrc")
+    for kernel, files in bench.KERNEL_SOURCES.items():
+        for f in files:
+            assert os.path.exists(os.path.join(csrc, f)), (kernel, f)
+
+
+def test_traffic_matches_only_its_capture_conditions():
+    for key, e in _entries().items():
+        workload, kernel = key.split(":")
+        depth, sweeps = e.get("temporal_depth", 1), e.get("sweeps", 0)
+        if e["source_sha"] != bench.kernel_source_sha(kernel):
+            continue   # a stale entry is reported as null, which the next check also covers
+        assert bench.traffic_from_profile(kernel, workload, depth, sweeps) == e["dram_bytes_per_launch"]
+        assert bench.traffic_from_profile(kernel, workload, depth + 1, sweeps) is None
+        assert bench.traffic_from_profile(kernel, workload, depth, sweeps + 1) is None
+        assert bench.traffic_from_profile(kernel, "other_workload", depth, sweeps) is None
+
+
+def test_traffic_is_null_once_a_source_changes(monkeypatch):
+    key, e = next(iter(_entries().items()))
+    workload, kernel = key.split(":")
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda k: "0" * 16)
+    assert bench.traffic_from_profile(kernel, workload, e.get("temporal_depth", 1), e.get("sweeps", 0)) is None
+
+
+@pytest.mark.parametrize("ranks,nodes,steps,seconds,want", [(1, 100, 10, 1.0, 1e-3), (4, 100, 10, 2.0, 2e-3)])
+def test_job_mlups_counts_every_rank(ranks, nodes, steps, seconds, want):
+    assert bench.job_mlups(ranks, nodes, steps, seconds) == pytest.approx(want)
