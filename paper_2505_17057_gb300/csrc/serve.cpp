@@ -64,9 +64,11 @@ struct Req {
     CUtensorMap tmaps[3][4] = {};   // march solos only (the direct kernel takes none)
 };
 
-// A request this large is stepped with its own single-solve launches (the march kernel, 2D or
-// 3D, when it is at least 128 columns wide, else the direct kernel); smaller ones are packed
-// into the batched kernel of their class.
+// A request this large is stepped with its own single-solve launches (the march kernel when it
+// is at least 128 columns wide in 2D or 64 in 3D, else the direct kernel); smaller ones are
+// packed into the batched kernel of their class.  A 3D grid of 64 .. 127 columns fills only part
+// of the GPU with march items, which is why a single solve keeps the direct kernel there; in the
+// server the solos of several requests run side by side and fill it.
 constexpr long long kSoloNodes = 1ll << 16;
 
 struct ClassTables {
@@ -180,7 +182,7 @@ int admit(Server* s, Req* q) {
     q->init.shrink_to_fit();
     q->solo = nullptr;
     const bool large = (long long)q->g.nx * q->g.ny * q->g.nz >= kSoloNodes;
-    if (large && q->g.nx >= 128) {
+    if (large && q->g.nx >= (q->g.dim == 3 ? 64 : 128)) {
         LaunchFn fn = q->g.dim == 2 ? find_march2d(q->r->lat, q->r->pde, q->r->levels, q->r->st)
                                     : find_march3d(q->r->lat, q->r->pde, q->r->levels, q->r->st);
         bool ok = fn != nullptr;
