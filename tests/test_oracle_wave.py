@@ -117,3 +117,38 @@ def test_wave_stability_is_p1_within_2():
         if rmax > 1 + 1e-9 and np.all(np.abs(p1 + np.conj(p1) * p0) <= 1 - np.abs(p0) ** 2 + 1e-12):
             degenerate += 1
     assert total > 40 and 5 < unstable < total - 5 and agree == total and degenerate == unstable
+
+
+# ----------------------------------------------------------------------------- Table 4
+
+def _table4():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "example3_table4.json")) as fh:
+        return json.load(fh)
+
+
+def test_example3_table4_case1_reproduced():
+    # Example 3 as printed (Dirichlet values of exp(x + y + t), the paper's start-up, GRE over the
+    # interior nodes at t = 1): Case 1 (D2Q5) gives the printed GRE of Table 4 to its three digits
+    import example3_dirichlet as E3
+    t4 = _table4()
+    for nx, printed in zip(t4["nx"], t4["gre"]["case1"]):
+        prob, _, _, _ = E3.problem(1, nx)
+        got = E3.interior_gre(1, nx, lambda cur, prev: orc.step(prob, [cur], [prev])[0])
+        assert float("%.2e" % got) == float(printed), (nx, got, printed)    # equal to the printed digits
+
+
+def test_example3_table4_cases2_3_order():
+    # Cases 2-3 (D2Q9) converge at second order as Table 4 says, but their absolute GRE comes out
+    # 5-10x below the printed values under the same procedure (parity unpinned, see the readings)
+    import example3_dirichlet as E3
+    t4 = _table4()
+    for case in (2, 3):
+        gres = []
+        for nx in t4["nx"]:
+            prob, _, _, _ = E3.problem(case, nx)
+            gres.append(E3.interior_gre(case, nx, lambda cur, prev: orc.step(prob, [cur], [prev])[0]))
+        assert all(1.9 <= o <= 2.4 for o in E3.orders(gres)), (case, gres)
+        printed = [float(v) for v in t4["gre"][f"case{case}"]]
+        assert all(g < p / 4 for g, p in zip(gres, printed)), (case, gres, printed)
