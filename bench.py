@@ -446,7 +446,22 @@ def run_ours(args):
         jd = max(1, info.temporal_depth)
         sweep_launches = info.sweeps // jd + (1 if info.sweeps % jd else 0)
         launches_per_step = (1 + sweep_launches) if theta else 1
+        theta_launches = None
         if theta:
+            # what one step launches: the right-hand side, then the sweeps (fused jd per launch; a
+            # remainder of one runs on the single-sweep kernel, a longer one on a shallower fused launch)
+            full, rem = divmod(info.sweeps, jd)
+            single = kernel_name.replace("_tb", "_src") if kernel_name.endswith("_tb") else kernel_name
+            parts = [kernel_name.replace("_tb", "").replace("_src", "") + " (right-hand side)"]
+            if jd > 1:
+                parts.append(f"{full} x {kernel_name} ({jd} sweeps each)")
+                if rem == 1:
+                    parts.append(f"1 x {single}")
+                elif rem > 1:
+                    parts.append(f"1 x {kernel_name} ({rem} sweeps)")
+            else:
+                parts.append(f"{info.sweeps} x {kernel_name}")
+            theta_launches = " + ".join(parts)
             es = {"fp32": 4, "fp64": 8}[args.storage]
             alg_bytes = es * (2 + 3 * sweep_launches) * nodes
             effective = bytes_per_lu * nodes / avg_launch_s / 1e9
@@ -510,7 +525,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": (kernel_name + " + k_march2d (one theta step)") if theta else kernel_name,
+                     "kernel": theta_launches if theta else kernel_name,
                      "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                      "effective_gbs": effective,
