@@ -202,7 +202,11 @@ int mmfd_desc_init(mmfd_desc* d);
  * create-time stability check, and allocate the level buffers.  *out owns all device memory.
  * The stability check covers the LCDE only (the exact amplification symbol on the grid's wave
  * numbers, Sec. III); NCDE and NSE problems are nonlinear and are not checked here -- watch
- * them with mmfd_reduce(..., MMFD_RED_NONFINITE, ...). */
+ * them with mmfd_reduce(..., MMFD_RED_NONFINITE, ...).
+ * The step kernel family is chosen here (mmfd_get_info names it): the TMA marching kernels for
+ * grids at least 128 nodes wide, the one-node-per-thread direct kernel otherwise.  Setting the
+ * environment variable MMFD_FORCE_KERNEL=direct before mmfd_create selects the direct kernel
+ * for any grid (for comparisons; it computes the same update). */
 int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
 
 /* Copy one level into the solver.  level 0 = t_n, level 1 = t_{n-1} (three-level only).
