@@ -55,6 +55,9 @@ def job_mlups(ranks: int, nodes_per_rank: int, steps: int, seconds: float) -> fl
     return ranks * nodes_per_rank * steps / seconds / 1e6
 
 
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the measured copy bandwidth is the denominator of frac)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -525,6 +528,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "kernel": theta_launches if theta else kernel_name,
                      "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
