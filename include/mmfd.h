@@ -60,6 +60,10 @@ enum { MMFD_SRC_NONE = 0, MMFD_SRC_S = 1, MMFD_SRC_SU = 2, MMFD_SRC_SM = 3 };
 #define MMFD_FLAG_TWO_SETS 0x8u         /* multiple-parameter-set scheme, Eq. (2-2-1b): see mmfd_desc */
 #define MMFD_FLAG_THETA 0x10u           /* two-level theta-scheme, Eq. (GCN): see mmfd_desc */
 
+/* Boundary treatment (mmfd_desc.boundary). */
+#define MMFD_BC_PERIODIC 0              /* periodic in every direction (the default) */
+#define MMFD_BC_DIRICHLET 1             /* prescribed values on the outermost ring of nodes */
+
 typedef int (*mmfd_alloc_fn)(size_t bytes, void** ptr, void* ctx);
 typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
 
@@ -141,6 +145,16 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        iteration would not contract.  The stability check uses Eq. (Tcond1-1).
  *                        temporal_depth fuses sweeps (see there); the server does not take such
  *                        requests.
+ *  boundary              MMFD_BC_PERIODIC (0, default) or MMFD_BC_DIRICHLET: the nodes with
+ *                        x = 0 or nx - 1, y = 0 or ny - 1 (and z = 0 or nz - 1 in 3D) hold
+ *                        prescribed values.  Every step updates the other nodes as usual (their
+ *                        stencils reach only nodes of the grid) and then sets the boundary nodes
+ *                        of the new level from the boundary values (mmfd_set_boundary; until it
+ *                        is called, those of the field given to mmfd_set_fields level 0).  This
+ *                        is how Example 3 of Sec. IV is posed (exact values on the boundary).
+ *                        Needs at least 3 nodes along every axis; runs unblocked; not with the
+ *                        theta-scheme; the server does not take such requests.  The create-time
+ *                        stability check still uses the periodic symbol.
  */
 typedef struct {
     int pde, lattice, levels;
@@ -170,6 +184,7 @@ typedef struct {
     int source;
     double b[3], bhat[3];
     double theta;
+    int boundary;
 } mmfd_desc;
 
 /* Derived constants of a created solver (read-only view, for checking and reporting). */
@@ -229,6 +244,12 @@ int mmfd_set_fields(mmfd_solver* s, int level, const void* const* fields, int wh
  * level 0 also sets level 1 unless level 1 is set explicitly.  Both levels start at zero.
  * MMFD_ERR_STATE if the solver has no source. */
 int mmfd_set_source(mmfd_solver* s, int level, const void* const* fields, int where, int dtype);
+
+/* MMFD_BC_DIRICHLET solvers: the boundary values the following steps give the boundary nodes of
+ * every new level (set them before each step for time-dependent values).  fields: nf pointers
+ * to full nx*ny*nz arrays (x fastest) of type dtype on host or device, of which only the
+ * boundary nodes are used; copied, not retained.  MMFD_ERR_STATE if the solver is periodic. */
+int mmfd_set_boundary(mmfd_solver* s, const void* const* fields, int where, int dtype);
 
 /* Advance nsteps time levels (Eq. (2-2-2) / Eq. (3layerMMFD-1)), asynchronously on the
  * solver's stream. */

@@ -243,6 +243,61 @@ dim3 grid_rows(const Geom& g) {
 
 }  // namespace
 
+namespace {
+
+// The boundary ring of a grid (nodes with x = 0 / nx - 1, y = 0 / ny - 1, and z = 0 / nz - 1 in
+// 3D), enumerated face by face without repeats: in 3D the two z faces whole, then the two y faces
+// between them, then the two x faces between those; in 2D the y faces and then the x faces.
+__host__ __device__ inline long long ring_nodes(const Geom& g) {
+    const long long zn = g.dim == 3 ? g.nz - 2 : 1;
+    return (g.dim == 3 ? 2ll * g.nx * g.ny : 0ll) + 2ll * g.nx * zn + 2ll * (g.ny - 2) * zn;
+}
+
+template <typename E>
+__global__ void k_ring_copy(Geom g, const E* __restrict__ src, E* __restrict__ dst, long long count) {
+    const long long zn = g.dim == 3 ? g.nz - 2 : 1;
+    const int z0 = g.dim == 3 ? 1 : 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long k = i;
+        int x, y, z;
+        const long long zface = g.dim == 3 ? (long long)g.nx * g.ny : 0;
+        const long long yface = (long long)g.nx * zn;
+        const long long xface = (long long)(g.ny - 2) * zn;
+        if (k < 2 * zface) {
+            z = k < zface ? 0 : g.nz - 1;
+            const long long r = k % zface;
+            x = (int)(r % g.nx);
+            y = (int)(r / g.nx);
+        } else if ((k -= 2 * zface) < 2 * yface) {
+            y = k < yface ? 0 : g.ny - 1;
+            const long long r = k % yface;
+            x = (int)(r % g.nx);
+            z = z0 + (int)(r / g.nx);
+        } else {
+            k -= 2 * yface;
+            x = k < xface ? 0 : g.nx - 1;
+            const long long r = k % xface;
+            y = 1 + (int)(r % (g.ny - 2));
+            z = z0 + (int)(r / (g.ny - 2));
+        }
+        const long long at = g.at(x, y, z);
+        for (int f = 0; f < g.nf; ++f) dst[(long long)f * g.fs + at] = src[(long long)f * g.fs + at];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ring_copy(const Geom& g, const void* src_level, void* dst_level, cudaStream_t s) {
+    const long long count = ring_nodes(g);
+    if (count <= 0) return cudaSuccess;
+    const int blocks = (int)((count + 255) / 256 < 1184 ? (count + 255) / 256 : 1184);
+    if (g.es == 8) k_ring_copy<unsigned long long><<<blocks, 256, 0, s>>>(g, static_cast<const unsigned long long*>(src_level), static_cast<unsigned long long*>(dst_level), count);
+    else if (g.es == 4) k_ring_copy<unsigned int><<<blocks, 256, 0, s>>>(g, static_cast<const unsigned int*>(src_level), static_cast<unsigned int*>(dst_level), count);
+    else k_ring_copy<unsigned short><<<blocks, 256, 0, s>>>(g, static_cast<const unsigned short*>(src_level), static_cast<unsigned short*>(dst_level), count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, void* dst_level, int field,
                         double ref, cudaStream_t s) {
     const dim3 blocks = grid_rows(g);

@@ -72,6 +72,9 @@ cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, v
                         double ref, cudaStream_t s);
 cudaError_t launch_unpack(const Geom& g, int st, const void* src_level, int field, double ref, void* dst,
                           int dst_dtype, cudaStream_t s);
+// Copy the boundary ring (x = 0 / nx - 1, y = 0 / ny - 1, z = 0 / nz - 1 in 3D) of every field
+// from one level buffer to another of the same layout and storage (Dirichlet boundaries).
+cudaError_t launch_ring_copy(const Geom& g, const void* src_level, void* dst_level, cudaStream_t s);
 // Deterministic FP64 reductions over the interior of one field: op 0 sum, 1 max|v|,
 // 2 non-finite count; with ref != NULL: op 3 -> (sum |v - ref|, sum |ref|, max |v - ref|, max |ref|).
 cudaError_t launch_reduce(const Geom& g, int st, const void* level, int field, double fref, int op,

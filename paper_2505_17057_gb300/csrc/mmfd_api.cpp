@@ -214,6 +214,12 @@ int mmfd_set_source(mmfd_solver* h, int level, const void* const* fields, int wh
     return solver_set_source(s, level, fields, where, dtype);
 }
 
+int mmfd_set_boundary(mmfd_solver* h, const void* const* fields, int where, int dtype) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !fields) return set_error(MMFD_ERR_ARG, "null argument");
+    return solver_set_boundary(s, fields, where, dtype);
+}
+
 int mmfd_step(mmfd_solver* h, long long nsteps) {
     Solver* s = reinterpret_cast<Solver*>(h);
     if (!s || nsteps < 0) return set_error(MMFD_ERR_ARG, "bad argument");

@@ -458,6 +458,17 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
     //     x <- rhs / d + (theta_1 / d) (E - W0 I) x,
     // i.e. an LCDE stencil without a centre weight plus a centre-only source term rhs / d.  The
     // sweep contracts by at most rho = theta_1 sum_p (|Wp| + |Wm|) / d per step.
+    // ---- boundary treatment
+    if (d.boundary != MMFD_BC_PERIODIC && d.boundary != MMFD_BC_DIRICHLET)
+        return fail(msg, MMFD_ERR_ARG, "unknown boundary treatment");
+    r.dirichlet = d.boundary == MMFD_BC_DIRICHLET ? 1 : 0;
+    if (r.dirichlet) {
+        for (int a = 0; a < dim; ++a)
+            if (d.n[a] < 3) return fail(msg, MMFD_ERR_ARG, "Dirichlet boundaries need at least 3 nodes along every axis");
+        if (d.flags & MMFD_FLAG_THETA)
+            return fail(msg, MMFD_ERR_UNSUPPORTED, "the theta-scheme is built for periodic grids");
+    }
+
     r.theta_on = (d.flags & MMFD_FLAG_THETA) != 0 ? 1 : 0;
     r.theta = 1.0;
     r.sweeps = 0;

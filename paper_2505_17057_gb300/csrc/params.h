@@ -30,6 +30,7 @@ struct Resolved {
     // two-level theta-scheme (Eq. (GCN)): right-hand side (I + theta L) phi^n as an LCDE stencil
     // (thr), Jacobi sweep x <- x_rhs / d + ((1 - theta) / d) (E - W0 I) x as an LCDE stencil (thj)
     // plus a centre-only source block (ths) with weight 1 / d, d = 1 + (1 - theta)(1 - W0)
+    int dirichlet;      // MMFD_BC_DIRICHLET: boundary ring of nodes prescribed
     int theta_on;
     double theta;
     int sweeps;

@@ -587,13 +587,14 @@ int mmfd_submit(mmfd_server* h, const mmfd_desc* d, const void* const* init, int
         s->st.rejected++;
         return set_error(rc, msg);
     }
-    if (q->r->src || q->r->theta_on) {
-        const bool src = q->r->src != 0;
+    if (q->r->src || q->r->theta_on || q->r->dirichlet) {
+        const char* why = q->r->src ? "the server does not take requests with source terms"
+                        : q->r->theta_on ? "the server does not take theta-scheme requests"
+                                         : "the server takes periodic requests only";
         delete q->r;
         delete q;
         s->st.rejected++;
-        return set_error(MMFD_ERR_UNSUPPORTED, src ? "the server does not take requests with source terms"
-                                                   : "the server does not take theta-scheme requests");
+        return set_error(MMFD_ERR_UNSUPPORTED, why);
     }
     q->desc = *d;
     q->g = make_geom(*q->r);

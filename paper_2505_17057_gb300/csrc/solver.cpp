@@ -60,6 +60,13 @@ int solver_init_device(Solver* s) {
         s->src_i0 = s->src_i1 = 0;
         s->src_fresh = true;
     }
+    if (s->r.dirichlet) {
+        // boundary values, in the level layout and storage
+        rc = dev_alloc(s, s->level_bytes, &s->bnd);
+        if (rc != MMFD_OK) return rc;
+        cudaError_t e = cudaMemsetAsync(s->bnd, 0, s->level_bytes, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
     if (s->r.theta_on) {
         // same element size and ghosted layout as a level (FP64 / FP32 storage only)
         rc = dev_alloc(s, s->level_bytes, &s->rhs);
@@ -90,6 +97,8 @@ void solver_free_device(Solver* s) {
     }
     dev_free(s, s->rhs);
     s->rhs = nullptr;
+    dev_free(s, s->bnd);
+    s->bnd = nullptr;
     dev_free(s, s->d_red);
     s->d_red = nullptr;
     dev_free(s, s->d_flag);
@@ -141,6 +150,11 @@ int solver_set_fields(Solver* s, int level, const void* const* fields, int where
             e = launch_pack(s->g, s->r.st, src, dtype, s->lev[s->prev()], f, s->r.ref[f], s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
         }
+        if (s->r.dirichlet && level == 0) {
+            // Dirichlet: the boundary keeps these values until mmfd_set_boundary replaces them
+            e = launch_pack(s->g, s->r.st, src, dtype, s->bnd, f, s->r.ref[f], s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
+        }
     }
     s->fields_set = true;
     if (level == 0) s->src_fresh = true;
@@ -187,6 +201,34 @@ int solver_set_source(Solver* s, int level, const void* const* fields, int where
             }
         }
         cudaError_t e = launch_pack(gs, sst, src, dtype, s->srcbuf[idx], f, 0.0, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
+    }
+    return MMFD_OK;
+}
+
+int solver_set_boundary(Solver* s, const void* const* fields, int where, int dtype) {
+    if (!s->r.dirichlet) return set_error(MMFD_ERR_STATE, "the solver has periodic boundaries");
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    if (where != MMFD_HOST && where != MMFD_DEVICE) return set_error(MMFD_ERR_ARG, "where must be HOST or DEVICE");
+    const size_t bytes = (size_t)nodes(s) * (dtype == MMFD_DT_F64 ? 8 : 4);
+    int rc;
+    if (where == MMFD_HOST && (rc = ensure_stage(s)) != MMFD_OK) return rc;
+    for (int f = 0; f < s->g.nf; ++f) {
+        if (!fields[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
+        const void* src = fields[f];
+        if (where == MMFD_HOST) {
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, src) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                pa.devicePointer) {
+                src = pa.devicePointer;
+            } else {
+                cudaGetLastError();
+                cudaError_t e = cudaMemcpyAsync(s->stage, src, bytes, cudaMemcpyHostToDevice, s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+                src = s->stage;
+            }
+        }
+        cudaError_t e = launch_pack(s->g, s->r.st, src, dtype, s->bnd, f, s->r.ref[f], s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
     }
     return MMFD_OK;
@@ -285,6 +327,11 @@ int solver_step(Solver* s, long long nsteps) {
             cudaError_t e = s->fn(a);
             if (e != cudaSuccess) return cuda_fail(e, "step kernel");
             s->cur = s->next();
+            if (s->r.dirichlet) {
+                // the new level's boundary nodes take the prescribed values
+                e = launch_ring_copy(s->g, s->bnd, s->lev[s->cur], s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "boundary kernel");
+            }
             s->steps_done += 1;
             done += 1;
             if (s->r.src) {
@@ -455,7 +502,7 @@ int solver_pick_kernels(Solver* s) {
                 if (want > maxd) want = maxd;
                 solver_use_depth(s, want);
             }
-            if (!srcv && s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
+            if (!srcv && !s->r.dirichlet && s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
                 find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
                 s->max_depth = maxd;
                 int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
@@ -491,7 +538,7 @@ int solver_pick_kernels(Solver* s) {
             s->H = 0;
             // temporal blocking (two-level LCDE): the blocked kernel streams one-row boxes of the
             // level, with rows and planes wrapped periodically, so any ny and nz will do
-            if (!srcv && s->desc.temporal_depth != 1 &&
+            if (!srcv && !s->r.dirichlet && s->desc.temporal_depth != 1 &&
                 find_march3d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
                 bool ok = true;
                 for (int b = 0; b < s->nlev && ok; ++b)

@@ -44,6 +44,7 @@ struct Solver {
     size_t src_bytes = 0;
     int src_i0 = 0, src_i1 = 0;                  // buffers holding the sources at t_n and t_{n-1}
     bool src_fresh = true;                       // no step since creation or set_fields(level 0)
+    void* bnd = nullptr;                         // Dirichlet: boundary values (a level in the level layout)
     void* rhs = nullptr;                         // theta-scheme: right-hand side (I + theta L) phi^n
     LaunchFn fn_rhs = nullptr;                   // theta-scheme: kernel writing rhs (plain LCDE step)
 
@@ -62,6 +63,7 @@ int solver_init_device(Solver* s);
 void solver_free_device(Solver* s);
 int solver_set_fields(Solver* s, int level, const void* const* fields, int where, int dtype);
 int solver_set_source(Solver* s, int level, const void* const* fields, int where, int dtype);
+int solver_set_boundary(Solver* s, const void* const* fields, int where, int dtype);
 int solver_step(Solver* s, long long nsteps);
 int solver_get_fields(Solver* s, int level, void* const* out, int where, int dtype);
 int solver_reduce(Solver* s, int what, double* out);

@@ -42,6 +42,7 @@ MMFD_FLAG_DROP_OFFDIAG = 0x2
 MMFD_FLAG_STOCHASTIC_ROUND = 0x4
 MMFD_FLAG_TWO_SETS = 0x8
 MMFD_FLAG_THETA = 0x10
+MMFD_BC_PERIODIC, MMFD_BC_DIRICHLET = 0, 1
 MMFD_RED_SUM, MMFD_RED_MAXABS, MMFD_RED_NONFINITE = 0, 1, 2
 MMFD_SRC_NONE, MMFD_SRC_S, MMFD_SRC_SU, MMFD_SRC_SM = 0, 1, 2, 3
 
@@ -69,7 +70,7 @@ class mmfd_desc(C.Structure):
         ("seed", C.c_ulonglong), ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", C.c_void_p),
         ("source", C.c_int), ("b", C.c_double * 3), ("bhat", C.c_double * 3),
-        ("theta", C.c_double),
+        ("theta", C.c_double), ("boundary", C.c_int),
     ]
 
 
@@ -115,6 +116,7 @@ SIGNATURES = {
     "mmfd_create": (C.c_int, [C.POINTER(mmfd_desc), _PV]),
     "mmfd_set_fields": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
     "mmfd_set_source": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
+    "mmfd_set_boundary": (C.c_int, [_VP, _PV, C.c_int, C.c_int]),
     "mmfd_step": (C.c_int, [_VP, C.c_longlong]),
     "mmfd_fields": (C.c_int, [_VP, C.c_int, _PV, C.c_int, C.c_int]),
     "mmfd_reduce": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_double)]),
@@ -238,6 +240,10 @@ def mmfd_set_source(h: int, level: int, ptrs: Sequence[int], where: int, dtype: 
     check(lib.mmfd_set_source(h, level, _ptr_array(ptrs), where, dtype), "mmfd_set_source")
 
 
+def mmfd_set_boundary(h: int, ptrs: Sequence[int], where: int, dtype: int) -> None:
+    check(lib.mmfd_set_boundary(h, _ptr_array(ptrs), where, dtype), "mmfd_set_boundary")
+
+
 def mmfd_step(h: int, nsteps: int) -> None:
     check(lib.mmfd_step(h, int(nsteps)), "mmfd_step")
 
@@ -296,7 +302,7 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
               rho0: float = 1.0, a=None, ahat=None, abar=None, abarhat=None, targets=None, targets_bar=None,
               d0=None, flags: int = 0, ref=None, temporal_depth: int = 1, seed: Optional[int] = None,
               stream: Optional[int] = None, sets: Optional[dict] = None, source: str = "none",
-              b=None, bhat=None, theta: Optional[float] = None) -> mmfd_desc:
+              b=None, bhat=None, theta: Optional[float] = None, boundary: str = "periodic") -> mmfd_desc:
     """Fill an mmfd_desc (plain field assignment; every derived constant is computed by the library).
 
     sets: the multiple-parameter-set scheme (MMFD_FLAG_TWO_SETS): a dict with "d2", "d1" and,
@@ -305,6 +311,7 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
     coefficient triples (None: the library's defaults).
     theta: the two-level theta-scheme of Eq. (GCN) with this theta (MMFD_FLAG_THETA); None: the
     explicit scheme.
+    boundary: "periodic" or "dirichlet" (prescribed values on the outermost ring of nodes).
     """
     d = mmfd_desc_init()
     d.pde = PDE[pde]
@@ -374,6 +381,7 @@ def make_desc(pde: str, lattice: str, levels: int, n: Sequence[int], dt: float, 
     if theta is not None:
         d.flags |= MMFD_FLAG_THETA
         d.theta = float(theta)
+    d.boundary = {"periodic": MMFD_BC_PERIODIC, "dirichlet": MMFD_BC_DIRICHLET}[boundary]
     if seed is not None:
         d.seed = int(seed)
     if stream is not None:
@@ -472,6 +480,19 @@ class Solver:
         else:
             arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
             mmfd_set_source(self.h, level, [a.ctypes.data for a in arrs], MMFD_HOST, MMFD_DT_F64)
+
+    def set_boundary(self, fields):
+        """Dirichlet solvers: boundary values for the following steps, as full fields (numpy
+        arrays on the host or CUDA torch tensors) of which the boundary nodes are used."""
+        t = self.torch
+        if fields and isinstance(fields[0], t.Tensor) and fields[0].is_cuda:
+            f32 = all(f.dtype == t.float32 and f.is_contiguous() for f in fields)
+            ts = list(fields) if f32 else [f.contiguous().to(t.float64) for f in fields]
+            mmfd_set_boundary(self.h, [f.data_ptr() for f in ts], MMFD_DEVICE, MMFD_DT_F32 if f32 else MMFD_DT_F64)
+            self._keep_bnd = ts
+        else:
+            arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+            mmfd_set_boundary(self.h, [a.ctypes.data for a in arrs], MMFD_HOST, MMFD_DT_F64)
 
     def step(self, nsteps: int = 1):
         mmfd_step(self.h, nsteps)

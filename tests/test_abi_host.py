@@ -348,3 +348,20 @@ def test_theta_check_at_the_eq_tcond1_3_bound(mm):
     with pytest.raises(mm.MMFDError) as e:
         _describe(mm, **heavy, theta=ts + 1e-3)
     assert e.value.code == mm.MMFD_ERR_UNSTABLE
+
+
+def test_dirichlet_descriptor(mm):
+    base = dict(pde="LCDE", lattice="D2Q9", levels=2, n=[32, 16], dt=1.0, dx=[1, 1], K=np.eye(2) * 0.02,
+                u=[0.1, 0.0])
+    _describe(mm, **base, boundary="dirichlet")
+    for bad, code in [(dict(n=[32, 2]), mm.MMFD_ERR_ARG), (dict(theta=0.5), mm.MMFD_ERR_UNSUPPORTED)]:
+        kw = dict(base, boundary="dirichlet")
+        kw.update(bad)
+        with pytest.raises(mm.MMFDError) as e:
+            _describe(mm, **kw)
+        assert e.value.code == code, bad
+    d = mm.make_desc(**base)
+    d.boundary = 7
+    with pytest.raises(mm.MMFDError) as e:
+        mm.mmfd_describe(d)
+    assert e.value.code == mm.MMFD_ERR_ARG
