@@ -142,10 +142,53 @@ def theta_cn(ns=(64, 128, 256), kx=0.3, ky=0.2, t_end=1.0):
     return res
 
 
+def example3(nxs=(5, 10, 20, 40)):
+    """Example 3 of Sec. IV as printed: the wave equation d_t^2 phi = (1/2) lap phi on [0, 1]^2 with
+    Dirichlet values of the exact solution exp(x + y + t) set before every step (MMFD_BC_DIRICHLET),
+    N_t = 2 N_x, the second level from the printed Taylor start-up; GRE over the interior nodes at
+    t = 1 for Cases 1-3 (FP64), next to the values Table 4 prints."""
+    cases = {1: ("D2Q5", 3 / 8), 2: ("D2Q9", 3 / 8), 3: ("D2Q9", 1 / 2)}
+    printed = {1: [2.86e-4, 6.09e-5, 1.39e-5, 3.30e-6], 2: [6.04e-3, 1.74e-3, 4.55e-4, 1.16e-4],
+               3: [3.91e-3, 1.13e-3, 2.97e-4, 7.58e-5]}
+    res = {"case": "example3", "reference": "exact solution exp(x + y + t); Table 4 of the paper"}
+    for c, (lat, gamma) in cases.items():
+        gres = []
+        for nx in nxs:
+            dx, nt = 1.0 / nx, 2 * nx
+            dt = 1.0 / nt
+            g = np.arange(nx + 1) * dx
+            Y, X = np.meshgrid(g, g, indexing="ij")
+            p0 = np.exp(X + Y)
+            second = np.zeros_like(p0)
+            second[1:-1, :] += p0[2:, :] - 2 * p0[1:-1, :] + p0[:-2, :]
+            second[:, 1:-1] += p0[:, 2:] - 2 * p0[:, 1:-1] + p0[:, :-2]
+            p1 = p0 + dt * p0 + (dt / (2 * dx)) ** 2 * second
+            e1 = np.exp(X + Y + dt)
+            for sl in ((0, slice(None)), (-1, slice(None)), (slice(None), 0), (slice(None), -1)):
+                p1[sl] = e1[sl]
+            s = mmfd.Solver(mmfd.make_desc("LWE", lat, 3, [nx + 1, nx + 1], dt, [dx, dx], K=0.5 * np.eye(2),
+                                           storage="fp64", boundary="dirichlet", **mmfd.mmfd_wave_coefficients(gamma)))
+            try:
+                s.set_fields([p1])
+                s.set_fields([p0], level=1)
+                for m in range(1, nt):
+                    s.set_boundary([np.exp(X + Y + (m + 1) * dt)])
+                    s.step(1)
+                out = s.fields()[0]
+            finally:
+                s.close()
+            ex = np.exp(X + Y + 1.0)
+            gres.append(float(np.abs(out - ex)[1:-1, 1:-1].sum() / np.abs(ex)[1:-1, 1:-1].sum()))
+        res[f"case{c}"] = {"nx": list(nxs), "gre": gres, "printed": printed[c][:len(nxs)],
+                           "orders": [math.log2(gres[i] / gres[i + 1]) for i in range(len(gres) - 1)]}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--case", nargs="*", default=["cde2d", "tgv100", "tgv1000", "ncde2d", "cde3d", "nse3d", "theta"])
+    ap.add_argument("--case", nargs="*",
+                    default=["cde2d", "tgv100", "tgv1000", "ncde2d", "cde3d", "nse3d", "theta", "example3"])
     args = ap.parse_args()
     q = args.quick
     runs = {
@@ -156,6 +199,7 @@ def main():
         "cde3d": lambda: three_d("cde3d", 128 if q else 512, 200 if q else 1000),
         "nse3d": lambda: three_d("nse3d", 128 if q else 512, 200 if q else 1000),
         "theta": lambda: theta_cn((64, 128) if q else (64, 128, 256)),
+        "example3": lambda: example3(),
     }
     import torch
     torch.cuda.init()
