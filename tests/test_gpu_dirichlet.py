@@ -6,7 +6,9 @@
 - Parity with the oracle for every PDE on 2D and 3D lattices and the three kernel families: the
   oracle takes a periodic step and then resets the boundary ring, which is the definition of
   the boundary treatment (interior stencils never reach past the ring).  FP64 1e-12, FP32 1e-5.
-- Time-dependent boundary values from device memory; the server refuses such requests.
+- Time-dependent boundary values from device memory; sources together with the boundary; a 3D
+  heat problem with zero boundary values converging at second order to its closed form; the
+  server refuses such requests.
 """
 import json
 import os
@@ -141,3 +143,60 @@ def test_server_refuses_dirichlet(mm):
         assert e.value.code == mm.MMFD_ERR_UNSUPPORTED
     finally:
         srv.close()
+
+
+def test_dirichlet_with_sources(mm):
+    # source terms and a prescribed boundary together (FP64): the oracle steps with the same
+    # sources and then resets the ring
+    rng = np.random.default_rng(23)
+    kw, prob = G.case("D2Q9", "LCDE", 3, [150, 40], "fp64")
+    b3, b3h = (1.2, 0.1, 0.2), (-0.4, 0.0, -0.1)
+    kw.update(source="s", b=b3, bhat=b3h)
+    prob.source, prob.b, prob.bhat = "s", b3, b3h
+    L0, L1 = G.random_level(prob, rng), G.random_level(prob, rng)
+    srcs = [[0.3 + 0.2 * rng.standard_normal(prob.shape)] for _ in range(5)]
+    ring = _ring_mask(prob.shape)
+    s = mm.Solver(mm.make_desc(**kw, boundary="dirichlet"))
+    try:
+        s.set_fields(L0)
+        s.set_fields(L1, level=1)
+        s.set_source(srcs[0], level=1)
+        for m in range(1, 4):
+            s.set_source(srcs[m])
+            s.step(1)
+        got = s.fields()
+    finally:
+        s.close()
+    cur, prev = L0, L1
+    for m in range(1, 4):
+        new = orc.step(prob, cur, prev, src=(srcs[m], srcs[m - 1]))
+        new[0][ring] = L0[0][ring]
+        prev, cur = cur, new
+    assert G.rel_err(got, cur) <= 1e-12
+
+
+def test_dirichlet_3d_heat_converges(mm):
+    # D3Q7 LCDE with u = 0 on [0, 1]^3, zero boundary values: phi = sin(pi x) sin(pi y) sin(pi z)
+    # decays as exp(-3 pi^2 kappa t); with dt proportional to dx^2 the error falls at second order
+    kappa, t_end = 0.05, 0.1
+    errs = []
+    for nx in (16, 32):
+        n = nx + 1
+        dx = 1.0 / nx
+        dt = 0.1 * dx * dx / kappa      # derived d_0 = 2 kappa dt / dx^2 = 0.2 per axis (App. A: sum < 1)
+        steps = int(round(t_end / dt))
+        dt = t_end / steps
+        g = np.arange(n) * dx
+        Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+        phi0 = np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)
+        s = mm.Solver(mm.make_desc("LCDE", "D3Q7", 2, [n, n, n], dt, [dx] * 3, K=kappa * np.eye(3), u=[0.0] * 3,
+                                   targets=[0, -1, -1, 0, 0.5], storage="fp64", boundary="dirichlet"))
+        try:
+            s.set_fields([phi0])
+            s.step(steps)
+            out = s.fields()[0]
+        finally:
+            s.close()
+        errs.append(float(np.abs(out - phi0 * np.exp(-3 * np.pi ** 2 * kappa * t_end)).max()))
+    order = np.log2(errs[0] / errs[1])
+    assert 1.9 <= order <= 2.2 and errs[1] < 1e-3, (errs, order)
