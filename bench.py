@@ -77,6 +77,11 @@ KERNEL_SOURCES = {
                      "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     "k_march3d": ["k_march3d.cuh", "k_march3d.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
                   "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
+    # the lean He-Luo NSE variants (streaming / general momentum) of the marching kernels
+    "k_march2d_nse_s": ["k_march_lean.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
+                        "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp"],
+    "k_march3d_nse_s": ["k_march_lean.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh",
+                        "mmfd_internal.h", "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp"],
     "k_march2d_src": ["k_march2d_src.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
                       "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     "k_march3d_tb": ["k_march3d_tb.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",

@@ -215,13 +215,20 @@ int mmfd_desc_init(mmfd_desc* d);
 
 /* Validate the descriptor, resolve the scheme coefficients and EDF constants, run the
  * create-time stability check, and allocate the level buffers.  *out owns all device memory.
- * The stability check covers the LCDE only (the exact amplification symbol on the grid's wave
- * numbers, Sec. III); NCDE and NSE problems are nonlinear and are not checked here -- watch
- * them with mmfd_reduce(..., MMFD_RED_NONFINITE, ...).
+ * The stability check is exact for the LCDE (the amplification symbol on the grid's wave numbers,
+ * Sec. III); NCDE and NSE problems are checked linearised about their reference state (see
+ * mmfd_linear_stability; mmfd_check_fields repeats it about the fields' extreme states) -- watch
+ * long nonlinear runs with mmfd_reduce(..., MMFD_RED_NONFINITE, ...).
  * The step kernel family is chosen here (mmfd_get_info names it): the TMA marching kernels for
- * grids at least 128 nodes wide, the one-node-per-thread direct kernel otherwise.  Setting the
- * environment variable MMFD_FORCE_KERNEL=direct before mmfd_create selects the direct kernel
- * for any grid (for comparisons; it computes the same update). */
+ * grids at least 128 nodes wide, the one-node-per-thread direct kernel otherwise.  For the
+ * He-Luo NSE with one speed on every axis on D2Q9, or on D3Q19 with d_0 = 1/3 (FP32 / BF16 storage)
+ * the marching kernels run a lean form of the same update: the uu terms of Eq. (3-3) through
+ * |u|^2 and (e_p . u)^2, a+ / a- folded into the pair parts, and, when the momentum set is
+ * proportional to the scalar one ((abar-, abar+) = kappa (a+, a-), e.g. LBGK tau = 1), the
+ * momentum taken from the scalar contributions (kernel names *_nse_s, else *_nse_g).  Setting
+ * the environment variable MMFD_FORCE_KERNEL=direct before mmfd_create selects the direct
+ * kernel for any grid, MMFD_FORCE_KERNEL=generic the general pair form (for comparisons; both
+ * compute the same update). */
 int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
 
 /* Copy one level into the solver.  level 0 = t_n, level 1 = t_{n-1} (three-level only).
@@ -273,6 +280,25 @@ int mmfd_reduce(mmfd_solver* s, int what, double* out);
  * synchronous. */
 int mmfd_error_norms(mmfd_solver* s, int field, const void* ref, int where, int dtype, double* out);
 
+/* Frozen-coefficient stability of the nonlinear schemes (the paper analyses the linear CDE only,
+ * Sec. III.D, Theorems 1-3; the NCDE and NSE are checked here linearised about a uniform state).
+ * The update is linearised about `state` -- NCDE: (phi); NSE: (rho, u_x, u_y[, u_z]) -- and a
+ * Fourier mode of the perturbation is multiplied per level by the scheme's symbol matrix
+ * (Eq. (TforMMFD-3) with the EDF's Jacobian; three-level: the companion matrix of Eq. (3-level)).
+ * *max_amp = the largest eigenvalue modulus over the grid's wave numbers (all of them up to 96
+ * per axis, else a sample).  Returns MMFD_ERR_UNSTABLE when it exceeds 1 + 1e-9 (*max_amp set),
+ * MMFD_OK otherwise, MMFD_ERR_UNSUPPORTED for the linear PDEs (mmfd_create checks those exactly).
+ * Host only.  mmfd_create runs the same check about the reference state (the NCDE at
+ * phi = ref[0], 0 unless given; the NSE at rest, rho0 and u = 0) and refuses an unstable
+ * descriptor unless MMFD_FLAG_ALLOW_UNSTABLE is set. */
+int mmfd_linear_stability(const mmfd_desc* desc, const double* state, double* max_amp);
+
+/* The same check about the extreme states of the solver's current level: the NCDE at nine values
+ * of phi spanning [-max|phi|, max|phi|], the NSE at rho0 with u at the origin and on the corners
+ * of the box |u_a| <= max|u_a|.  Synchronous (field reductions on the solver's stream);
+ * MMFD_ERR_NONFINITE if the level holds non-finite values. */
+int mmfd_check_fields(mmfd_solver* s, double* max_amp);
+
 /* mmfd_reduce_static: the deterministic FP64 reduction of mmfd_reduce (what = MMFD_RED_SUM,
  * MMFD_RED_MAXABS or MMFD_RED_NONFINITE) over one dense device array, for callers that cannot
  * allocate device memory at the point of use (cudaFree synchronises the whole device and both
@@ -285,10 +311,15 @@ int mmfd_error_norms(mmfd_solver* s, int field, const void* ref, int where, int 
  *   count  1 .. 2^27 elements (larger counts return MMFD_ERR_ARG: the scratch has one slot
  *          per 2^17 elements);
  *   out    device pointer to one double, written asynchronously on `stream`.
- * The first call on a device looks up the scratch array's device address (with that device
- * current); make that first call before any stream capture.  All calls share the array and
- * each overwrites the slots it uses, so nothing needs clearing; calls that overlap on the GPU
- * (other streams or threads) race on it and must be serialised by the caller. */
+ * field and out must be device memory of the current device, or managed memory; a host
+ * pointer or another device's pointer returns MMFD_ERR_ARG before anything is launched.
+ * Outside stream capture every call looks up the scratch array's device address with the
+ * current device (so a cudaDeviceReset, after which the array may move, is harmless); a call
+ * made while `stream` is capturing reuses the address of the last uncaptured call on that
+ * device, so the first call on a device must come before any capture (MMFD_ERR_STATE
+ * otherwise).  All calls share the array and each overwrites the slots it uses, so nothing
+ * needs clearing; calls that overlap on the GPU (other streams or threads) race on it and must
+ * be serialised by the caller. */
 int mmfd_reduce_static(const void* field, int dtype, long long count, int what, double* out, void* stream);
 
 int mmfd_get_info(const mmfd_solver* s, mmfd_info_t* out);
@@ -335,7 +366,11 @@ typedef struct {
 
 int mmfd_autotune(mmfd_solver* s, const char* cache_path, mmfd_tune_info* out);
 
-/* Resolve a descriptor's constants without touching the GPU (info filled as by create). */
+/* Resolve a descriptor's constants without touching the GPU (info filled as by create; kernel
+ * names the step kernel family create would pick for a periodic explicit solver: the marching
+ * kernels from 128 columns -- k_march2d / k_march3d, or their lean He-Luo NSE variants *_nse_s
+ * (streaming momentum) and *_nse_g (general momentum) for FP32 / BF16 storage with one speed on
+ * every axis on D2Q9, or on D3Q19 with d_0 = 1/3 -- and k_direct otherwise). */
 int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out);
 
 /* Diagnostic: launch a kernel whose mbarrier wait can never complete and check that the

@@ -312,7 +312,7 @@ __device__ __forceinline__ void source_quad(const Geom& g, const SrcArgs<T>& sa,
     }
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE>
 __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ TmapSet maps, Geom g,
                                                      void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                      StepExtra ex, int H, int nitems, int* __restrict__ err,
@@ -436,6 +436,46 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                         if constexpr (TM >= 0 && TM < LN) {
                             if constexpr (EY == 1) accN[TM][0] += cf.Wm[l][P_] * phi;
                             else accC[TM][0] += cf.Wm[l][P_] * phi;
+                        }
+                    });
+                } else if constexpr (PDE == PDE_NSE && LEAN != LEAN_NONE) {
+                    // lean He-Luo form (Coef::nA): a+ / a- folded into E', O'; one FMA per pair
+                    // on a per-node base shared by the axis / diagonal pairs
+                    constexpr int MASK = pushed_pairs<LAT, LN>(C);
+                    const T* f = raw[C + 1];
+                    const T rho = f[0], ux = f[1], uy = f[2];
+                    const T U = uy * uy + ux * ux;
+                    if constexpr (OWN) {
+                        accC[C][0] += cf.nc[l][1] * U + cf.nc[l][0] * rho;
+                        accC[C][1] += cf.ab0[l] * ux;
+                        accC[C][2] += cf.ab0[l] * uy;
+                    }
+                    constexpr bool AX = (MASK & 3) != 0, DG = (MASK & 12) != 0;
+                    [[maybe_unused]] T Bk[2];
+                    if constexpr (AX) Bk[0] = cf.nU[l][0] * U + cf.nA[l][0] * rho;
+                    if constexpr (DG) Bk[1] = cf.nU[l][1] * U + cf.nA[l][1] * rho;
+                    static_for<0, NP>([&](auto pcc) {
+                        constexpr int P_ = decltype(pcc)::value;
+                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+                        constexpr int TP = C - EX, TM = C + EX;
+                        constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
+                        if constexpr (HP || HM) {
+                            const T cu = edot<LAT, P_>(ux, uy, T(0));
+                            const T E = cf.nk[l][P_] * (cu * cu) + Bk[pair_class(LAT, P_)];
+                            const T O = cf.no[l][P_] * cu;
+                            [[maybe_unused]] T sE = T(0), mO = T(0);
+                            if constexpr (LEAN == LEAN_GENERAL) {
+                                sE = cf.ap[l] * E;
+                                mO = cf.abp[l] * O;
+                            }
+                            if constexpr (HP) {
+                                T* acc = EY == 1 ? accP[TP] : accC[TP];
+                                lean_push<LAT, LEAN, P_, 1, NF>(acc, cf, l, E, O, sE, mO);
+                            }
+                            if constexpr (HM) {
+                                T* acc = EY == 1 ? accN[TM] : accC[TM];
+                                lean_push<LAT, LEAN, P_, -1, NF>(acc, cf, l, E, O, sE, mO);
+                            }
                         }
                     });
                 } else {
@@ -674,12 +714,12 @@ constexpr int march2d_stages() {
     return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE>
 cudaError_t launch_march2d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE, LN, RPS>();
-    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC>;
+    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC, LEAN>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -26,7 +26,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0>
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE>
 __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant__ TmapSet maps, Geom g,
                                                            void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                            StepExtra ex, int H, int nitems, int* __restrict__ err,
@@ -171,6 +171,57 @@ __global__ void __launch_bounds__((TY + 1) * 32) k_march3d(const __grid_constant
                                     else accC[KM][0] += cf.Wm[l][P_] * phi;
                                 }
                             });
+                        } else if constexpr (PDE == PDE_NSE && LEAN != LEAN_NONE) {
+                            // lean He-Luo form (Coef::nA): a+ / a- folded into E', O'; one FMA
+                            // per pair on a per-node base shared by the axis / diagonal pairs
+                            constexpr auto uses = [](int p) constexpr {
+                                const int ex = pair_e(LAT, p, 0), ey = pair_e(LAT, p, 1);
+                                const bool plus = DY == ey && C - ex >= 0 && C - ex < LN;
+                                const bool minus = DY == -ey && C + ex >= 0 && C + ex < LN;
+                                return plus || minus;
+                            };
+                            constexpr bool CENTRE = DY == 0 && C >= 0 && C < LN;
+                            constexpr bool AX = uses(0) || uses(1) || uses(2);
+                            constexpr bool DG = uses(3) || uses(4) || uses(5) || uses(6) || uses(7) || uses(8);
+                            if constexpr (CENTRE || AX || DG) {
+                                const T rho = f[0], ux = f[1], uy = f[2], uz = f[3];
+                                const T U = uz * uz + (uy * uy + ux * ux);
+                                if constexpr (CENTRE) {
+                                    accC[C][0] += cf.nc[l][1] * U + cf.nc[l][0] * rho;
+                                    accC[C][1] += cf.ab0[l] * ux;
+                                    accC[C][2] += cf.ab0[l] * uy;
+                                    accC[C][3] += cf.ab0[l] * uz;
+                                }
+                                [[maybe_unused]] T Bk[2];
+                                if constexpr (AX) Bk[0] = cf.nU[l][0] * U + cf.nA[l][0] * rho;
+                                if constexpr (DG) Bk[1] = cf.nU[l][1] * U + cf.nA[l][1] * rho;
+                                static_for<0, NP>([&](auto pcc) {
+                                    constexpr int P_ = decltype(pcc)::value;
+                                    constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1),
+                                                  EZ = pair_e(LAT, P_, 2);
+                                    constexpr int KP = C - EX, KM = C + EX;
+                                    constexpr bool HP = DY == EY && KP >= 0 && KP < LN;
+                                    constexpr bool HM = DY == -EY && KM >= 0 && KM < LN;
+                                    if constexpr (HP || HM) {
+                                        const T cu = edot<LAT, P_>(ux, uy, uz);
+                                        const T E = cf.nk[l][P_] * (cu * cu) + Bk[pair_class(LAT, P_)];
+                                        const T O = cf.no[l][P_] * cu;
+                                        [[maybe_unused]] T sE = T(0), mO = T(0);
+                                        if constexpr (LEAN == LEAN_GENERAL) {
+                                            sE = cf.ap[l] * E;
+                                            mO = cf.abp[l] * O;
+                                        }
+                                        if constexpr (HP) {
+                                            T* acc = EZ == 1 ? accP[KP] : accC[KP];
+                                            lean_push<LAT, LEAN, P_, 1, NF>(acc, cf, l, E, O, sE, mO);
+                                        }
+                                        if constexpr (HM) {
+                                            T* acc = EZ == 1 ? accN[KM] : accC[KM];
+                                            lean_push<LAT, LEAN, P_, -1, NF>(acc, cf, l, E, O, sE, mO);
+                                        }
+                                    }
+                                });
+                            }
                         } else {
                             constexpr auto uses = [](int p) constexpr {
                                 const int ex = pair_e(LAT, p, 0), ey = pair_e(LAT, p, 1);
@@ -289,13 +340,13 @@ constexpr int march3d_stages() {
     return n < 2 ? 2 : (n > 8 ? 8 : (int)n);
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0>
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE>
 cudaError_t launch_march3d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march3d_smem<ST, LEVELS, NF, TY, NSTAGE>();
     constexpr int THREADS = (TY + 1) * 32;
-    auto kern = k_march3d<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC>;
+    auto kern = k_march3d<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC, LEAN>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -18,6 +18,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "../../include/mmfd.h"
 #include "solver.h"
@@ -73,26 +74,46 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_final(const double* _
     if (threadIdx.x == 0) *out = sh[0];
 }
 
-// Device address of g_static_parts, looked up once per device with that device current.
-// (In host code the symbol's name is only a host-side stand-in, not a device address.)  The
-// first call on a device performs this lookup; make that first call before any stream capture.
+// Device address of g_static_parts for the current device.  In host code the symbol's name is
+// only a host-side stand-in, not a device address, so the address is looked up with the device
+// current.  Outside stream capture it is looked up on every call (cheap once the module is
+// loaded; after cudaDeviceReset the module is loaded again and the array may move); during
+// capture the address cached by the last uncaptured call on that device is used, so the first
+// call on a device must come before any capture (MMFD_ERR_STATE otherwise).
 constexpr int kMaxDevices = 64;
 double* g_parts_addr[kMaxDevices] = {};
 std::mutex g_parts_mu;
 
-int static_parts_for_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+int static_parts_for_current_device(int dev, cudaStream_t stream, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return set_error(MMFD_ERR_ARG, "device ordinal out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lock(g_parts_mu);
-    if (!g_parts_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_parts);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
         g_parts_addr[dev] = static_cast<double*>(p);
+    } else if (!g_parts_addr[dev]) {
+        return set_error(MMFD_ERR_STATE, "the first mmfd_reduce_static call on a device must precede stream capture");
     }
     *out = g_parts_addr[dev];
+    return MMFD_OK;
+}
+
+// field and out must be device memory of the current device (or managed memory): a host
+// pointer or another GPU's pointer handed to the kernels would fault the GPU.
+int check_device_pointer(const void* p, int dev, const char* name) {
+    cudaPointerAttributes pa{};
+    cudaError_t e = cudaPointerGetAttributes(&pa, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MMFD_ERR_ARG, std::string(name) + " is not a device pointer");
+    }
+    if (pa.type == cudaMemoryTypeManaged) return MMFD_OK;
+    if (pa.type != cudaMemoryTypeDevice) return set_error(MMFD_ERR_ARG, std::string(name) + " is not device memory");
+    if (pa.device != dev) return set_error(MMFD_ERR_ARG, std::string(name) + " belongs to another device");
     return MMFD_OK;
 }
 
@@ -109,11 +130,17 @@ extern "C" int mmfd_reduce_static(const void* field, int dtype, long long count,
     if (count < 1) return set_error(MMFD_ERR_ARG, "count must be positive");
     if (count > (long long)kStaticParts * kElemsPerBlock)
         return set_error(MMFD_ERR_ARG, "count exceeds the static scratch capacity of 2^27 elements");
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "cudaGetDevice");
+    int rc = check_device_pointer(field, dev, "field");
+    if (rc == MMFD_OK) rc = check_device_pointer(out, dev, "out");
+    if (rc != MMFD_OK) return rc;
     double* parts = nullptr;
-    int rc = static_parts_for_current_device(&parts);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = static_parts_for_current_device(dev, s, &parts);
     if (rc != MMFD_OK) return rc;
     const int nblocks = (int)((count + kElemsPerBlock - 1) / kElemsPerBlock);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_static_parts<<<nblocks, kStaticThreads, 0, s>>>(field, dtype, count, what, parts);
     k_static_final<<<1, kStaticThreads, 0, s>>>(parts, nblocks, what, out);
     cudaError_t e = cudaGetLastError();

@@ -62,6 +62,10 @@ LaunchFn find_march3d_tb(int lat, int pde, int levels, int st, int depth);
 LaunchFn find_march3d_src(int lat, int pde, int levels, int st, int src);
 // Rows of the x-y tile a 3D march CTA stages per plane (the TMA box is 128+halo x rows+2 x 1).
 int march3d_tile_rows(int pde);
+// The 2D (D2Q9) and 3D (D3Q19) marching kernels in the lean He-Luo NSE form (lean = LEAN_STREAM
+// or LEAN_GENERAL, see Coef::nA; FP32 / BF16 storage, two or three levels; nullptr elsewhere).
+// They take the same tensor maps and launch arguments as find_march2d / find_march3d.
+LaunchFn find_march_lean(int lat, int levels, int st, int lean);
 
 // Encode a 2D / 3D tiled TMA descriptor over one field of a ghosted level buffer
 // (box = boxw x 1 [x 1] elements).  Returns 0 on success.

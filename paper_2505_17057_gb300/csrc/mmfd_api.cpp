@@ -2,6 +2,7 @@
 // layout, set/get of fields, stepping, reductions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -171,7 +172,41 @@ int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out) {
         return set_error(rc, msg);
     }
     fill_info(*r, out);
+    // the step kernel family mmfd_create would pick, as far as it follows from the descriptor
+    // alone: the marching kernels from 128 columns (their lean He-Luo variants where the host
+    // check accepts the coefficients, FP32 / BF16 storage), the direct kernel below
+    const bool march = r->n[0] >= 128 && !r->theta_on && r->src == 0;
+    const char* name = "k_direct";
+    if (march) {
+        const bool lean = r->lean != LEAN_NONE && r->st != ST_F64;
+        if (r->dim == 2) name = !lean ? "k_march2d" : r->lean == LEAN_STREAM ? "k_march2d_nse_s" : "k_march2d_nse_g";
+        else name = !lean ? "k_march3d" : r->lean == LEAN_STREAM ? "k_march3d_nse_s" : "k_march3d_nse_g";
+    }
+    std::strncpy(out->kernel, name, sizeof(out->kernel) - 1);
     delete r;
+    return MMFD_OK;
+}
+
+int mmfd_linear_stability(const mmfd_desc* desc, const double* state, double* max_amp) {
+    if (!desc || !state || !max_amp) return set_error(MMFD_ERR_ARG, "null argument");
+    if (desc->pde != MMFD_NCDE && desc->pde != MMFD_NSE)
+        return set_error(MMFD_ERR_UNSUPPORTED, "linearised check: NCDE and NSE only (mmfd_create checks the linear PDEs exactly)");
+    const int nst = desc->pde == MMFD_NSE ? 1 + desc->dim : 1;
+    for (int i = 0; i < nst; ++i)
+        if (!std::isfinite(state[i])) return set_error(MMFD_ERR_ARG, "non-finite state");
+    mmfd_desc d = *desc;
+    d.flags |= MMFD_FLAG_ALLOW_UNSTABLE;
+    Resolved* r = new (std::nothrow) Resolved;
+    if (!r) return MMFD_ERR_OOM;
+    std::string msg;
+    int rc = resolve(d, *r, &msg);
+    if (rc != MMFD_OK) {
+        delete r;
+        return set_error(rc, msg);
+    }
+    *max_amp = linear_amplification(*r, state, true);
+    delete r;
+    if (*max_amp > 1.0 + 1e-9) return set_error(MMFD_ERR_UNSTABLE, "max |lambda| > 1 for the linearised scheme");
     return MMFD_OK;
 }
 
@@ -236,6 +271,38 @@ int mmfd_reduce(mmfd_solver* h, int what, double* outv) {
     Solver* s = reinterpret_cast<Solver*>(h);
     if (!s || !outv) return set_error(MMFD_ERR_ARG, "null argument");
     return solver_reduce(s, what, outv);
+}
+
+int mmfd_check_fields(mmfd_solver* h, double* max_amp) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !max_amp) return set_error(MMFD_ERR_ARG, "null argument");
+    if (s->r.pde != PDE_NCDE && s->r.pde != PDE_NSE)
+        return set_error(MMFD_ERR_UNSUPPORTED, "linearised check: NCDE and NSE only (mmfd_create checks the linear PDEs exactly)");
+    double mx[4] = {0.0, 0.0, 0.0, 0.0};
+    int rc = solver_reduce(s, MMFD_RED_MAXABS, mx);
+    if (rc != MMFD_OK) return rc;
+    for (int f = 0; f < s->r.nf; ++f)
+        if (!std::isfinite(mx[f])) return set_error(MMFD_ERR_NONFINITE, "non-finite values in the current level");
+    double lmax = 0.0;
+    if (s->r.pde == PDE_NCDE) {
+        // nine states spanning [-max|phi|, max|phi|]
+        for (int i = 0; i <= 8; ++i) {
+            const double st[1] = {mx[0] * (i - 4) / 4.0};
+            lmax = std::max(lmax, linear_amplification(s->r, st, true));
+        }
+    } else {
+        // rho0 with u at the origin and on the corners of the box |u_a| <= max |u_a|
+        const int dim = s->r.dim;
+        for (int corner = -1; corner < (1 << dim); ++corner) {
+            double st[4] = {s->desc.rho0, 0.0, 0.0, 0.0};
+            if (corner >= 0)
+                for (int a = 0; a < dim; ++a) st[1 + a] = ((corner >> a) & 1) ? mx[1 + a] : -mx[1 + a];
+            lmax = std::max(lmax, linear_amplification(s->r, st, true));
+        }
+    }
+    *max_amp = lmax;
+    if (lmax > 1.0 + 1e-9) return set_error(MMFD_ERR_UNSTABLE, "max |lambda| > 1 for the scheme linearised about the fields' extreme states");
+    return MMFD_OK;
 }
 
 int mmfd_error_norms(mmfd_solver* h, int field, const void* ref, int where, int dtype, double* outv) {

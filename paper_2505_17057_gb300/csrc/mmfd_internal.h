@@ -77,7 +77,20 @@ struct Coef {
     T flux[3][4], m2[5];               // NCDE polynomials
     T ePhi[kMaxPair], eM2[kMaxPair], rPhi, rM2;  // NCDE: E_p = ePhi phi + eM2 M2(phi)
     T ref[4];                          // BF16 offsets per field
+    // He-Luo NSE, lean form (host-checked, see nse_lean in params.cpp): with one speed c on every
+    // axis, on D2Q9 (any isotropic d_0) or on D3Q19 with d_0 = 1/3, the uu terms of Eq. (3-3)
+    // reduce to |u|^2 and (e_p . u)^2.  Per level l (k: 0 axis pairs, 1 diagonal pairs):
+    //   E_p = nA[l][k] rho + nU[l][k] |u|^2 + nk[l][p] (e_p . u)^2,   O_p = no[l][p] (e_p . u)
+    //   a0 rho + a+ f_0^eq = nc[l][0] rho + nc[l][1] |u|^2.
+    // When the momentum set is proportional to the scalar one, (abar-, abar+) = kappa (a+, a-)
+    // (LBGK tau = 1 among others), a+ and a- are folded into E_p and O_p (the scalar contribution
+    // is then E_p +- O_p) and the momentum one is +-kappa times it, nsm[l][a] = kappa c_a / rho0.
+    // Otherwise the per-level values are E_p, O_p themselves and the general combination applies.
+    T nA[2][2], nU[2][2], nk[2][kMaxPair], no[2][kMaxPair], nc[2][2], nsm[2][3];
 };
+
+// Lean NSE variants of the marching kernels (Coef::nA): 0 none, 1 streaming momentum, 2 general.
+enum : int { LEAN_NONE = 0, LEAN_STREAM = 1, LEAN_GENERAL = 2 };
 
 // Source terms of one step (Eq. (2-1) with F_j = g_j^eq(S, M_1F, 0), Eq. (SourceF)), folded on
 // the host from the central form Eq. (3layerMMFD-2) per level l (0: t, 1: t - dt):

@@ -137,6 +137,94 @@ static int coeffs_for(const mmfd_desc& d, const double* explicit_a, const double
     return MMFD_OK;
 }
 
+// Lean He-Luo form (Coef::nA): whether the folded EDF coefficients of every pair p have the shape
+//   E_p = eA_k rho + q_k |u|^2 + k_p (e_p . u)^2,   O_p = o_p (e_p . u)
+// with eA_k, q_k shared by the axis pairs (k = 0) and by the diagonal pairs (k = 1), and an equal
+// rest coefficient on every axis.  By Eq. (3-3)-(3-4) this holds with the same speed c on every
+// axis on D2Q9 for any isotropic d_0 (a diagonal pair spans both axes, its cross term fixes k_p),
+// and on D3Q19 for d_0 = 1/3 (only then does the cross term of a diagonal pair equal 2 k_p times
+// the sign of e_pa e_pb, given q_k from the third axis).  Fills the per-level lean coefficients and returns LEAN_STREAM when
+// every level's momentum set satisfies (abar-, abar+) = kappa (a+, a-) (a+ and a- then folded
+// in), LEAN_GENERAL otherwise, LEAN_NONE when the shape does not hold.
+static int nse_lean(Coef<double>& c, int lat, int dim, int levels) {
+    auto close = [](double x, double y) { return x == y || std::fabs(x - y) <= 1e-13 * (std::fabs(x) + std::fabs(y)); };
+    const int NP = lat_npair(lat);
+    double q[kMaxPair], k[kMaxPair], o[kMaxPair];
+    int cls[kMaxPair];
+    for (int p = 0; p < NP; ++p) {
+        int in[3], out[3], nin = 0, nout = 0;
+        for (int a = 0; a < dim; ++a) {
+            if (pair_e(lat, p, a) != 0) in[nin++] = a;
+            else out[nout++] = a;
+        }
+        if (nin < 1 || nin > 2) return LEAN_NONE;
+        cls[p] = nin - 1;
+        double cross = 0.0;
+        int sgn = 1;
+        if (nin == 2) {
+            const int a = in[0], b = in[1];
+            cross = c.eC[p][(a == 0 && b == 1) ? 3 : (a == 0 && b == 2) ? 4 : 5];
+            sgn = pair_e(lat, p, a) * pair_e(lat, p, b);
+        }
+        if (nout > 0) {
+            q[p] = c.eC[p][out[0]];
+            for (int i = 1; i < nout; ++i)
+                if (!close(c.eC[p][out[i]], q[p])) return LEAN_NONE;
+        } else {
+            q[p] = c.eC[p][in[0]] - 0.5 * cross * sgn;   // 2D diagonal pairs: the cross term fixes k
+        }
+        k[p] = c.eC[p][in[0]] - q[p];
+        for (int i = 1; i < nin; ++i)
+            if (!close(c.eC[p][in[i]] - q[p], k[p])) return LEAN_NONE;
+        if (nin == 2 && !close(cross, 2.0 * k[p] * sgn)) return LEAN_NONE;
+        o[p] = c.oB[p][in[0]] * pair_e(lat, p, in[0]);
+        for (int i = 1; i < nin; ++i)
+            if (!close(c.oB[p][in[i]] * pair_e(lat, p, in[i]), o[p])) return LEAN_NONE;
+    }
+    double eAk[2] = {0.0, 0.0}, qk[2] = {0.0, 0.0};
+    bool seen[2] = {false, false};
+    for (int p = 0; p < NP; ++p) {
+        const int kk = cls[p];
+        if (!seen[kk]) {
+            seen[kk] = true;
+            eAk[kk] = c.eA[p];
+            qk[kk] = q[p];
+        } else if (!close(c.eA[p], eAk[kk]) || !close(q[p], qk[kk])) {
+            return LEAN_NONE;
+        }
+    }
+    for (int a = 1; a < dim; ++a)
+        if (!close(c.rC[a], c.rC[0])) return LEAN_NONE;
+    const int nl = levels == 3 ? 2 : 1;
+    bool stream = true;
+    double kap[2] = {0.0, 0.0};
+    for (int l = 0; l < nl; ++l) {
+        const double ap = c.ap[l], am = c.am[l], bp = c.abp[l], bm = c.abm[l];
+        if (std::fabs(bm * am - bp * ap) > 1e-13 * (std::fabs(bm * am) + std::fabs(bp * ap))) {
+            stream = false;
+        } else if (ap != 0.0 || am != 0.0) {
+            kap[l] = ap != 0.0 ? bm / ap : bp / am;
+        } else if (bm != 0.0 || bp != 0.0) {
+            stream = false;   // the level moves momentum but no scalar
+        }
+    }
+    for (int l = 0; l < nl; ++l) {
+        const double sE = stream ? c.ap[l] : 1.0, sO = stream ? c.am[l] : 1.0;
+        for (int kk = 0; kk < 2; ++kk) {
+            c.nA[l][kk] = sE * eAk[kk];
+            c.nU[l][kk] = sE * qk[kk];
+        }
+        for (int p = 0; p < NP; ++p) {
+            c.nk[l][p] = sE * k[p];
+            c.no[l][p] = sO * o[p];
+        }
+        c.nc[l][0] = c.a0[l] + c.ap[l] * c.rA;
+        c.nc[l][1] = c.ap[l] * c.rC[0];
+        for (int a = 0; a < dim; ++a) c.nsm[l][a] = stream ? kap[l] * c.fmom[a] : 0.0;
+    }
+    return stream ? LEAN_STREAM : LEAN_GENERAL;
+}
+
 static int fail(std::string* msg, int code, const char* why) {
     if (msg) *msg = why;
     return code;
@@ -393,6 +481,7 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
         for (int a = 0; a < 3; ++a) c.rC[a] *= rho0;
     }
     for (int f = 0; f < 4; ++f) c.ref[f] = r.ref[f];
+    r.lean = (d.pde == PDE_NSE && !axis) ? nse_lean(c, d.lattice, dim, d.levels) : LEAN_NONE;
 
     // float copy
     {
@@ -614,6 +703,17 @@ int resolve(const mmfd_desc& d_in, Resolved& r, std::string* msg) {
                 return fail(msg, MMFD_ERR_UNSUPPORTED, "theta-scheme: the Jacobi iteration would need more than 20000 sweeps");
             r.sweeps = k;
         }
+    }
+    if (d.pde == PDE_NCDE || d.pde == PDE_NSE) {
+        // nonlinear schemes: frozen-coefficient check about the reference state -- the NCDE at
+        // phi = ref[0] (0 unless given), the NSE at rest (rho0, u = 0); see linstab.cpp
+        double st[4] = {0.0, 0.0, 0.0, 0.0};
+        st[0] = d.pde == PDE_NSE ? d.rho0 : (std::isnan(d.ref[0]) ? 0.0 : d.ref[0]);
+        const double lmax = linear_amplification(r, st, false);
+        r.max_lambda = lmax;
+        if (lmax > 1.0 + 1e-9 && !(d.flags & MMFD_FLAG_ALLOW_UNSTABLE))
+            return fail(msg, MMFD_ERR_UNSTABLE,
+                        "max |lambda| > 1 for the scheme linearised about the reference state");
     }
     return MMFD_OK;
 }

@@ -22,6 +22,7 @@ struct Resolved {
     double max_lambda;
     Coef<double> cd;
     Coef<float> cf;
+    int lean;           // LEAN_*: lean He-Luo form available to the marching kernels
     int src;            // MMFD_SRC_* (0: none)
     int nsrc;           // source fields per level (S, then M_1F components)
     double b[3], bhat[3];
@@ -45,6 +46,12 @@ int resolve(const mmfd_desc& d, Resolved& r, std::string* msg);
 
 // Eq. (X): design targets (a_0, A_10, A_11, A_21, A_22) -> (a_{-1}, a_0, a_1), (ahat_{-1}, ahat_0, ahat_1).
 int solve_three_level_targets(const double t[5], double a[3], double ah[3]);
+
+// Frozen-coefficient stability (linstab.cpp): the largest amplification-factor modulus of the
+// NCDE / NSE scheme linearised about the uniform state `state` (NCDE: phi; NSE: rho, u), over the
+// grid's wave numbers (dense: every one up to 96 per axis, else up to 32, then a sample).
+// Returns -1 for the linear PDEs.
+double linear_amplification(const Resolved& r, const double* state, bool dense);
 
 // Compulsory HBM bytes per lattice update: every stored level read once, one written.
 double bytes_per_lu(const Resolved& r);

@@ -183,8 +183,10 @@ int admit(Server* s, Req* q) {
     q->solo = nullptr;
     const bool large = (long long)q->g.nx * q->g.ny * q->g.nz >= kSoloNodes;
     if (large && q->g.nx >= (q->g.dim == 3 ? 64 : 128)) {
-        LaunchFn fn = q->g.dim == 2 ? find_march2d(q->r->lat, q->r->pde, q->r->levels, q->r->st)
-                                    : find_march3d(q->r->lat, q->r->pde, q->r->levels, q->r->st);
+        LaunchFn fn = find_march_lean(q->r->lat, q->r->levels, q->r->st, q->r->lean);
+        if (!fn)
+            fn = q->g.dim == 2 ? find_march2d(q->r->lat, q->r->pde, q->r->levels, q->r->st)
+                               : find_march3d(q->r->lat, q->r->pde, q->r->levels, q->r->st);
         bool ok = fn != nullptr;
         const int boxw = 128 + 2 * (16 / q->g.es);
         const int boxh = q->g.dim == 2 ? march2d_rows_per_stage(q->r->pde) : march3d_tile_rows(q->r->pde) + 2;

@@ -430,6 +430,15 @@ void solver_blocked_maps(Solver* s, LaunchArgs& a) {
     }
 }
 
+// Name of a marching kernel family with its lean He-Luo variant: "_nse_s" (streaming momentum),
+// "_nse_g" (general momentum), none for the general pair form.
+static const char* lean_name(const Solver* s, const char* family) {
+    static const char* const names[2][3] = {{"k_march2d", "k_march2d_nse_s", "k_march2d_nse_g"},
+                                            {"k_march3d", "k_march3d_nse_s", "k_march3d_nse_g"}};
+    const int d = std::strcmp(family, "k_march2d") == 0 ? 0 : 1;
+    return names[d][s->lean];
+}
+
 void solver_use_depth(Solver* s, int depth) {
     LaunchFn fb = nullptr;
     if (depth >= 2 && s->r.theta_on)
@@ -446,7 +455,7 @@ void solver_use_depth(Solver* s, int depth) {
         s->depth = 1;
         if (s->r.src || s->r.theta_on)
             s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d_src" : "k_march3d_src") : "k_direct_src";
-        else s->kernel_name = s->use_tma ? (s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
+        else s->kernel_name = s->use_tma ? lean_name(s, s->r.dim == 2 ? "k_march2d" : "k_march3d") : "k_direct";
     }
 }
 
@@ -464,9 +473,16 @@ int solver_pick_kernels(Solver* s) {
     // side enters as a centre-only source) and its right-hand side a plain step.
     const int srcv = s->r.theta_on ? 1 : s->r.src == 0 ? 0 : (s->r.src == MMFD_SRC_SM ? 2 : 1);
     s->fn_rhs = nullptr;
+    // the lean He-Luo NSE form where the coefficients allow it (MMFD_FORCE_KERNEL=generic keeps the
+    // general pair form, for comparisons; it computes the same update)
+    const bool want_generic = force && std::strcmp(force, "generic") == 0;
+    const int lean = (!want_generic && !srcv && !s->r.theta_on) ? s->r.lean : LEAN_NONE;
+    LaunchFn fn_lean = lean != LEAN_NONE ? find_march_lean(s->r.lat, s->r.levels, s->r.st, lean) : nullptr;
+    s->lean = fn_lean ? lean : LEAN_NONE;
     if (s->r.dim == 2 && s->g.nx >= 128 && !want_direct) {
-        s->fn = srcv ? find_march2d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
-                     : find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        s->fn = fn_lean ? fn_lean
+                : srcv  ? find_march2d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
+                        : find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
         if (s->r.theta_on) {
             s->fn_rhs = find_march2d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
             if (!s->fn_rhs) s->fn = nullptr;
@@ -486,7 +502,7 @@ int solver_pick_kernels(Solver* s) {
         }
         if (s->fn) {
             s->use_tma = true;
-            s->kernel_name = srcv ? "k_march2d_src" : "k_march2d";
+            s->kernel_name = srcv ? "k_march2d_src" : lean_name(s, "k_march2d");
             s->H = 0;  // chosen by the launcher from the kernel's occupancy
             // temporal blocking: 0 asks for the deepest blocking the storage allows (the
             // autotuner may then pick a shallower one); the x ghost columns, kept current to
@@ -513,8 +529,9 @@ int solver_pick_kernels(Solver* s) {
         }
     }
     if (s->r.dim == 3 && s->g.nx >= 128 && !want_direct) {
-        s->fn = srcv ? find_march3d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
-                     : find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
+        s->fn = fn_lean ? fn_lean
+                : srcv  ? find_march3d_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
+                        : find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
         if (s->r.theta_on) {
             s->fn_rhs = find_march3d(s->r.lat, s->r.pde, s->r.levels, s->r.st);
             if (!s->fn_rhs) s->fn = nullptr;
@@ -534,7 +551,7 @@ int solver_pick_kernels(Solver* s) {
         }
         if (s->fn) {
             s->use_tma = true;
-            s->kernel_name = srcv ? "k_march3d_src" : "k_march3d";
+            s->kernel_name = srcv ? "k_march3d_src" : lean_name(s, "k_march3d");
             s->H = 0;
             // temporal blocking (two-level LCDE): the blocked kernel streams one-row boxes of the
             // level, with rows and planes wrapped periodically, so any ny and nz will do
@@ -553,6 +570,7 @@ int solver_pick_kernels(Solver* s) {
             return MMFD_OK;
         }
     }
+    s->lean = LEAN_NONE;
     s->fn = srcv ? find_direct_src(s->r.lat, s->r.pde, s->r.levels, s->r.st, srcv)
                  : find_direct(s->r.lat, s->r.pde, s->r.levels, s->r.st);
     s->kernel_name = srcv ? "k_direct_src" : "k_direct";

@@ -36,6 +36,7 @@ struct Solver {
     int* d_flag = nullptr;                       // device error flag written by kernels
     bool fields_set = false;
     bool use_tma = false;                        // kernel family consumes tensor maps
+    int lean = 0;                                // LEAN_* variant of the marching kernel in use
     CUtensorMap tmaps[3][4];                     // per level buffer, per field
     CUtensorMap tbmaps[3];                       // 3D blocked kernel: one-row boxes of field 0 per buffer
     TmapSet launch_maps;                         // assembled per launch (inputs of this step)

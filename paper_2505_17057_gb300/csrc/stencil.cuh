@@ -155,6 +155,52 @@ struct Basis<LAT, PDE_NSE, T> {
     __device__ __forceinline__ T mom(int a) const { return u[a]; }
 };
 
+// ------------------------------------------------------------------ lean He-Luo form
+// Whether pair p is an axis pair (one nonzero component of e_p) -- class 0 of Coef::nA.
+__host__ __device__ constexpr int pair_class(int lat, int p) {
+    int n = 0;
+    for (int a = 0; a < lat_dim(lat); ++a) n += pair_e(lat, p, a) != 0 ? 1 : 0;
+    return n == 1 ? 0 : 1;
+}
+
+// e_p . u for a representative direction (unit components, at most two nonzero).
+template <int LAT, int P, typename T>
+__device__ __forceinline__ T edot(T ux, T uy, T uz) {
+    constexpr int ex = pair_e(LAT, P, 0), ey = pair_e(LAT, P, 1), ez = lat_dim(LAT) == 3 ? pair_e(LAT, P, 2) : 0;
+    auto term = [](int e, T v) { return e > 0 ? v : -v; };
+    if constexpr (ex != 0 && ey != 0) return ey > 0 ? (ex > 0 ? uy + ux : uy - ux) : term(ex, ux) - uy;
+    else if constexpr (ex != 0 && ez != 0) return ez > 0 ? (ex > 0 ? uz + ux : uz - ux) : term(ex, ux) - uz;
+    else if constexpr (ey != 0 && ez != 0) return ez > 0 ? (ey > 0 ? uz + uy : uz - uy) : term(ey, uy) - uz;
+    else if constexpr (ex != 0) return term(ex, ux);
+    else if constexpr (ey != 0) return term(ey, uy);
+    else return term(ez, uz);
+}
+
+// One plus (SIGN = +1: output x - e_p) or minus (SIGN = -1: output x + e_p) contribution of pair P
+// in the lean form (Coef::nA) from the input node's E, O.  Streaming momentum: E, O carry a+, a-
+// already, the scalar contribution is E +- O and the momentum one +-kappa times it (nsm).
+// General: sE = a+ E and mO = abar+ O (formed once per pair and node), the scalar contribution
+// a- O +- ... and the momentum abar- E +- ... of Eq. (2-4-1) as in the general pair form.
+// acc points at the output node's NF accumulators.
+template <int LAT, int LEAN, int P, int SIGN, int NF, typename T>
+__device__ __forceinline__ void lean_push(T* acc, const Coef<T>& cf, int l, T E, T O, T sE, T mO) {
+    constexpr int D = lat_dim(LAT);
+    if constexpr (LEAN == LEAN_STREAM) {
+        const T sv = SIGN > 0 ? E + O : E - O;
+        acc[0] += sv;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (pair_e(LAT, P, a) != 0) acc[1 + a] += (T(SIGN * pair_e(LAT, P, a)) * cf.nsm[l][a]) * sv;
+    } else {
+        const T sv = SIGN > 0 ? cf.am[l] * O + sE : sE - cf.am[l] * O;
+        const T mv = SIGN > 0 ? cf.abm[l] * E + mO : mO - cf.abm[l] * E;
+        acc[0] += sv;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (pair_e(LAT, P, a) != 0) acc[1 + a] += (T(pair_e(LAT, P, a)) * cf.fmom[a]) * mv;
+    }
+}
+
 // ------------------------------------------------------------------ ghost write-through
 // Write value v of node (x, y, z) to its interior slot and to every periodic ghost image
 // (x < gx also lands at x + nx, x >= nx - gx also at x - nx, with gx the ghost depth in x;

@@ -122,6 +122,8 @@ SIGNATURES = {
     "mmfd_reduce": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_double)]),
     "mmfd_error_norms": (C.c_int, [_VP, C.c_int, _VP, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mmfd_reduce_static": (C.c_int, [_VP, C.c_int, C.c_longlong, C.c_int, _VP, _VP]),
+    "mmfd_linear_stability": (C.c_int, [C.POINTER(mmfd_desc), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mmfd_check_fields": (C.c_int, [_VP, C.POINTER(C.c_double)]),
     "mmfd_get_info": (C.c_int, [_VP, C.POINTER(mmfd_info_t)]),
     "mmfd_autotune": (C.c_int, [_VP, C.c_char_p, C.POINTER(mmfd_tune_info)]),
     "mmfd_set_stream": (C.c_int, [_VP, _VP]),
@@ -267,6 +269,25 @@ def mmfd_error_norms(h: int, field: int, ref_ptr: int, where: int, dtype: int) -
 def mmfd_reduce_static(field_ptr: int, dtype: int, count: int, what: int, out_ptr: int,
                        stream: Optional[int]) -> None:
     check(lib.mmfd_reduce_static(field_ptr, dtype, int(count), what, out_ptr, stream), "mmfd_reduce_static")
+
+
+def mmfd_linear_stability(d: mmfd_desc, state: Sequence[float]):
+    """(status, max_amp): MMFD_OK or MMFD_ERR_UNSTABLE with the largest amplification modulus."""
+    st = (C.c_double * 4)(*([float(v) for v in state] + [0.0] * (4 - len(state))))
+    out = C.c_double(0.0)
+    rc = lib.mmfd_linear_stability(C.byref(d), st, C.byref(out))
+    if rc != MMFD_ERR_UNSTABLE:
+        check(rc, "mmfd_linear_stability")
+    return rc, out.value
+
+
+def mmfd_check_fields(h: int):
+    """(status, max_amp) about the current level's extreme states (MMFD_OK or MMFD_ERR_UNSTABLE)."""
+    out = C.c_double(0.0)
+    rc = lib.mmfd_check_fields(h, C.byref(out))
+    if rc != MMFD_ERR_UNSTABLE:
+        check(rc, "mmfd_check_fields")
+    return rc, out.value
 
 
 def mmfd_get_info(h: int) -> mmfd_info_t:

@@ -64,10 +64,10 @@ def solve_one(mm, kw, fields, steps, depth):
     return info, stored, out
 
 
-FULL = [("tgv2d", configs.tgv2d_4096, 4096, "k_march2d"),
+FULL = [("tgv2d", configs.tgv2d_4096, 4096, "k_march2d_nse_s"),
         ("lcde2d", configs.lcde2d_8192, 8192, "k_march2d"),
         ("cde3d", configs.cde3d_512, 512, "k_march3d"),
-        ("nse3d", configs.nse3d_512, 512, "k_march3d")]
+        ("nse3d", configs.nse3d_512, 512, "k_march3d_nse_s")]
 
 
 @pytest.mark.parametrize("name,maker,n,kernel", FULL, ids=[f[0] for f in FULL])

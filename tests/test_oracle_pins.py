@@ -482,6 +482,71 @@ def test_stability_growth_just_outside_bound():
             assert lmax <= 1 + 1e-12 and growth <= 1 + 1e-12
 
 
+def _three_level_case(kappa, shape=(16, 16)):
+    # Eq. (X) with a_0 = 0, A_10 = A_11 = -1, A_21 = 1/4, A_22 = 1/2: the printed set
+    # a = (7/8, 0, 1/8), ahat = (1/8, 0, -1/8) of Examples 1-2; isotropic diffusion kappa
+    a, ah = P.solve_three_level(0.0, -1.0, -1.0, 0.25, 0.5)
+    return P.problem_lcde("D2Q9", 3, list(shape[::-1]), 1.0, [1.0, 1.0], [[kappa, 0.0], [0.0, kappa]], [0.05, 0.03],
+                          a, ah)
+
+
+def _three_level_rmax(prob, shape=(16, 16)):
+    l1, l2, _, _ = F.three_level_roots(prob, shape)
+    lam = np.where(np.abs(l1) >= np.abs(l2), l1, l2)
+    lam[0, 0] = 0.0          # theta = 0: conserved mass, root exactly 1
+    return lam
+
+
+def test_three_level_growth_just_inside_and_outside_theorem3():
+    # Theorem 3 (Eq. (3-level)): on a 16^2 grid, bisect the diffusion number at which the largest
+    # root of lambda^2 - p_1 lambda - p_0 reaches 1, take kappa* (1 -+ 1e-3), and run the oracle's
+    # three-level scheme from an eigen-start of the fastest mode (phi^{-1} = phi^0 / lambda in that
+    # mode).  Outside: Theorem 3's inequality fails and the oracle grows as |lambda_max|^n (1e-8);
+    # inside: it holds and nothing grows.
+    shape = (16, 16)
+    lo, hi = 0.01, 1.0
+    assert np.abs(_three_level_rmax(_three_level_case(lo))).max() <= 1 and \
+        np.abs(_three_level_rmax(_three_level_case(hi))).max() > 1
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if np.abs(_three_level_rmax(_three_level_case(mid))).max() > 1:
+            hi = mid
+        else:
+            lo = mid
+    kstar = 0.5 * (lo + hi)
+    th = F.thetas(shape)
+    y, x = np.arange(shape[0])[:, None], np.arange(shape[1])[None, :]
+    for kappa, outside in [(kstar * (1 + 1e-3), True), (kstar * (1 - 1e-3), False)]:
+        prob = _three_level_case(kappa)
+        lam = _three_level_rmax(prob)
+        # a mode whose real field is a single eigenmode: +-theta distinct, or theta = -theta
+        # (components 0 or pi) with a real root
+        selfconj = np.isclose(np.abs(np.sin(th[0])) + np.abs(np.sin(th[1])), 0.0)
+        real = np.abs(lam.imag) <= 1e-12 * np.abs(lam)
+        mag = np.where(selfconj & ~real, 0.0, np.abs(lam))
+        i = np.unravel_index(np.argmax(mag), mag.shape)
+        li = lam[i] if not selfconj[i] else complex(lam[i].real, 0.0)
+        phase = th[0][i] * y + th[1][i] * x
+        phi0 = np.cos(phase)
+        phim1 = np.real(np.exp(1j * phase) / li)
+        n = 80
+        out, _ = orc.run(prob, [phi0], [phim1], nsteps=n)
+        growth = np.sqrt((out[0] ** 2).sum() / (phi0 ** 2).sum())
+        if outside:
+            assert not F.theorem3_holds(prob, shape)
+            assert abs(li) > 1 + 1e-6
+            assert abs(growth / abs(li) ** n - 1) < 1e-8, (growth, abs(li) ** n)
+        else:
+            mask = np.ones(shape, dtype=bool)
+            mask[0, 0] = False
+            p1 = F.symbol(prob, prob.a, shape)
+            p0 = F.symbol(prob, prob.ahat, shape)
+            sc = np.abs(p1 + np.conj(p1) * p0)[mask] <= (1.0 - np.abs(p0) ** 2)[mask] + 1e-12
+            assert sc.all()
+            assert abs(li) <= 1 + 1e-12 and growth <= 1 + 1e-12
+            assert abs(growth / abs(li) ** n - 1) < 1e-8
+
+
 def test_theorem3_matches_roots():
     # Theorem 3 (Schur-Cohn) agrees with the roots of lambda^2 - p_1 lambda - p_0 on random three-level
     # schemes away from the boundary.  The theta = 0 mode (conserved mass, root exactly 1) is excluded.

@@ -51,3 +51,77 @@ def test_reduce_static_matches_reduce():
                                 out.data_ptr(), stream)
     assert e.value.code == mmfd.MMFD_ERR_ARG
     s.close()
+
+
+def test_reduce_static_fp32_and_nonfinite():
+    # the FP32 load path and a non-zero non-finite count, against mmfd_reduce of an FP32 solver
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_17057_gb300 import mmfd
+
+    rng = np.random.default_rng(2028)
+    shape = (260, 1031)  # three 2^17-element blocks with a ragged tail
+    phi = 1.0 + 0.3 * rng.standard_normal(shape)
+    bad = phi.copy()
+    where = rng.choice(bad.size, 37, replace=False)
+    bad.reshape(-1)[where[:20]] = np.nan
+    bad.reshape(-1)[where[20:30]] = np.inf
+    bad.reshape(-1)[where[30:]] = -np.inf
+    d = mmfd.make_desc("LCDE", "D2Q9", 2, [shape[1], shape[0]], 1.0, [1.0, 1.0], storage="fp32",
+                       K=[[0.02, 0.0], [0.0, 0.02]], u=[0.05, 0.0], targets=[0, -1, -1, 0, 0.5], ref=[1.0])
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    s = mmfd.Solver(d)
+    try:
+        s.set_fields([phi])
+        s.step(2)
+        dev = s.fields(0, device=True, dtype=np.float32)[0]
+        for what in (mmfd.MMFD_RED_SUM, mmfd.MMFD_RED_MAXABS, mmfd.MMFD_RED_NONFINITE):
+            ref = s.reduce(what)[0]
+            for call in range(2):
+                mmfd.mmfd_reduce_static(dev.data_ptr(), mmfd.MMFD_DT_F32, dev.numel(), what, out.data_ptr(), stream)
+                torch.cuda.synchronize()
+                got = float(out.item())
+                # the solver reduces the stored FP32 offsets plus the reference in FP64; the dense
+                # copy holds the FP32-rounded values
+                scale = float(torch.abs(dev.double()).sum().item()) if what == mmfd.MMFD_RED_SUM else abs(ref)
+                assert abs(got - ref) <= 1e-7 * max(scale, 1.0), (what, call, got, ref)
+        s.set_fields([bad])
+        dev = s.fields(0, device=True, dtype=np.float32)[0]
+        ref = s.reduce(mmfd.MMFD_RED_NONFINITE)[0]
+        assert ref == 37
+        for call in range(2):
+            mmfd.mmfd_reduce_static(dev.data_ptr(), mmfd.MMFD_DT_F32, dev.numel(), mmfd.MMFD_RED_NONFINITE,
+                                    out.data_ptr(), stream)
+            torch.cuda.synchronize()
+            assert float(out.item()) == ref, (call, out.item())
+    finally:
+        s.close()
+
+
+def test_reduce_static_rejects_host_pointers():
+    # host memory (pageable or page-locked) is refused before anything is launched: out keeps
+    # its sentinel value
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_17057_gb300 import mmfd
+
+    stream = torch.cuda.current_stream().cuda_stream
+    out = torch.full((1,), -7.0, dtype=torch.float64, device="cuda")
+    dev = torch.ones(1000, dtype=torch.float64, device="cuda")
+    host = np.ones(1000)
+    pinned = torch.ones(1000, dtype=torch.float64).pin_memory()
+    host_out = np.zeros(1)
+    cases = [(host.ctypes.data, out.data_ptr()), (pinned.data_ptr(), out.data_ptr()),
+             (dev.data_ptr(), host_out.ctypes.data)]
+    for field, dst in cases:
+        with pytest.raises(mmfd.MMFDError) as e:
+            mmfd.mmfd_reduce_static(field, mmfd.MMFD_DT_F64, 1000, mmfd.MMFD_RED_SUM, dst, stream)
+        assert e.value.code == mmfd.MMFD_ERR_ARG
+    torch.cuda.synchronize()
+    assert float(out.item()) == -7.0 and host_out[0] == 0.0
+    mmfd.mmfd_reduce_static(dev.data_ptr(), mmfd.MMFD_DT_F64, 1000, mmfd.MMFD_RED_SUM, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert float(out.item()) == 1000.0
