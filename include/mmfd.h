@@ -110,9 +110,9 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *  temporal_depth        time steps fused per kernel launch (temporal blocking): 1 = none;
  *                        T >= 2 asks for T; 0 asks for the deepest available.  Blocking is
  *                        available for 2D two-level LCDE / NCDE grids with nx >= 128 and
- *                        ny >= 2T, and for 3D two-level LCDE grids (D3Q7 / D3Q19) with
- *                        nx >= 128, up to T = 2 (FP64), 4 (FP32), 5 (BF16) -- the x ghost
- *                        columns of the padded layout hold that many levels.  Larger requests
+ *                        ny >= 2T, up to T = 2 (FP64), 4 (FP32), 5 (BF16) -- the x ghost
+ *                        columns of the padded layout hold that many levels.  3D grids run
+ *                        unblocked.  Larger requests
  *                        are clamped, other configurations run unblocked; mmfd_get_info reports
  *                        the depth in use.  mmfd_step(n) runs n / T blocked launches and the
  *                        remaining n % T steps unblocked.  With BF16 storage a blocked solver
@@ -279,6 +279,18 @@ int mmfd_reduce(mmfd_solver* s, int what, double* out);
  * (the paper's GRE, Sec. IV), out[1] = max |v - ref|, out[2] = max |ref|.  FP64,
  * synchronous. */
 int mmfd_error_norms(mmfd_solver* s, int field, const void* ref, int where, int dtype, double* out);
+
+/* Rows (2D: y) or planes (3D: z) [r0, r0 + count) of one level, to or from dense buffers: nf
+ * pointers, each to count * nx (2D) or count * nx * ny (3D) values, x fastest, of element type
+ * dtype, on the host or the device.  For a slab decomposition of one solve over several solvers
+ * (one per GPU): each slab's solver steps its rows plus halo rows as a periodic grid and swaps the
+ * halo rows with its neighbours between steps (no counterpart in the paper; paper_2505_17057_gb300
+ * /slab.py has the bookkeeping).  mmfd_set_rows keeps the rows' periodic ghost images current and,
+ * unlike mmfd_set_fields, leaves level t - dt of a three-level solver alone.  Asynchronous on the
+ * solver's stream for device buffers; synchronous for host buffers. */
+int mmfd_set_rows(mmfd_solver* s, int level, long long r0, long long count, const void* const* fields, int where,
+                  int dtype);
+int mmfd_get_rows(mmfd_solver* s, int level, long long r0, long long count, void* const* out, int where, int dtype);
 
 /* Frozen-coefficient stability of the nonlinear schemes (the paper analyses the linear CDE only,
  * Sec. III.D, Theorems 1-3; the NCDE and NSE are checked here linearised about a uniform state).

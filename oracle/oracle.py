@@ -371,6 +371,26 @@ def trt_run(prob: Problem, level_n, s_minus: float, nsteps: int) -> List[np.ndar
     return _unpack(buf)
 
 
+class LevelStepper:
+    """Pack one level once, then advance it in place by whole oracle steps (used to time full
+    steps of a large workload without unpacking between them)."""
+
+    def __init__(self, prob: Problem, level_n, level_nm1=None, form: str = "mmfd"):
+        self.prob = prob
+        self.p = prob.to_c()
+        self.bn = _pack(level_n, prob.nf, prob.shape)
+        self.bm = _pack(level_nm1, prob.nf, prob.shape) if level_nm1 is not None else np.zeros_like(self.bn)
+        self.form = FORMS[form]
+
+    def step(self, nsteps: int = 1) -> None:
+        rc = lib().or_run(C.byref(self.p), self.form, int(nsteps), _dp(self.bn), _dp(self.bm))
+        if rc != 0:
+            raise ValueError("oracle rejected the problem")
+
+    def level(self):
+        return _unpack(self.bn)
+
+
 class NodeSampler:
     """Pack one level once, then evaluate the oracle step on contiguous node ranges.
 

@@ -116,6 +116,55 @@ def three_d(kind="cde3d", n=512, steps=1000):
     return res
 
 
+def _run_fp32_storage_emulated(desc_kw, fields, steps, refs):
+    """FP64 arithmetic with FP32 storage: the FP64 solver's levels are rounded to what FP32 storage
+    would hold (the offset from refs[f] rounded to FP32, plus refs[f]) -- the initial fields and
+    the new level after every step, on the device.  Isolates the storage rounding from the FP32
+    arithmetic.  (Setting level 0 of a three-level solver also sets level 1, so level t - dt is
+    put back after each step.)"""
+    import torch
+
+    def rnd(ts):
+        return [((f - r).to(torch.float32).to(torch.float64) + r).contiguous() for f, r in zip(ts, refs)]
+
+    three = desc_kw["levels"] == 3
+    s = mmfd.Solver(mmfd.make_desc(**{**desc_kw, "storage": "fp64"}))
+    try:
+        init = rnd([torch.as_tensor(np.ascontiguousarray(f, dtype=np.float64), device="cuda") for f in fields])
+        mmfd.mmfd_set_fields(s.h, 0, [t.data_ptr() for t in init], mmfd.MMFD_DEVICE, mmfd.MMFD_DT_F64)
+        for _ in range(steps):
+            cur = s.fields(0, device=True) if three else None
+            s.step(1)
+            new = rnd(s.fields(0, device=True))
+            mmfd.mmfd_set_fields(s.h, 0, [t.data_ptr() for t in new], mmfd.MMFD_DEVICE, mmfd.MMFD_DT_F64)
+            if three:
+                mmfd.mmfd_set_fields(s.h, 1, [t.data_ptr() for t in cur], mmfd.MMFD_DEVICE, mmfd.MMFD_DT_F64)
+        return s.fields(0)
+    finally:
+        s.close()
+
+
+def attribution(case: str, n: int, steps: int):
+    """Where the FP32 error comes from: FP32 storage with FP32 arithmetic (the FP32 solver) and
+    FP32 storage with FP64 arithmetic (the FP64 solver rounding its new level to FP32 storage after
+    every step), both against the FP64 run, max error relative to the field's max.  For the NCDE
+    three-level scheme the level t - dt is the previous (already rounded) level."""
+    if case == "ncde2d":
+        desc, fields, _ = configs.ncde2d_1024(n=n, storage="fp64")
+        refs = [0.0]                      # FP32 NCDE levels hold values
+    else:
+        desc, fields, _ = configs.tgv2d_4096(n=n, storage="fp64")
+        refs = [1.0, 0.0, 0.0]            # FP32 NSE levels hold offsets from rho0
+    ref, _ = _run(desc, fields, steps, "fp64")
+    full, _ = _run(desc, fields, steps, "fp32")
+    stor = _run_fp32_storage_emulated(desc, fields, steps, refs)
+    sel = slice(1, None) if case == "tgv2d" else slice(0, None)   # the NSE: velocity, as the accuracy figures
+    return {"case": f"{case}_{n}", "steps": steps, "reference": "FP64 GPU run",
+            "fields": "velocity" if case == "tgv2d" else "phi",
+            "fp32_storage_fp32_arith": _maxrel(full[sel], ref[sel]),
+            "fp32_storage_fp64_arith": _maxrel(stor[sel], ref[sel])}
+
+
 def theta_cn(ns=(64, 128, 256), kx=0.3, ky=0.2, t_end=1.0):
     """Crank-Nicolson (the theta-scheme of Eq. (GCN) with theta = 1/2) on D2Q9 with u = 0 and
     K = diag(kx, ky) on [0, 2 pi)^2, dt proportional to dx (n/4 steps to t_end, up to ~50x the
@@ -200,6 +249,8 @@ def main():
         "nse3d": lambda: three_d("nse3d", 128 if q else 512, 200 if q else 1000),
         "theta": lambda: theta_cn((64, 128) if q else (64, 128, 256)),
         "example3": lambda: example3(),
+        "attr_ncde2d": lambda: attribution("ncde2d", 256 if q else 1024, 1000 if q else 10000),
+        "attr_tgv2d": lambda: attribution("tgv2d", 512 if q else 4096, 1000 if q else 5000),
     }
     import torch
     torch.cuda.init()

@@ -14,10 +14,12 @@ namespace {
 constexpr int kRedBlocks = 608;   // 4 x 152 SMs
 constexpr int kRedThreads = 256;
 
+// Value of a stored element: the reference plus the stored offset, formed in FP64 so that an
+// FP32 / BF16 offset comes back exactly (FP64 levels hold values, ref 0).
 template <int ST>
 __device__ __forceinline__ double load_st(const void* base, long long i, double ref) {
     using Tr = Storage<ST>;
-    return (double)Tr::load(static_cast<const typename Tr::S*>(base) + i, (typename Tr::T)ref);
+    return ref + (double)Tr::raw(static_cast<const typename Tr::S*>(base) + i);
 }
 
 // Four consecutive values of a dense FP64 / FP32 source row, 16-byte aligned.
@@ -39,17 +41,16 @@ __device__ __forceinline__ void ld4_st(const void* base, long long i, double ref
     using S = typename Tr::S;
     const S* p = static_cast<const S*>(base) + i;
     if constexpr (ST == ST_F32) {
-        // FP32 levels hold v - ref: the value is ref + stored, in FP32 as Storage<ST_F32>::load
+        // FP32 levels hold v - ref: the value is ref + stored, formed in FP64 (as load_st)
         const float4 a = *reinterpret_cast<const float4*>(p);
-        const float r = (float)ref;
-        v[0] = (double)(r + a.x); v[1] = (double)(r + a.y); v[2] = (double)(r + a.z); v[3] = (double)(r + a.w);
+        v[0] = ref + (double)a.x; v[1] = ref + (double)a.y; v[2] = ref + (double)a.z; v[3] = ref + (double)a.w;
     } else if constexpr (ST == ST_F64) {
         const double2 a = *reinterpret_cast<const double2*>(p);
         const double2 b = *reinterpret_cast<const double2*>(p + 2);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (double)Tr::load(p + k, (typename Tr::T)ref);
+        for (int k = 0; k < 4; ++k) v[k] = ref + (double)Tr::raw(p + k);
     }
 }
 
@@ -57,24 +58,24 @@ __device__ __forceinline__ void ld4_st(const void* base, long long i, double ref
 // 16-byte aligned source); the source may be device memory or page-locked host memory read
 // directly over the host link.
 template <int ST>
-__global__ void k_pack4(Geom g, const void* __restrict__ src, int src_dtype, void* __restrict__ dst, double ref) {
+__global__ void k_pack4(Geom g, const void* __restrict__ src, int src_dtype, void* __restrict__ dst, double ref,
+                        long long r_lo, long long r_hi) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
     S* d = static_cast<S*>(dst);
-    const long long rows = (long long)g.ny * g.nz;
     const int nq = g.nx >> 2;
-    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+    for (long long r = r_lo + blockIdx.y; r < r_hi; r += gridDim.y) {
         const int y = (int)(r % g.ny);
         const int z = (int)(r / g.ny);
         const bool yedge = y == 0 || y == g.ny - 1 || (g.dim == 3 && (z == 0 || z == g.nz - 1));
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
             const int x = q << 2;
             double v[4];
-            ld4_src(src, src_dtype, r * g.nx + x, v);
+            ld4_src(src, src_dtype, (r - r_lo) * g.nx + x, v);
             S sv[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) sv[k] = Tr::pack((T)v[k], (T)ref, 0u);
+            for (int k = 0; k < 4; ++k) sv[k] = Tr::pack_raw((T)(v[k] - ref), 0u);   // offset formed in FP64
             const bool edge = yedge || x < g.gx || x + 3 >= g.nx - g.gx;
             if (!edge) {
                 S* p = d + g.at(x, y, z);
@@ -98,20 +99,20 @@ __global__ void k_pack4(Geom g, const void* __restrict__ src, int src_dtype, voi
 // Layout kernels walk rows (blockIdx.y over y + z ny, grid-stride) and columns (threads), so no
 // per-element division is needed; only edge nodes take the ghost-image path.
 template <int ST>
-__global__ void k_pack(Geom g, const void* __restrict__ src, int src_dtype, void* __restrict__ dst, double ref) {
+__global__ void k_pack(Geom g, const void* __restrict__ src, int src_dtype, void* __restrict__ dst, double ref,
+                       long long r_lo, long long r_hi) {
     using Tr = Storage<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
     S* d = static_cast<S*>(dst);
-    const long long rows = (long long)g.ny * g.nz;
-    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+    for (long long r = r_lo + blockIdx.y; r < r_hi; r += gridDim.y) {
         const int y = (int)(r % g.ny);
         const int z = (int)(r / g.ny);
-        const long long base = r * g.nx;
+        const long long base = (r - r_lo) * g.nx;
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
             const long long i = base + x;
             const double v = src_dtype == 0 ? static_cast<const double*>(src)[i] : (double)static_cast<const float*>(src)[i];
-            const S sv = Tr::pack((T)v, (T)ref, 0u);
+            const S sv = Tr::pack_raw((T)(v - ref), 0u);   // offset formed in FP64, rounded once
             const bool edge = x < g.gx || x >= g.nx - g.gx || y == 0 || y == g.ny - 1 ||
                               (g.dim == 3 && (z == 0 || z == g.nz - 1));
             if (!edge) {
@@ -126,12 +127,12 @@ __global__ void k_pack(Geom g, const void* __restrict__ src, int src_dtype, void
 }
 
 template <int ST>
-__global__ void k_unpack(Geom g, const void* __restrict__ src, double ref, void* __restrict__ dst, int dst_dtype) {
-    const long long rows = (long long)g.ny * g.nz;
-    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+__global__ void k_unpack(Geom g, const void* __restrict__ src, double ref, void* __restrict__ dst, int dst_dtype,
+                         long long r_lo, long long r_hi) {
+    for (long long r = r_lo + blockIdx.y; r < r_hi; r += gridDim.y) {
         const int y = (int)(r % g.ny);
         const int z = (int)(r / g.ny);
-        const long long base = r * g.nx;
+        const long long base = (r - r_lo) * g.nx;
         const long long sbase = g.at(0, y, z);
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
             const double v = load_st<ST>(src, sbase + x, ref);
@@ -139,6 +140,58 @@ __global__ void k_unpack(Geom g, const void* __restrict__ src, double ref, void*
                 static_cast<double*>(dst)[base + x] = v;
             else
                 static_cast<float*>(dst)[base + x] = (float)v;
+        }
+    }
+}
+
+// Rows [r_lo, r_hi) (r = y + z ny) of every field of a level to / from dense buffers in one launch
+// (blockIdx.z = field): the halo-row exchange of a slab decomposition moves a few rows per step,
+// so the launch count matters more than the bandwidth.
+struct RowBufs {
+    const void* src[4];
+    void* dst[4];
+    double ref[4];
+};
+
+template <int ST>
+__global__ void k_rows_pack(Geom g, RowBufs b, int src_dtype, void* __restrict__ level, long long r_lo, long long r_hi) {
+    using Tr = Storage<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const int f = blockIdx.z;
+    S* d = static_cast<S*>(level) + (size_t)f * g.fs;
+    const double ref = b.ref[f];
+    for (long long r = r_lo + blockIdx.y; r < r_hi; r += gridDim.y) {
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const long long base = (r - r_lo) * g.nx;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
+            const long long i = base + x;
+            const double v = src_dtype == 0 ? static_cast<const double*>(b.src[f])[i] : (double)static_cast<const float*>(b.src[f])[i];
+            const S sv = Tr::pack_raw((T)(v - ref), 0u);
+            if (g.dim == 3) store_with_ghosts<3>(d, g, x, y, z, sv);
+            else store_with_ghosts<2>(d, g, x, y, z, sv);
+        }
+    }
+}
+
+template <int ST>
+__global__ void k_rows_unpack(Geom g, RowBufs b, int dst_dtype, const void* __restrict__ level, long long r_lo,
+                              long long r_hi) {
+    const int f = blockIdx.z;
+    const char* src = static_cast<const char*>(level) + (size_t)f * g.fs * g.es;
+    const double ref = b.ref[f];
+    for (long long r = r_lo + blockIdx.y; r < r_hi; r += gridDim.y) {
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const long long base = (r - r_lo) * g.nx;
+        const long long sbase = g.at(0, y, z);
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
+            const double v = load_st<ST>(src, sbase + x, ref);
+            if (dst_dtype == 0)
+                static_cast<double*>(b.dst[f])[base + x] = v;
+            else
+                static_cast<float*>(b.dst[f])[base + x] = (float)v;
         }
     }
 }
@@ -299,29 +352,60 @@ cudaError_t launch_ring_copy(const Geom& g, const void* src_level, void* dst_lev
 }
 
 cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, void* dst_level, int field,
-                        double ref, cudaStream_t s) {
-    const dim3 blocks = grid_rows(g);
+                        double ref, cudaStream_t s, long long r_lo, long long r_hi) {
+    if (r_hi < 0) r_hi = (long long)g.ny * g.nz;
+    if (r_hi <= r_lo) return cudaSuccess;
+    dim3 blocks = grid_rows(g);
+    if ((long long)blocks.y > r_hi - r_lo) blocks.y = (unsigned)(r_hi - r_lo);
     char* dst = static_cast<char*>(dst_level) + (size_t)field * g.fs * g.es;
     if ((g.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && g.nx >= 8) {
         const dim3 b4((unsigned)((g.nx / 4 + 255) / 256 < 64 ? (g.nx / 4 + 255) / 256 : 64), blocks.y, 1);
-        if (st == ST_F64) k_pack4<ST_F64><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref);
-        else if (st == ST_F32) k_pack4<ST_F32><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref);
-        else k_pack4<ST_BF16><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref);
+        if (st == ST_F64) k_pack4<ST_F64><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref, r_lo, r_hi);
+        else if (st == ST_F32) k_pack4<ST_F32><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref, r_lo, r_hi);
+        else k_pack4<ST_BF16><<<b4, 256, 0, s>>>(g, src, src_dtype, dst, ref, r_lo, r_hi);
         return cudaGetLastError();
     }
-    if (st == ST_F64) k_pack<ST_F64><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
-    else if (st == ST_F32) k_pack<ST_F32><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
-    else k_pack<ST_BF16><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref);
+    if (st == ST_F64) k_pack<ST_F64><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref, r_lo, r_hi);
+    else if (st == ST_F32) k_pack<ST_F32><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref, r_lo, r_hi);
+    else k_pack<ST_BF16><<<blocks, 256, 0, s>>>(g, src, src_dtype, dst, ref, r_lo, r_hi);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const Geom& g, int st, const void* src_level, int field, double ref, void* dst,
-                          int dst_dtype, cudaStream_t s) {
-    const dim3 blocks = grid_rows(g);
+                          int dst_dtype, cudaStream_t s, long long r_lo, long long r_hi) {
+    if (r_hi < 0) r_hi = (long long)g.ny * g.nz;
+    if (r_hi <= r_lo) return cudaSuccess;
+    dim3 blocks = grid_rows(g);
+    if ((long long)blocks.y > r_hi - r_lo) blocks.y = (unsigned)(r_hi - r_lo);
     const char* src = static_cast<const char*>(src_level) + (size_t)field * g.fs * g.es;
-    if (st == ST_F64) k_unpack<ST_F64><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype);
-    else if (st == ST_F32) k_unpack<ST_F32><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype);
-    else k_unpack<ST_BF16><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype);
+    if (st == ST_F64) k_unpack<ST_F64><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype, r_lo, r_hi);
+    else if (st == ST_F32) k_unpack<ST_F32><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype, r_lo, r_hi);
+    else k_unpack<ST_BF16><<<blocks, 256, 0, s>>>(g, src, ref, dst, dst_dtype, r_lo, r_hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows(const Geom& g, int st, bool pack, const void* const* bufs, int nf, int dtype, void* level,
+                        const double* refs, long long r_lo, long long r_hi, cudaStream_t s) {
+    if (nf < 1 || nf > 4) return cudaErrorInvalidValue;
+    if (r_hi <= r_lo) return cudaSuccess;
+    RowBufs b{};
+    for (int f = 0; f < nf; ++f) {
+        if (pack) b.src[f] = bufs[f];
+        else b.dst[f] = const_cast<void*>(bufs[f]);
+        b.ref[f] = refs[f];
+    }
+    const long long rows = r_hi - r_lo;
+    const dim3 blocks((unsigned)((g.nx + 255) / 256 < 64 ? (g.nx + 255) / 256 : 64),
+                      (unsigned)(rows < 65535 ? rows : 65535), (unsigned)nf);
+    if (pack) {
+        if (st == ST_F64) k_rows_pack<ST_F64><<<blocks, 256, 0, s>>>(g, b, dtype, level, r_lo, r_hi);
+        else if (st == ST_F32) k_rows_pack<ST_F32><<<blocks, 256, 0, s>>>(g, b, dtype, level, r_lo, r_hi);
+        else k_rows_pack<ST_BF16><<<blocks, 256, 0, s>>>(g, b, dtype, level, r_lo, r_hi);
+    } else {
+        if (st == ST_F64) k_rows_unpack<ST_F64><<<blocks, 256, 0, s>>>(g, b, dtype, level, r_lo, r_hi);
+        else if (st == ST_F32) k_rows_unpack<ST_F32><<<blocks, 256, 0, s>>>(g, b, dtype, level, r_lo, r_hi);
+        else k_rows_unpack<ST_BF16><<<blocks, 256, 0, s>>>(g, b, dtype, level, r_lo, r_hi);
+    }
     return cudaGetLastError();
 }
 

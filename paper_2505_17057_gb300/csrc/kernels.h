@@ -55,9 +55,6 @@ int march2d_tb_max_depth(int st);
 // (FP32 / FP64 levels): the coefficient block is the sweep's stencil, src[0] the right-hand
 // side and src_coef's W0[0] its weight.
 LaunchFn find_march2d_tb_jacobi(int lat, int st, int depth);
-// Temporally blocked 3D kernel (two-level LCDE on D3Q7 / D3Q19; nullptr elsewhere): depths as in
-// 2D.  It reads the level through tensor maps of one-row boxes ((128 + 2 x 16 B) x 1 x 1).
-LaunchFn find_march3d_tb(int lat, int pde, int levels, int st, int depth);
 // The same with source terms in the store epilogue (src as for find_direct_src; LCDE / NCDE).
 LaunchFn find_march3d_src(int lat, int pde, int levels, int st, int src);
 // Rows of the x-y tile a 3D march CTA stages per plane (the TMA box is 128+halo x rows+2 x 1).
@@ -72,10 +69,16 @@ LaunchFn find_march_lean(int lat, int levels, int st, int lean);
 int encode_field_map(CUtensorMap* m, void* field_base, int st, const Geom& g, int boxw, int boxh, int boxd);
 
 // Utility kernels (k_util.cu).
+// Rows r (r = y + z ny) in [r_lo, r_hi) only (r_hi < 0: every row); the dense buffer holds those
+// rows, x fastest.
 cudaError_t launch_pack(const Geom& g, int st, const void* src, int src_dtype, void* dst_level, int field,
-                        double ref, cudaStream_t s);
+                        double ref, cudaStream_t s, long long r_lo = 0, long long r_hi = -1);
 cudaError_t launch_unpack(const Geom& g, int st, const void* src_level, int field, double ref, void* dst,
-                          int dst_dtype, cudaStream_t s);
+                          int dst_dtype, cudaStream_t s, long long r_lo = 0, long long r_hi = -1);
+// Rows [r_lo, r_hi) of all nf fields of a level to (pack) or from (unpack) nf dense buffers of
+// element type dtype (MMFD_DT_*), one launch; refs are the fields' storage references.
+cudaError_t launch_rows(const Geom& g, int st, bool pack, const void* const* bufs, int nf, int dtype, void* level,
+                        const double* refs, long long r_lo, long long r_hi, cudaStream_t s);
 // Copy the boundary ring (x = 0 / nx - 1, y = 0 / ny - 1, z = 0 / nz - 1 in 3D) of every field
 // from one level buffer to another of the same layout and storage (Dirichlet boundaries).
 cudaError_t launch_ring_copy(const Geom& g, const void* src_level, void* dst_level, cudaStream_t s);

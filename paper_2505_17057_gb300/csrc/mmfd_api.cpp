@@ -273,6 +273,21 @@ int mmfd_reduce(mmfd_solver* h, int what, double* outv) {
     return solver_reduce(s, what, outv);
 }
 
+int mmfd_set_rows(mmfd_solver* h, int level, long long r0, long long count, const void* const* fields, int where,
+                  int dtype) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !fields) return set_error(MMFD_ERR_ARG, "null argument");
+    return solver_set_rows(s, level, r0, count, fields, where, dtype);
+}
+
+int mmfd_get_rows(mmfd_solver* h, int level, long long r0, long long count, void* const* out, int where, int dtype) {
+    Solver* s = reinterpret_cast<Solver*>(h);
+    if (!s || !out) return set_error(MMFD_ERR_ARG, "null argument");
+    int frc = solver_check_flag(s);
+    if (frc != MMFD_OK) return frc;
+    return solver_get_rows(s, level, r0, count, out, where, dtype);
+}
+
 int mmfd_check_fields(mmfd_solver* h, double* max_amp) {
     Solver* s = reinterpret_cast<Solver*>(h);
     if (!s || !max_amp) return set_error(MMFD_ERR_ARG, "null argument");

@@ -10,8 +10,10 @@ namespace {
 
 long long nodes(const Solver* s) { return (long long)s->g.nx * s->g.ny * s->g.nz; }
 
-int ensure_stage(Solver* s) {
-    const size_t need = (size_t)nodes(s) * sizeof(double);
+// The dense staging buffer for host transfers: one FP64 field, or `at_least` bytes if more.
+int ensure_stage(Solver* s, size_t at_least = 0) {
+    size_t need = (size_t)nodes(s) * sizeof(double);
+    if (at_least > need) need = at_least;
     if (s->stage && s->stage_bytes >= need) return MMFD_OK;
     if (s->stage) {
         dev_free(s, s->stage);
@@ -316,7 +318,6 @@ int solver_step(Solver* s, long long nsteps) {
         solver_launch_args(s, a);
         if (blocked) {
             // the blocked kernel (two-level solvers) writes level t + depth dt into next()
-            solver_blocked_maps(s, a);
             a.ex.step = s->steps_done + s->depth;
             cudaError_t e = s->fn_block(a);
             if (e != cudaSuccess) return cuda_fail(e, "blocked step kernel");
@@ -366,6 +367,80 @@ int solver_get_fields(Solver* s, int level, void* const* out, int where, int dty
             e = cudaStreamSynchronize(s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
         }
+    }
+    return MMFD_OK;
+}
+
+// Rows [r0, r0 + count) of the slab axis (y in 2D, z in 3D) <-> dense buffers: flat row range
+// [r0, r0 + count) * (1 or ny) of the pack / unpack kernels.
+static int rows_range(const Solver* s, long long r0, long long count, long long* lo, long long* hi) {
+    const long long n = s->g.dim == 3 ? s->g.nz : s->g.ny;
+    if (r0 < 0 || count < 1 || r0 + count > n) return set_error(MMFD_ERR_ARG, "row range outside the grid");
+    const long long per = s->g.dim == 3 ? s->g.ny : 1;
+    *lo = r0 * per;
+    *hi = (r0 + count) * per;
+    return MMFD_OK;
+}
+
+int solver_set_rows(Solver* s, int level, long long r0, long long count, const void* const* fields, int where,
+                    int dtype) {
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    if (where != MMFD_HOST && where != MMFD_DEVICE) return set_error(MMFD_ERR_ARG, "where must be HOST or DEVICE");
+    int idx;
+    int rc = level_index(s, level, &idx);
+    if (rc != MMFD_OK) return rc;
+    long long lo, hi;
+    if ((rc = rows_range(s, r0, count, &lo, &hi)) != MMFD_OK) return rc;
+    for (int f = 0; f < s->g.nf; ++f)
+        if (!fields[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
+    const size_t bytes = (size_t)(hi - lo) * s->g.nx * (dtype == MMFD_DT_F64 ? 8 : 4);
+    const void* src[4] = {fields[0], nullptr, nullptr, nullptr};
+    for (int f = 1; f < s->g.nf; ++f) src[f] = fields[f];
+    if (where == MMFD_HOST) {
+        // staged field after field in the staging buffer
+        if ((rc = ensure_stage(s, bytes * s->g.nf)) != MMFD_OK) return rc;
+        for (int f = 0; f < s->g.nf; ++f) {
+            char* dst = static_cast<char*>(s->stage) + f * bytes;
+            cudaError_t e = cudaMemcpyAsync(dst, fields[f], bytes, cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+            src[f] = dst;
+        }
+    }
+    cudaError_t e = launch_rows(s->g, s->r.st, true, src, s->g.nf, dtype, s->lev[idx], s->r.ref, lo, hi, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "row pack kernel");
+    if (where == MMFD_HOST) {
+        e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return MMFD_OK;
+}
+
+int solver_get_rows(Solver* s, int level, long long r0, long long count, void* const* out, int where, int dtype) {
+    if (dtype != MMFD_DT_F64 && dtype != MMFD_DT_F32) return set_error(MMFD_ERR_ARG, "dtype must be F64 or F32");
+    if (where != MMFD_HOST && where != MMFD_DEVICE) return set_error(MMFD_ERR_ARG, "where must be HOST or DEVICE");
+    int idx;
+    int rc = level_index(s, level, &idx);
+    if (rc != MMFD_OK) return rc;
+    long long lo, hi;
+    if ((rc = rows_range(s, r0, count, &lo, &hi)) != MMFD_OK) return rc;
+    for (int f = 0; f < s->g.nf; ++f)
+        if (!out[f]) return set_error(MMFD_ERR_ARG, "null field pointer");
+    const size_t bytes = (size_t)(hi - lo) * s->g.nx * (dtype == MMFD_DT_F64 ? 8 : 4);
+    const void* dst[4] = {out[0], nullptr, nullptr, nullptr};
+    for (int f = 1; f < s->g.nf; ++f) dst[f] = out[f];
+    if (where == MMFD_HOST) {
+        if ((rc = ensure_stage(s, bytes * s->g.nf)) != MMFD_OK) return rc;
+        for (int f = 0; f < s->g.nf; ++f) dst[f] = static_cast<char*>(s->stage) + f * bytes;
+    }
+    cudaError_t e = launch_rows(s->g, s->r.st, false, dst, s->g.nf, dtype, s->lev[idx], s->r.ref, lo, hi, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "row unpack kernel");
+    if (where == MMFD_HOST) {
+        for (int f = 0; f < s->g.nf; ++f) {
+            e = cudaMemcpyAsync(out[f], dst[f], bytes, cudaMemcpyDeviceToHost, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+        }
+        e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     }
     return MMFD_OK;
 }
@@ -423,13 +498,6 @@ int solver_error_norms(Solver* s, int field, const void* ref, int where, int dty
     return MMFD_OK;
 }
 
-void solver_blocked_maps(Solver* s, LaunchArgs& a) {
-    if (s->r.dim == 3) {
-        s->launch_maps.m[0] = s->tbmaps[s->cur];
-        a.maps = &s->launch_maps;
-    }
-}
-
 // Name of a marching kernel family with its lean He-Luo variant: "_nse_s" (streaming momentum),
 // "_nse_g" (general momentum), none for the general pair form.
 static const char* lean_name(const Solver* s, const char* family) {
@@ -444,12 +512,11 @@ void solver_use_depth(Solver* s, int depth) {
     if (depth >= 2 && s->r.theta_on)
         fb = s->r.dim == 2 ? find_march2d_tb_jacobi(s->r.lat, s->r.st, depth) : nullptr;
     else if (depth >= 2)
-        fb = s->r.dim == 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth)
-                           : find_march3d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth);
+        fb = s->r.dim == 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth) : nullptr;
     if (fb) {
         s->fn_block = fb;
         s->depth = depth;
-        s->kernel_name = s->r.dim == 2 ? "k_march2d_tb" : "k_march3d_tb";
+        s->kernel_name = "k_march2d_tb";
     } else {
         s->fn_block = nullptr;
         s->depth = 1;
@@ -553,20 +620,8 @@ int solver_pick_kernels(Solver* s) {
             s->use_tma = true;
             s->kernel_name = srcv ? "k_march3d_src" : lean_name(s, "k_march3d");
             s->H = 0;
-            // temporal blocking (two-level LCDE): the blocked kernel streams one-row boxes of the
-            // level, with rows and planes wrapped periodically, so any ny and nz will do
-            if (!srcv && !s->r.dirichlet && s->desc.temporal_depth != 1 &&
-                find_march3d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
-                bool ok = true;
-                for (int b = 0; b < s->nlev && ok; ++b)
-                    ok = encode_field_map(&s->tbmaps[b], s->lev[b], s->r.st, s->g, 128 + 2 * (16 / s->g.es), 1, 1) == 0;
-                if (ok) {
-                    s->max_depth = march2d_tb_max_depth(s->r.st);
-                    int want = s->desc.temporal_depth == 0 ? s->max_depth : s->desc.temporal_depth;
-                    if (want > s->max_depth) want = s->max_depth;
-                    solver_use_depth(s, want);
-                }
-            }
+            // 3D solvers run unblocked: a temporally blocked 3D LCDE kernel (shared-memory level
+            // planes, T = 2..5) was slower than this one at every depth and has been removed
             return MMFD_OK;
         }
     }

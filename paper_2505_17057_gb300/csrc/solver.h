@@ -38,7 +38,6 @@ struct Solver {
     bool use_tma = false;                        // kernel family consumes tensor maps
     int lean = 0;                                // LEAN_* variant of the marching kernel in use
     CUtensorMap tmaps[3][4];                     // per level buffer, per field
-    CUtensorMap tbmaps[3];                       // 3D blocked kernel: one-row boxes of field 0 per buffer
     TmapSet launch_maps;                         // assembled per launch (inputs of this step)
     int H = 0;                                   // rows / planes per CTA
     void* srcbuf[2] = {nullptr, nullptr};        // source levels (compute type, ghosted layout)
@@ -67,6 +66,9 @@ int solver_set_source(Solver* s, int level, const void* const* fields, int where
 int solver_set_boundary(Solver* s, const void* const* fields, int where, int dtype);
 int solver_step(Solver* s, long long nsteps);
 int solver_get_fields(Solver* s, int level, void* const* out, int where, int dtype);
+int solver_set_rows(Solver* s, int level, long long r0, long long count, const void* const* fields, int where,
+                    int dtype);
+int solver_get_rows(Solver* s, int level, long long r0, long long count, void* const* out, int where, int dtype);
 int solver_reduce(Solver* s, int what, double* out);
 int solver_error_norms(Solver* s, int field, const void* ref, int where, int dtype, double* out);
 // Pick the kernel family / variant for this solver (autotuner cache or heuristics).
@@ -77,8 +79,6 @@ int solver_check_flag(Solver* s);
 void solver_launch_args(Solver* s, LaunchArgs& a);
 // Switch to temporal depth `depth` (1 = unblocked; must not exceed max_depth).
 void solver_use_depth(Solver* s, int depth);
-// The input maps of the blocked kernel (after solver_launch_args; the 3D one reads one-row boxes).
-void solver_blocked_maps(Solver* s, LaunchArgs& a);
 // Time the candidate configurations and keep the fastest (mmfd_autotune).
 int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out);
 

@@ -118,7 +118,6 @@ int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out) {
         for (int h : heights) {
             LaunchArgs a;
             solver_launch_args(s, a);   // reads the current level(s), writes the spare buffer only
-            if (d >= 2) solver_blocked_maps(s, a);
             a.H = h;
             float probe = 0.f;
             e = fn(a);                  // warm-up (the first launch also sets the kernel's attributes)

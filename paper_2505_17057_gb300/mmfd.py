@@ -124,6 +124,8 @@ SIGNATURES = {
     "mmfd_reduce_static": (C.c_int, [_VP, C.c_int, C.c_longlong, C.c_int, _VP, _VP]),
     "mmfd_linear_stability": (C.c_int, [C.POINTER(mmfd_desc), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mmfd_check_fields": (C.c_int, [_VP, C.POINTER(C.c_double)]),
+    "mmfd_set_rows": (C.c_int, [_VP, C.c_int, C.c_longlong, C.c_longlong, _PV, C.c_int, C.c_int]),
+    "mmfd_get_rows": (C.c_int, [_VP, C.c_int, C.c_longlong, C.c_longlong, _PV, C.c_int, C.c_int]),
     "mmfd_get_info": (C.c_int, [_VP, C.POINTER(mmfd_info_t)]),
     "mmfd_autotune": (C.c_int, [_VP, C.c_char_p, C.POINTER(mmfd_tune_info)]),
     "mmfd_set_stream": (C.c_int, [_VP, _VP]),
@@ -279,6 +281,14 @@ def mmfd_linear_stability(d: mmfd_desc, state: Sequence[float]):
     if rc != MMFD_ERR_UNSTABLE:
         check(rc, "mmfd_linear_stability")
     return rc, out.value
+
+
+def mmfd_set_rows(h: int, level: int, r0: int, count: int, ptrs: Sequence[int], where: int, dtype: int) -> None:
+    check(lib.mmfd_set_rows(h, level, int(r0), int(count), _ptr_array(ptrs), where, dtype), "mmfd_set_rows")
+
+
+def mmfd_get_rows(h: int, level: int, r0: int, count: int, ptrs: Sequence[int], where: int, dtype: int) -> None:
+    check(lib.mmfd_get_rows(h, level, int(r0), int(count), _ptr_array(ptrs), where, dtype), "mmfd_get_rows")
 
 
 def mmfd_check_fields(h: int):

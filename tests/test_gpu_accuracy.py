@@ -37,17 +37,23 @@ def test_tgv_against_the_analytic_decay(acc, re):
 
 
 def test_ncde_storages_against_fp64(acc):
+    # the stated 1e-5 is not met by FP32 on the nonlinear NCDE (5.9e-4 at 1024^2 after 10k steps;
+    # FP32 storage with FP64 arithmetic alone gives 1.3e-4, so the FP32 arithmetic carries most of
+    # it): the bound asserted here is the measured one at a reduced size
     r = acc.ncde2d(256, 1000)
     assert abs(r["fp64"]["mass_drift"]) < 1e-13, r
     assert r["fp32"]["max_rel_vs_fp64"] < 1e-3 and abs(r["fp32"]["mass_drift"]) < 1e-5, r
     assert r["bf16_sr"]["max_rel_vs_fp64"] < 0.1, r
 
 
-@pytest.mark.parametrize("kind", ["cde3d", "nse3d"])
-def test_3d_storages_against_fp64(acc, kind):
-    r = acc.three_d(kind, 128, 200)
+@pytest.mark.parametrize("kind,n", [("cde3d", 512), ("nse3d", 256)])
+def test_3d_fp32_within_1e5_of_fp64_at_the_stated_step_count(acc, kind, n):
+    # the stated tolerance (FP32 storage within 1e-5 relative max-norm of FP64) after the 3D
+    # configuration's 1000 steps: met (cde3d_512 ~2e-6, the NSE ~1e-7; the 3D NSE on 256^3, where
+    # its FP64 reference, bound by FP64 arithmetic, takes seconds)
+    r = acc.three_d(kind, n, 1000)
     assert abs(r["fp64"]["mass_drift"]) < 1e-13, r
-    assert r["fp32"]["max_rel_vs_fp64"] < 1e-4, r
+    assert r["fp32"]["max_rel_vs_fp64"] < 1e-5, r
     assert r["bf16"]["max_rel_vs_fp64"] < 0.5, r
 
 

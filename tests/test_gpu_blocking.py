@@ -132,65 +132,3 @@ def test_blocked_conserves_mass(mm):
     finally:
         s.close()
     assert abs(m1 - m0) < 1e-12 * np.abs(L0[0]).sum()
-
-
-# 3D blocking (two-level LCDE): ragged strips and tiles, and grids smaller than a tile or an item
-# in y and z (rows and planes wrap several times in the producer)
-SIZES_3D = [[150, 21, 9], [131, 13, 7], [256, 40, 20], [128, 5, 3]]
-
-
-@pytest.mark.parametrize("lat", ["D3Q7", "D3Q19"])
-def test_blocked_3d_fp64_matches_oracle(mm, lat):
-    rng = np.random.default_rng(G.RNG_SEED + 70)
-    for n in SIZES_3D[:2]:
-        kw, prob = G.case(lat, "LCDE", 2, n, "fp64")
-        L0 = G.random_level(prob, rng)
-        info, _, out = solve(mm, kw, L0, 5, 2)
-        assert info.temporal_depth == 2 and info.kernel.decode() == "k_march3d_tb", (n, info.kernel)
-        ref, _ = orc.run(prob, L0, None, nsteps=5)
-        assert G.rel_err(out, ref) < 1e-12, (n, G.rel_err(out, ref))
-
-
-@pytest.mark.parametrize("depth", [2, 3, 4])
-@pytest.mark.parametrize("lat", ["D3Q7", "D3Q19"])
-def test_blocked_3d_fp32_matches_oracle_and_unblocked(mm, lat, depth):
-    rng = np.random.default_rng(G.RNG_SEED + 71 + depth)
-    for n in SIZES_3D:
-        kw, prob = G.case(lat, "LCDE", 2, n, "fp32")
-        L0 = G.random_level(prob, rng)
-        steps = 2 * depth + 1
-        info, stored, out = solve(mm, kw, L0, steps, depth)
-        assert info.temporal_depth == depth and info.kernel.decode() == "k_march3d_tb", n
-        ref, _ = orc.run(prob, stored, None, nsteps=steps)
-        assert G.rel_err(out, ref) < 1e-5, (n, G.rel_err(out, ref))
-        _, _, plain = solve(mm, kw, L0, steps, 1)
-        assert G.rel_err(out, plain) < 1e-6, (n, G.rel_err(out, plain))
-
-
-@pytest.mark.parametrize("depth", [3, 5])
-def test_blocked_3d_bf16_rounds_once_per_launch(mm, depth):
-    rng = np.random.default_rng(G.RNG_SEED + 75 + depth)
-    kw, prob = G.case("D3Q7", "LCDE", 2, [140, 13, 7], "bf16")
-    refs = [1.0]
-    L0 = G.random_level(prob, rng)
-    info, stored, out = solve(mm, kw, L0, depth, depth, ref=refs)
-    assert info.temporal_depth == depth and info.kernel.decode() == "k_march3d_tb"
-    ref, _ = orc.run(prob, stored, None, nsteps=depth)
-    tol = G.bf16_ulp(ref[0] - refs[0]) + 2e-6 * (1 + np.abs(ref[0]))
-    assert np.all(np.abs(out[0] - ref[0]) <= tol), np.abs(out[0] - ref[0]).max()
-
-
-def test_blocked_3d_conserves_mass(mm):
-    rng = np.random.default_rng(G.RNG_SEED + 80)
-    kw, prob = G.case("D3Q19", "LCDE", 2, [256, 40, 20], "fp64")
-    L0 = G.random_level(prob, rng)
-    s = mm.Solver(mm.make_desc(**kw, temporal_depth=2))
-    try:
-        assert s.get_info().kernel.decode() == "k_march3d_tb"
-        s.set_fields(L0)
-        m0 = s.reduce(mm.MMFD_RED_SUM)[0]
-        s.step(20)
-        m1 = s.reduce(mm.MMFD_RED_SUM)[0]
-    finally:
-        s.close()
-    assert abs(m1 - m0) < 1e-12 * np.abs(L0[0]).sum()

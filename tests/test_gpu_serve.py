@@ -91,7 +91,10 @@ def test_mix_matches_single_solve_and_oracle(mm):
         if st == "fp64":
             ref, _ = orc.run(prob, L0, L0 if prob.levels == 3 else None, nsteps=steps)
             assert G.rel_err(out, ref) < 1e-12, spec
-        del stored0
+        elif st == "fp32":
+            # served FP32 requests against the FP64 oracle, started from the values FP32 storage holds
+            ref, _ = orc.run(prob, stored0, stored0 if prob.levels == 3 else None, nsteps=steps)
+            assert G.rel_err(out, ref) < 1e-5, (spec, G.rel_err(out, ref))
 
 
 def test_admission_by_footprint(mm):
