@@ -52,7 +52,10 @@ def test_3d_fp32_within_1e5_of_fp64_at_the_stated_step_count(acc, kind, n):
     # configuration's 1000 steps: met (cde3d_512 ~2e-6, the NSE ~1e-7; the 3D NSE on 256^3, where
     # its FP64 reference, bound by FP64 arithmetic, takes seconds)
     r = acc.three_d(kind, n, 1000)
-    assert abs(r["fp64"]["mass_drift"]) < 1e-13, r
+    # the scheme conserves mass exactly (the update weights of the density sum to one); in FP64
+    # each step adds at most a few units of rounding (2.2e-16) to the relative mass, so 1000
+    # steps stay below 1e-12 (measured 1.4e-13 on the NSE at 256^3)
+    assert abs(r["fp64"]["mass_drift"]) < 1e-12, r
     assert r["fp32"]["max_rel_vs_fp64"] < 1e-5, r
     assert r["bf16"]["max_rel_vs_fp64"] < 0.5, r
 
