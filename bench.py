@@ -339,16 +339,21 @@ def serving_bench(count, seed, mmfd, stream, budget_gb=40.0, slots=64, steps_per
 
     lat32, mk32, out32, st32 = served("fp32")
     latmix, mkmix, outmix, stmix = served("mixed")
-    err32 = max(max(float(np.abs(a - b).max() / max(1e-30, np.abs(b).max())) for a, b in zip(o, p))
-                for o, p in zip(out32, plain_out))
-    errmix = max(max(float(np.abs(a - b).max() / max(1e-30, np.abs(b).max())) for a, b in zip(o, p))
-                 for o, p in zip(outmix, plain_out))
+    # deviation per field relative to the request's initial field scale: a decaying flow ends far
+    # below its initial magnitude (the low-Re vortices of small grids reach 1e-29 after 5000
+    # steps), where a ratio to the final field's own maximum measures only the rounding floor
+    def dev(outs):
+        return max(max(float(np.abs(a - b).max() / max(1e-30, np.abs(f0).max())) for a, b, f0 in zip(o, p, r.fields))
+                   for o, p, r in zip(outs, plain_out, reqs))
+    err32 = dev(out32)
+    errmix = dev(outmix)
     res = {"requests": count, "seed": seed, "arrival_rate_per_s": 0.8 * capacity, "total_lattice_updates": total_lu,
            "plain_fp32": summary(plain_lat, plain_makespan),
-           "served_fp32": {**summary(lat32, mk32), "max_rel_err_vs_plain": err32,
+           "served_fp32": {**summary(lat32, mk32), "max_dev_vs_plain": err32,
                            "ticks": st32["ticks"], "launches": st32["launches"], "graph_replays": st32["graph_replays"]},
-           "served_mixed_fp32_bf16": {**summary(latmix, mkmix), "max_rel_err_vs_plain_fp32": errmix},
-           "budget_gb": budget_gb, "max_slots": slots, "steps_per_tick": steps_per_tick}
+           "served_mixed_fp32_bf16": {**summary(latmix, mkmix), "max_dev_vs_plain_fp32": errmix},
+           "budget_gb": budget_gb, "max_slots": slots, "steps_per_tick": steps_per_tick,
+           "deviation": "max over requests and fields of max|served - plain| / max|initial field|"}
     res["served_fp32_vs_plain_mlups"] = res["served_fp32"]["mlups"] / res["plain_fp32"]["mlups"]
     # saturated throughput (capacity): plain = sum of service times; served = burst makespan
     res["capacity_mlups"] = {"plain_fp32": total_lu / sum(service) / 1e6, "served_fp32": burst("fp32"),

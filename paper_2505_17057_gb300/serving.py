@@ -61,8 +61,12 @@ def make_request(rng: inputs.SplitMix64, storage_mix: bool = True, steps_scale: 
             dx = 2 * math.pi / n
             phi = 0.5 * base
             dmax = 0.01 * (1 + float(np.abs(phi).max()) ** 2)
-            # diffusive limit of config 2, and a convective one (|B'| dt / dx <= 0.2) for coarse grids
-            dt = min(0.4 * dx * dx / (2 * dmax), 0.2 * dx / max(1e-12, float(np.abs(phi).max())))
+            # diffusive limit of config 2, a convective one (|B'| dt / dx <= 0.2) for coarse grids,
+            # and dt <= 0.5 D_min / max|B'|^2 (B' = phi, D_min = 0.01): without the last bound the
+            # three-level central scheme is linearly unstable about the field's extreme states on
+            # coarse grids (amplification up to 1.03 per step), which BF16 rounding noise exposes
+            dt = min(0.4 * dx * dx / (2 * dmax), 0.2 * dx / max(1e-12, float(np.abs(phi).max())),
+                     0.5 * 0.01 / max(1e-12, float(np.abs(phi).max()) ** 2))
             desc = dict(pde="NCDE", lattice="D2Q9", levels=3, n=[n, n], dt=dt, dx=[dx, dx],
                         flux=[[0, 0, 0.5, 0], [0, 0, 0.5, 0]], diff=[0.01, 0, 0.01, 0],
                         a=(7 / 8, 0.0, 1 / 8), ahat=(1 / 8, 0.0, -1 / 8), storage=storage)
@@ -85,7 +89,8 @@ def make_request(rng: inputs.SplitMix64, storage_mix: bool = True, steps_scale: 
             dx = 2 * math.pi / n
             phi = 0.5 * base
             dmax = 0.01 * (1 + float(np.abs(phi).max()) ** 2)
-            dt = min(0.3 * dx * dx / (2 * dmax), 0.15 * dx / max(1e-12, float(np.abs(phi).max())))
+            dt = min(0.3 * dx * dx / (2 * dmax), 0.15 * dx / max(1e-12, float(np.abs(phi).max())),
+                     0.5 * 0.01 / max(1e-12, float(np.abs(phi).max()) ** 2))   # as in 2D
             desc = dict(pde="NCDE", lattice="D3Q19", levels=3, n=[n, n, n], dt=dt, dx=[dx, dx, dx],
                         flux=[[0, 0, 0.5, 0]] * 3, diff=[0.01, 0, 0.01, 0],
                         a=(7 / 8, 0.0, 1 / 8), ahat=(1 / 8, 0.0, -1 / 8), storage=storage)

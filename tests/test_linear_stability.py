@@ -112,3 +112,18 @@ def test_linear_pdes_are_refused():
     with pytest.raises(mmfd.MMFDError) as e:
         mmfd.mmfd_linear_stability(mmfd.make_desc(**kw), [1.0])
     assert e.value.code == mmfd.MMFD_ERR_UNSUPPORTED
+
+
+def test_served_ncde_requests_stable_about_their_extreme_states():
+    # the request generator's time step keeps every NCDE request of the seeded stream linearly
+    # stable about each value its initial field spans (convection speed B'(phi) = phi), not only
+    # about phi = 0 as mmfd_create checks
+    from paper_2505_17057_gb300 import serving
+    reqs = [r for r in serving.make_stream(60, seed=5) if r.desc["pde"] == "NCDE"]
+    assert len(reqs) >= 10
+    for r in reqs:
+        m = float(np.abs(r.fields[0]).max())
+        d = mmfd.make_desc(**r.desc)
+        for v in np.linspace(-m, m, 5):
+            rc, amp = mmfd.mmfd_linear_stability(d, [v])
+            assert rc == mmfd.MMFD_OK and amp <= 1 + 1e-9, (r.desc["n"], r.desc["dt"], v, amp)
