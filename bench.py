@@ -101,15 +101,16 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel: str, workload: str, depth: int = 1, sweeps: int = 0):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source, at
-    this temporal depth and (theta-scheme) with this many Jacobi sweeps per step."""
+def traffic_from_profile(kernel: str, workload: str, depth: int = 1, sweeps: int = 0, storage: str = "fp32"):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source, with
+    this storage, at this temporal depth and (theta-scheme) with this many Jacobi sweeps per step.
+    Keys are "workload:kernel" for FP32 storage and "workload:kernel:storage" otherwise."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    e = d.get(f"{workload}:{kernel}")
+    e = d.get(f"{workload}:{kernel}" + ("" if storage == "fp32" else f":{storage}"))
     if not e or e.get("source_sha") != kernel_source_sha(kernel) or e.get("temporal_depth", 1) != depth:
         return None
     if e.get("sweeps", 0) != sweeps:
@@ -645,7 +646,7 @@ def run_ours(args):
             effective = bytes_per_lu * nodes / avg_launch_s / 1e9
         achieved = alg_bytes / avg_launch_s / 1e9
         traffic = traffic_from_profile("k_march2d_theta" if theta else kernel_name, args.workload,
-                                       jd if theta else depth, info.sweeps)
+                                       jd if theta else depth, info.sweeps, args.storage)
 
         # end to end through the public API: every step uploads the level from pinned host memory,
         # advances it and copies the stepped level back to pinned host memory (the step's result);

@@ -24,21 +24,29 @@ def test_source_lists_name_existing_files():
             assert os.path.exists(os.path.join(csrc, f)), (kernel, f)
 
 
+def _split(key):
+    parts = key.split(":")
+    return parts[0], parts[1], parts[2] if len(parts) > 2 else "fp32"
+
+
 def test_traffic_matches_only_its_capture_conditions():
     for key, e in _entries().items():
-        workload, kernel = key.split(":")
+        workload, kernel, storage = _split(key)
         depth, sweeps = e.get("temporal_depth", 1), e.get("sweeps", 0)
         if e["source_sha"] != bench.kernel_source_sha(kernel):
             continue   # a stale entry is reported as null, which the next check also covers
-        assert bench.traffic_from_profile(kernel, workload, depth, sweeps) == e["dram_bytes_per_launch"]
-        assert bench.traffic_from_profile(kernel, workload, depth + 1, sweeps) is None
-        assert bench.traffic_from_profile(kernel, workload, depth, sweeps + 1) is None
-        assert bench.traffic_from_profile(kernel, "other_workload", depth, sweeps) is None
+        assert bench.traffic_from_profile(kernel, workload, depth, sweeps, storage) == e["dram_bytes_per_launch"]
+        assert bench.traffic_from_profile(kernel, workload, depth + 1, sweeps, storage) is None
+        assert bench.traffic_from_profile(kernel, workload, depth, sweeps + 1, storage) is None
+        assert bench.traffic_from_profile(kernel, "other_workload", depth, sweeps, storage) is None
+        other = "bf16" if storage == "fp32" else "fp32"
+        if f"{workload}:{kernel}" + ("" if other == "fp32" else f":{other}") not in _entries():
+            assert bench.traffic_from_profile(kernel, workload, depth, sweeps, other) is None
 
 
 def test_traffic_is_null_once_a_source_changes(monkeypatch):
     key, e = next(iter(_entries().items()))
-    workload, kernel = key.split(":")
+    workload, kernel, _ = _split(key)
     monkeypatch.setattr(bench, "kernel_source_sha", lambda k: "0" * 16)
     assert bench.traffic_from_profile(kernel, workload, e.get("temporal_depth", 1), e.get("sweeps", 0)) is None
 
