@@ -429,6 +429,14 @@ typedef struct {
 
 typedef struct mmfd_server mmfd_server;
 
+/* Create a server.  Environment read at creation (for comparisons and tests):
+ *   MMFD_SERVE_QUEUE=1        every batched class runs all steps of a tick as one persistent
+ *                             launch: a device-resident work queue of (step, tile) items, each
+ *                             tile waiting (bounded, about a second) until its request's
+ *                             previous step is complete.  Same results as the per-step launches.
+ *   MMFD_SERVE_QUEUE_STALL=1  (with the queue) no wait can be met: every wait runs out and the
+ *                             results of the server's requests report MMFD_ERR_TIMEOUT.  Only
+ *                             for testing the failure path. */
 int mmfd_server_create(const mmfd_server_desc* desc, mmfd_server** out);
 /* Queue a solve: the descriptor (stream and allocator fields ignored), the initial level
  * (nf host pointers, MMFD_DT_F64 or F32, copied at submit) and the step count.  Returns
@@ -440,7 +448,9 @@ int mmfd_submit(mmfd_server* s, const mmfd_desc* d, const void* const* init, int
 int mmfd_poll(mmfd_server* s, unsigned long long ticket, mmfd_result* res);
 /* Run the scheduler until every queued request is finished. */
 int mmfd_server_drain(mmfd_server* s);
-/* Copy a finished request's final level (nf pointers, host or device, type dtype). */
+/* Copy a finished request's final level (nf pointers, host or device, type dtype).
+ * MMFD_ERR_TIMEOUT if a kernel of the server gave up a bounded wait (a TMA copy of a solo
+ * launch, or the work queue's wait for a previous step); the server's results are then void. */
 int mmfd_result_fields(mmfd_server* s, unsigned long long ticket, void* const* out, int where, int dtype);
 /* Forget a finished request and free its memory. */
 int mmfd_release(mmfd_server* s, unsigned long long ticket);

@@ -6,7 +6,9 @@
 //      (level buffers + coefficients) fits the budget; upload their initial level;
 //   3. launch one tick: steps_per_tick steps of every active request; per step, one batched
 //      grid-stride launch per kernel class (lattice, PDE, levels, storage) covering all of that
-//      class's requests -- uneven grids packed into one launch; the tick's launches are
+//      class's requests -- uneven grids packed into one launch (or, with MMFD_SERVE_QUEUE=1,
+//      one launch per class for all the tick's steps: a device work queue of (step, tile) items
+//      with bounded waits on each request's previous step); the tick's launches are
 //      captured once per batch composition as a CUDA graph and replayed;
 //   4. record the tick's event.
 // At most two ticks are in flight, so host scheduling overlaps GPU work.  Requests share no
@@ -14,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -73,6 +76,8 @@ constexpr long long kSoloNodes = 1ll << 16;
 
 struct ClassTables {
     BatchFn fn = nullptr;
+    QueueFn qfn = nullptr;                 // the work-queue kernel of the class (MMFD_SERVE_QUEUE=1)
+    unsigned* ctl = nullptr;               // its control words: head, abort, per-request counters
     std::vector<Req*> members;
     BatchItem* h[2] = {nullptr, nullptr};  // pinned host tables (double-buffered)
     BatchItem* d[2] = {nullptr, nullptr};  // device tables
@@ -103,7 +108,11 @@ struct Server {
     unsigned long long next_ticket = 1;
     int parity = 0;
     int sms = 152;
-    int* d_flag = nullptr;  // device error flag for the march kernels' bounded waits
+    int* d_flag = nullptr;  // device error flag for the kernels' bounded waits
+    // MMFD_SERVE_QUEUE=1 at server creation: the batched classes run all steps of a tick as one
+    // work-queue launch (k_batch_queue) instead of one k_batch launch per step
+    bool use_queue = false;
+    unsigned queue_stall = 0;   // MMFD_SERVE_QUEUE_STALL=1: every queue wait runs out (failure-detection test)
     void* stage = nullptr;
     size_t stage_bytes = 0;
     // graph cache: composition key -> executable graph
@@ -254,6 +263,10 @@ int ensure_tables(Server* s, ClassTables& c, int n) {
         int rc = srv_alloc(s, sizeof(BatchItem) * cap, reinterpret_cast<void**>(&c.d[p]));
         if (rc != MMFD_OK) return rc;
     }
+    if (c.ctl) srv_free(s, c.ctl);
+    c.ctl = nullptr;
+    int rc = srv_alloc(s, sizeof(unsigned) * (size_t)(cap + 2), reinterpret_cast<void**>(&c.ctl));
+    if (rc != MMFD_OK) return rc;
     c.cap = cap;
     return MMFD_OK;
 }
@@ -278,6 +291,8 @@ int launch_tick(Server* s) {
         const BatchItem* items;
         int n;
         long long total;
+        QueueFn qfn;        // set when the class runs as one work-queue launch
+        unsigned* ctl;
     };
     std::vector<Launch> launches;
     TickRec tick;
@@ -289,6 +304,7 @@ int launch_tick(Server* s) {
         if (!c.fn) {
             const Resolved& r = *c.members[0]->r;
             c.fn = find_batch(r.lat, r.pde, r.levels, r.st);
+            c.qfn = find_batch_queue(r.lat, r.pde, r.levels, r.st);
             if (!c.fn) return set_error(MMFD_ERR_UNSUPPORTED, "no batched kernel for this class");
         }
         int rc = ensure_tables(s, c, (int)c.members.size());
@@ -314,8 +330,9 @@ int launch_tick(Server* s) {
         }
         cudaError_t e = cudaMemcpyAsync(c.d[par], c.h[par], sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync batch table");
-        launches.push_back({c.fn, c.d[par], n, tile0});
-        key += std::to_string(kv.first) + ":" + std::to_string(n) + ":" + std::to_string(tile0) + ":" +
+        const bool queued = s->use_queue && c.qfn && tile0 * S < (1ll << 31);
+        launches.push_back({c.fn, c.d[par], n, tile0, queued ? c.qfn : nullptr, c.ctl});
+        key += std::to_string(kv.first) + (queued ? "q" : "") + ":" + std::to_string(n) + ":" + std::to_string(tile0) + ":" +
                std::to_string(reinterpret_cast<uintptr_t>(c.d[par])) + ";";
     }
     for (Req* q : solos) {
@@ -378,8 +395,16 @@ int launch_tick(Server* s) {
             for (int k = 0; k < nside && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s->side[k], s->fork_ev, 0);
             if (e != cudaSuccess) return e;
         }
+        for (const Launch& L : launches) {
+            if (!L.qfn) continue;
+            cudaError_t e = cudaMemsetAsync(L.ctl, 0, sizeof(unsigned) * (size_t)(L.n + 2), s->stream);
+            if (e == cudaSuccess) e = L.qfn(L.items, L.n, L.total, S, L.ctl, s->d_flag, s->queue_stall, s->stream);
+            if (e != cudaSuccess) return e;
+            s->st.launches++;
+        }
         for (int j = 0; j < S; ++j) {
             for (const Launch& L : launches) {
+                if (L.qfn) continue;
                 long long grid = L.total < (long long)s->sms * 8 ? L.total : (long long)s->sms * 8;
                 cudaError_t e = L.fn(L.items, L.n, L.total, j, (int)grid, s->stream);
                 if (e != cudaSuccess) return e;
@@ -535,6 +560,8 @@ int mmfd_server_create(const mmfd_server_desc* desc, mmfd_server** out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (const char* qv = std::getenv("MMFD_SERVE_QUEUE")) s->use_queue = std::strcmp(qv, "1") == 0;
+    if (const char* qv = std::getenv("MMFD_SERVE_QUEUE_STALL")) s->queue_stall = std::strcmp(qv, "1") == 0 ? (1u << 30) : 0u;
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.handleTypes = cudaMemHandleTypeNone;
@@ -688,7 +715,10 @@ int mmfd_result_fields(mmfd_server* h, unsigned long long ticket, void* const* o
         cudaError_t fe = cudaMemcpyAsync(&flag, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
         if (fe == cudaSuccess) fe = cudaStreamSynchronize(s->stream);
         if (fe != cudaSuccess) return cuda_fail(fe, "reading the server error flag");
-        if (flag != 0) return set_error(MMFD_ERR_TIMEOUT, "a kernel's bounded wait for its TMA copies ran out");
+        if (flag != 0)
+            return set_error(MMFD_ERR_TIMEOUT, flag == KERR_QUEUE_TIMEOUT
+                                                   ? "the batched work queue's bounded wait for a request's previous step ran out"
+                                                   : "a kernel's bounded wait for its TMA copies ran out");
     }
     const long long N = (long long)q->g.nx * q->g.ny * q->g.nz;
     const size_t esz = dtype == MMFD_DT_F64 ? 8 : 4;
@@ -749,11 +779,13 @@ int mmfd_server_destroy(mmfd_server* h) {
         delete q->r;
         delete q;
     }
-    for (auto& kv : s->classes)
+    for (auto& kv : s->classes) {
         for (int p = 0; p < 2; ++p) {
             if (kv.second.h[p]) cudaFreeHost(kv.second.h[p]);
             srv_free(s, kv.second.d[p]);
         }
+        srv_free(s, kv.second.ctl);
+    }
     for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
     srv_free(s, s->stage);
     srv_free(s, s->d_flag);

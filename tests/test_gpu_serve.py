@@ -138,3 +138,40 @@ def test_arrivals_while_running(mm):
     st = srv.stats()
     assert st["finished"] == len(reqs) and st["ticks"] > 0
     srv.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_work_queue_equals_per_step_batch(mm, monkeypatch, graphs):
+    # MMFD_SERVE_QUEUE=1: every batched class runs all steps of a tick as one launch of the
+    # device-resident work queue (k_batch_queue), each tile waiting for its request's previous
+    # step; the node update is the per-step kernel's, so the results are equal bit for bit
+    reqs = _requests(seed=8)
+    per_step, st1 = _serve(mm, reqs, graphs=graphs)
+    monkeypatch.setenv("MMFD_SERVE_QUEUE", "1")
+    queued, st2 = _serve(mm, reqs, graphs=graphs)
+    assert st2["launches"] < st1["launches"], (st1["launches"], st2["launches"])
+    for a, b, spec in zip(queued, per_step, MIX):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), spec
+
+
+def test_work_queue_wait_runs_out_and_reports(mm, monkeypatch):
+    # failure detection without a GPU fault: with MMFD_SERVE_QUEUE_STALL=1 no tile's wait for its
+    # request's previous step can be met, so every wait gives up after its bounded budget (about a
+    # second), the kernel records the timeout in the server's device flag and the result call
+    # reports MMFD_ERR_TIMEOUT; the context stays usable
+    monkeypatch.setenv("MMFD_SERVE_QUEUE", "1")
+    monkeypatch.setenv("MMFD_SERVE_QUEUE_STALL", "1")
+    kw, prob = G.case("D2Q9", "LCDE", 2, [64, 40], "fp32")
+    L0 = G.random_level(prob, np.random.default_rng(1))
+    srv = mm.Server(1 << 30, max_slots=4, steps_per_tick=4)
+    t = srv.submit(mm.make_desc(**kw), L0, 6)
+    srv.drain()
+    with pytest.raises(mm.MMFDError) as e:
+        srv.result(t)
+    assert e.value.code == mm.MMFD_ERR_TIMEOUT
+    srv.release(t)
+    srv.close()
+    monkeypatch.delenv("MMFD_SERVE_QUEUE_STALL")
+    res, _ = _serve(mm, _requests(seed=8)[:3])
+    assert len(res) == 3
