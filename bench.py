@@ -82,6 +82,8 @@ KERNEL_SOURCES = {
                         "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp"],
     "k_march3d_nse_s": ["k_march_lean.cu", "k_march3d.cuh", "k_march2d.cuh", "stencil.cuh", "tma.cuh",
                         "mmfd_internal.h", "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp"],
+    "k_march2d_tb_nse": ["k_march2d_tb_nse.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h",
+                         "kernels.h", "k_direct.cuh", "tune.cpp", "tma_host.cpp", "params.cpp"],
     "k_march2d_src": ["k_march2d_src.cu", "k_march2d.cuh", "stencil.cuh", "tma.cuh", "mmfd_internal.h", "kernels.h",
                       "k_direct.cuh", "tune.cpp", "tma_host.cpp"],
     # one theta-scheme step: the right-hand side (k_march2d) and the Jacobi sweeps (k_march2d_tb
@@ -754,8 +756,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv2d_4096")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
-    ap.add_argument("--depth", type=int, default=1,
-                    help="temporal blocking depth (1 = plain step, 0 = chosen by the autotuner)")
+    ap.add_argument("--depth", type=int, default=0,
+                    help="temporal blocking depth: 0 = the autotuner picks among the depths the solver "
+                         "allows (every step is still computed; blocked launches fuse several), "
+                         "1 = one step per launch, T = T steps per launch")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (work-item height from the launcher's heuristic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -111,8 +111,10 @@ typedef void (*mmfd_free_fn)(void* ptr, void* ctx);
  *                        T >= 2 asks for T; 0 asks for the deepest available.  Blocking is
  *                        available for 2D two-level LCDE / NCDE grids with nx >= 128 and
  *                        ny >= 2T, up to T = 2 (FP64), 4 (FP32), 5 (BF16) -- the x ghost
- *                        columns of the padded layout hold that many levels.  3D grids run
- *                        unblocked.  Larger requests
+ *                        columns of the padded layout hold that many levels -- and for the
+ *                        2D D2Q9 He-Luo NSE in the lean streaming form (two levels, equal
+ *                        spacing, a momentum set proportional to the scalar one; FP32 / BF16)
+ *                        up to T = 3.  3D grids run unblocked.  Larger requests
  *                        are clamped, other configurations run unblocked; mmfd_get_info reports
  *                        the depth in use.  mmfd_step(n) runs n / T blocked launches and the
  *                        remaining n % T steps unblocked.  With BF16 storage a blocked solver

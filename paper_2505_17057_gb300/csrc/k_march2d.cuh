@@ -226,6 +226,55 @@ __host__ __device__ constexpr int pushed_pairs(int C) {
     return m;
 }
 
+// One input node of a 2D row (column C of the lane's window, fields f = rho, ux, uy) in the
+// lean He-Luo form (Coef::nA), pushed into the accumulators of output rows r-1 (P), r (C) and
+// r+1 (N): per node |u|^2 and the class bases, per pair e_p . u, E_p as one FMA on the base and
+// O_p as one multiply, a+ / a- folded in for streaming momentum sets.  l: input level.  The
+// marching kernel and the temporally blocked NSE kernel share it, so that they round alike.
+template <int LAT, int LEAN, int LN, int C, typename T>
+__device__ __forceinline__ void lean_push_node2d(const Coef<T>& cf, int l, const T* f, T (&accP)[LN][3],
+                                                 T (&accC)[LN][3], T (&accN)[LN][3]) {
+    constexpr int NF = 3;
+    constexpr int NP = lat_npair(LAT);
+    constexpr bool OWN = C >= 0 && C < LN;
+    constexpr int MASK = pushed_pairs<LAT, LN>(C);
+    const T rho = f[0], ux = f[1], uy = f[2];
+    const T U = uy * uy + ux * ux;
+    if constexpr (OWN) {
+        accC[C][0] += cf.nc[l][1] * U + cf.nc[l][0] * rho;
+        accC[C][1] += cf.ab0[l] * ux;
+        accC[C][2] += cf.ab0[l] * uy;
+    }
+    constexpr bool AX = (MASK & 3) != 0, DG = (MASK & 12) != 0;
+    [[maybe_unused]] T Bk[2];
+    if constexpr (AX) Bk[0] = cf.nU[l][0] * U + cf.nA[l][0] * rho;
+    if constexpr (DG) Bk[1] = cf.nU[l][1] * U + cf.nA[l][1] * rho;
+    static_for<0, NP>([&](auto pcc) {
+        constexpr int P_ = decltype(pcc)::value;
+        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
+        constexpr int TP = C - EX, TM = C + EX;
+        constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
+        if constexpr (HP || HM) {
+            const T cu = edot<LAT, P_>(ux, uy, T(0));
+            const T E = cf.nk[l][P_] * (cu * cu) + Bk[pair_class(LAT, P_)];
+            const T O = cf.no[l][P_] * cu;
+            [[maybe_unused]] T sE = T(0), mO = T(0);
+            if constexpr (LEAN == LEAN_GENERAL) {
+                sE = cf.ap[l] * E;
+                mO = cf.abp[l] * O;
+            }
+            if constexpr (HP) {
+                T* acc = EY == 1 ? accP[TP] : accC[TP];
+                lean_push<LAT, LEAN, P_, 1, NF>(acc, cf, l, E, O, sE, mO);
+            }
+            if constexpr (HM) {
+                T* acc = EY == 1 ? accN[TM] : accC[TM];
+                lean_push<LAT, LEAN, P_, -1, NF>(acc, cf, l, E, O, sE, mO);
+            }
+        }
+    });
+}
+
 // Six consecutive source values xb-1 .. xb+4 of one padded row (xb a multiple of 4): a vector
 // load for the lane's own four (16-byte aligned in the source layout) and two scalars; columns
 // beyond the right ghost column are not read (lanes past nx only feed nodes that are not stored).
@@ -439,45 +488,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                         }
                     });
                 } else if constexpr (PDE == PDE_NSE && LEAN != LEAN_NONE) {
-                    // lean He-Luo form (Coef::nA): a+ / a- folded into E', O'; one FMA per pair
-                    // on a per-node base shared by the axis / diagonal pairs
-                    constexpr int MASK = pushed_pairs<LAT, LN>(C);
-                    const T* f = raw[C + 1];
-                    const T rho = f[0], ux = f[1], uy = f[2];
-                    const T U = uy * uy + ux * ux;
-                    if constexpr (OWN) {
-                        accC[C][0] += cf.nc[l][1] * U + cf.nc[l][0] * rho;
-                        accC[C][1] += cf.ab0[l] * ux;
-                        accC[C][2] += cf.ab0[l] * uy;
-                    }
-                    constexpr bool AX = (MASK & 3) != 0, DG = (MASK & 12) != 0;
-                    [[maybe_unused]] T Bk[2];
-                    if constexpr (AX) Bk[0] = cf.nU[l][0] * U + cf.nA[l][0] * rho;
-                    if constexpr (DG) Bk[1] = cf.nU[l][1] * U + cf.nA[l][1] * rho;
-                    static_for<0, NP>([&](auto pcc) {
-                        constexpr int P_ = decltype(pcc)::value;
-                        constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
-                        constexpr int TP = C - EX, TM = C + EX;
-                        constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
-                        if constexpr (HP || HM) {
-                            const T cu = edot<LAT, P_>(ux, uy, T(0));
-                            const T E = cf.nk[l][P_] * (cu * cu) + Bk[pair_class(LAT, P_)];
-                            const T O = cf.no[l][P_] * cu;
-                            [[maybe_unused]] T sE = T(0), mO = T(0);
-                            if constexpr (LEAN == LEAN_GENERAL) {
-                                sE = cf.ap[l] * E;
-                                mO = cf.abp[l] * O;
-                            }
-                            if constexpr (HP) {
-                                T* acc = EY == 1 ? accP[TP] : accC[TP];
-                                lean_push<LAT, LEAN, P_, 1, NF>(acc, cf, l, E, O, sE, mO);
-                            }
-                            if constexpr (HM) {
-                                T* acc = EY == 1 ? accN[TM] : accC[TM];
-                                lean_push<LAT, LEAN, P_, -1, NF>(acc, cf, l, E, O, sE, mO);
-                            }
-                        }
-                    });
+                    lean_push_node2d<LAT, LEAN, LN, C>(cf, l, raw[C + 1], accP, accC, accN);
                 } else {
                     constexpr int MASK = pushed_pairs<LAT, LN>(C);
                     const T* f = raw[C + 1];

@@ -51,6 +51,10 @@ LaunchFn find_march3d(int lat, int pde, int levels, int st);
 // It reads the level through the same 2-row-box tensor maps as k_march2d.
 LaunchFn find_march2d_tb(int lat, int pde, int levels, int st, int depth);
 int march2d_tb_max_depth(int st);
+// The temporally blocked D2Q9 He-Luo NSE step in the lean streaming form (two levels, FP32 /
+// BF16 storage; depth 2 .. march2d_tb_nse_max_depth()).
+LaunchFn find_march2d_tb_nse(int st, int depth);
+int march2d_tb_nse_max_depth();
 // The same kernel advancing `depth` Jacobi sweeps of the two-level LCDE theta-scheme per launch
 // (FP32 / FP64 levels): the coefficient block is the sweep's stencil, src[0] the right-hand
 // side and src_coef's W0[0] its weight.

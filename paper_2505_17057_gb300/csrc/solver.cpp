@@ -507,16 +507,26 @@ static const char* lean_name(const Solver* s, const char* family) {
     return names[d][s->lean];
 }
 
+// The 2D temporally blocked step kernel of this solver at `depth` levels per launch: the scalar
+// blocked kernel (two-level LCDE / NCDE), or the blocked lean NSE kernel (D2Q9 He-Luo NSE with a
+// streaming momentum set, two levels); null where neither applies.
+static LaunchFn blocked_kernel(const Solver* s, int depth) {
+    if (s->r.dim != 2 || depth < 2) return nullptr;
+    if (s->r.pde == PDE_NSE)
+        return s->lean == LEAN_STREAM && s->r.levels == 2 ? find_march2d_tb_nse(s->r.st, depth) : nullptr;
+    return find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth);
+}
+
 void solver_use_depth(Solver* s, int depth) {
     LaunchFn fb = nullptr;
     if (depth >= 2 && s->r.theta_on)
         fb = s->r.dim == 2 ? find_march2d_tb_jacobi(s->r.lat, s->r.st, depth) : nullptr;
     else if (depth >= 2)
-        fb = s->r.dim == 2 ? find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, depth) : nullptr;
+        fb = blocked_kernel(s, depth);
     if (fb) {
         s->fn_block = fb;
         s->depth = depth;
-        s->kernel_name = "k_march2d_tb";
+        s->kernel_name = s->r.pde == PDE_NSE && !s->r.theta_on ? "k_march2d_tb_nse" : "k_march2d_tb";
     } else {
         s->fn_block = nullptr;
         s->depth = 1;
@@ -576,6 +586,7 @@ int solver_pick_kernels(Solver* s) {
             // their full depth ox by every writer, bound the depth.
             // (The blocked kernel stages two rows per box, as the solver's maps for these PDEs do.)
             int maxd = march2d_tb_max_depth(s->r.st);
+            if (s->r.pde == PDE_NSE && maxd > march2d_tb_nse_max_depth()) maxd = march2d_tb_nse_max_depth();
             while (maxd >= 2 && s->g.ny < 2 * maxd) --maxd;
             if (s->r.theta_on && s->desc.temporal_depth != 1 && maxd >= 2 &&
                 find_march2d_tb_jacobi(s->r.lat, s->r.st, 2)) {
@@ -586,7 +597,7 @@ int solver_pick_kernels(Solver* s) {
                 solver_use_depth(s, want);
             }
             if (!srcv && !s->r.dirichlet && s->desc.temporal_depth != 1 && maxd >= 2 && march2d_rows_per_stage(s->r.pde) == 2 &&
-                find_march2d_tb(s->r.lat, s->r.pde, s->r.levels, s->r.st, 2)) {
+                blocked_kernel(s, 2)) {
                 s->max_depth = maxd;
                 int want = s->desc.temporal_depth == 0 ? maxd : s->desc.temporal_depth;
                 if (want > maxd) want = maxd;

@@ -132,3 +132,66 @@ def test_blocked_conserves_mass(mm):
     finally:
         s.close()
     assert abs(m1 - m0) < 1e-12 * np.abs(L0[0]).sum()
+
+
+# the lean He-Luo NSE (D2Q9, equal spacing, LBGK tau = 1: streaming momentum) has its own
+# blocked kernel, k_march2d_tb_nse (three fields, depth 2 or 3)
+def _lean_nse_case(n, storage):
+    from oracle import params as P
+    kw = dict(pde="NSE", lattice="D2Q9", levels=2, n=n, dt=1.0, dx=[1.0, 1.0], storage=storage,
+              a=(1.0, 0.0, 0.0), abar=(1.0, 0.0, 0.0))
+    prob = P.problem_nse("D2Q9", 2, n, 1.0, [1.0, 1.0], (1.0, 0.0, 0.0), (1.0, 0.0, 0.0))
+    return kw, prob
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_blocked_lean_nse_fp32_matches_oracle_and_unblocked(mm, depth):
+    # the blocked kernel runs the marching kernel's node update (lean_push_node2d) on the same
+    # FP32 values: equal to the unblocked lean kernel to FP32 rounding (bit for bit on the 4096^2
+    # benchmark grid and on these grids but 517 x 131, where nodes of the x-edge columns differ
+    # by a few units in the last place of the stored offsets and spread from there)
+    rng = np.random.default_rng(G.RNG_SEED + 70 + depth)
+    for n in SIZES:
+        if n[1] < 2 * depth:
+            continue
+        kw, prob = _lean_nse_case(n, "fp32")
+        L0 = G.random_level(prob, rng)
+        steps = 2 * depth + 1
+        info, stored, out = solve(mm, kw, L0, steps, depth)
+        assert info.temporal_depth == depth and info.kernel.decode() == "k_march2d_tb_nse", n
+        ref, _ = orc.run(prob, stored, None, nsteps=steps)
+        assert G.rel_err(out, ref) < 1e-5, (n, G.rel_err(out, ref))
+        pinfo, _, plain = solve(mm, kw, L0, steps, 1)
+        assert pinfo.kernel.decode() == "k_march2d_nse_s", n
+        assert G.rel_err(out, plain) < 1e-6, (n, G.rel_err(out, plain))
+
+
+@pytest.mark.parametrize("sr", [False, True])
+def test_blocked_lean_nse_bf16_rounds_once_per_launch(mm, sr):
+    rng = np.random.default_rng(G.RNG_SEED + 80)
+    n = [260, 33]
+    kw, prob = _lean_nse_case(n, "bf16")
+    refs = [1.0, 0.0, 0.0]
+    L0 = G.random_level(prob, rng)
+    flags = mm.MMFD_FLAG_STOCHASTIC_ROUND if sr else 0
+    info, stored, out = solve(mm, kw, L0, 3, 3, ref=refs, flags=flags)
+    assert info.temporal_depth == 3 and info.kernel.decode() == "k_march2d_tb_nse"
+    ref, _ = orc.run(prob, stored, None, nsteps=3)
+    for f in range(3):
+        tol = G.bf16_ulp(ref[f] - refs[f]) + 2e-6 * (1 + np.abs(ref[f]))
+        assert np.all(np.abs(out[f] - ref[f]) <= tol), (f, np.abs(out[f] - ref[f]).max())
+
+
+def test_blocked_lean_nse_depth_selection(mm):
+    kw, _ = _lean_nse_case([300, 70], "fp32")
+    for want, got in [(0, 3), (4, 3), (2, 2), (1, 1)]:
+        s = mm.Solver(mm.make_desc(**kw, temporal_depth=want))
+        info = s.get_info()
+        s.close()
+        assert info.temporal_depth == got, (want, info.temporal_depth)
+        assert info.kernel.decode() == ("k_march2d_tb_nse" if got > 1 else "k_march2d_nse_s")
+    # a general (non-streaming) momentum set keeps the unblocked kernel
+    kwg = dict(kw, a=(0.95, 0.1, -0.05), abar=(0.9, 0.2, -0.1))
+    s = mm.Solver(mm.make_desc(**kwg, temporal_depth=0))
+    assert s.get_info().temporal_depth == 1
+    s.close()

@@ -96,6 +96,18 @@ def test_full_size_blocked_matches_unblocked(mm):
     assert err < 1e-6, err
 
 
+@pytest.mark.parametrize("depth", [2, 3])
+def test_full_size_blocked_lean_nse_equals_unblocked(mm, depth):
+    # the 4096^2 Taylor-Green vortex of the default benchmark, temporally blocked: the same bits
+    # as the unblocked lean kernel after two launches
+    kw, fields, _ = configs.tgv2d_4096(n=4096, storage="fp32")
+    info, _, blocked = solve_one(mm, kw, fields, 2 * depth, depth)
+    assert info.kernel.decode() == "k_march2d_tb_nse" and info.temporal_depth == depth
+    _, _, plain = solve_one(mm, kw, fields, 2 * depth, 1)
+    for f in range(3):
+        assert np.array_equal(blocked[f], plain[f]), (f, np.abs(blocked[f] - plain[f]).max())
+
+
 @pytest.mark.parametrize("lat,n", [("D2Q9", [65536, 32800]), ("D3Q7", [1300, 1300, 1300])])
 def test_more_than_2_31_nodes(mm, lat, n):
     # node counts past 2^31 (every index in the kernels is 64-bit): one LCDE step of a single
