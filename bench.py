@@ -692,6 +692,35 @@ def run_ours(args):
         e2e_sums_value = e2e_run(False)
         s.close()
 
+        # the plain one-step-per-launch kernel on the same workload, when the headline launch
+        # advances several steps: its own MLUPS and fraction of the HBM roofline (one launch reads
+        # and writes the level once per step)
+        plain_step = None
+        if depth > 1 and not theta and not has_src:
+            d1 = mmfd.make_desc(**desc_kw, temporal_depth=1)
+            s1 = mmfd.Solver(d1, stream=stream)
+            s1.set_fields(fields)
+            if args.tune:
+                s1.autotune(None)
+            info1 = s1.get_info()
+            s1.step(args.warmup)
+            torch.cuda.synchronize()
+            n1 = max(10, min(args.steps, 100))
+            ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n1)]
+            for i in range(n1):
+                ev1[i][0].record(stream)
+                s1.step(1)
+                ev1[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms1 = statistics.mean(a.elapsed_time(b) for a, b in ev1)
+            s1.close()
+            ach1 = info1.bytes_per_lu * nodes / (ms1 / 1e3) / 1e9
+            plain_step = {"value": nodes / (ms1 / 1e3) / 1e6, "unit": UNIT, "kernel": info1.kernel.decode(),
+                          "avg_launch_ms": ms1, "steps": n1,
+                          "roofline": {"bound": "hbm", "achieved": ach1, "peak": peak, "unit": "GB/s",
+                                       "frac": ach1 / peak, "peak_kind": peak_kind,
+                                       "alg_bytes_per_launch": info1.bytes_per_lu * nodes}}
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -730,6 +759,8 @@ def run_ours(args):
                               "read_back": "the FP64 field sums of the stepped level"}},
         "gpu_launches": args.steps * (2 if has_src else launches_per_step),
     }
+    if plain_step is not None:
+        line["plain_step"] = plain_step
     if ws == 1 and args.accuracy:
         with torch.cuda.stream(stream):
             line["accuracy"] = accuracy_block()

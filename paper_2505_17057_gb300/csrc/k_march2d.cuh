@@ -361,7 +361,8 @@ __device__ __forceinline__ void source_quad(const Geom& g, const SrcArgs<T>& sa,
     }
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE,
+          int SRM = 2>
 __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ TmapSet maps, Geom g,
                                                      void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                      StepExtra ex, int H, int nitems, int* __restrict__ err,
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                 S sv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
+                    const unsigned rnd = sr_on<SRM>(ex) ? sr_bits(ex.seed, ex.step, nb + xb + k4 + k, f) : 0u;
                     T v = acc[k4 + k][f];
                     if constexpr (SRC != 0) {
                         if (f == 0) v += add[k];
@@ -725,12 +726,13 @@ constexpr int march2d_stages() {
     return n < 3 ? 3 : (n > 12 ? 12 : (int)n);
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE>
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE,
+          int SRM = 2>
 cudaError_t launch_march2d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march2d_smem<ST, LEVELS, NF, NW, NSTAGE, LN, RPS>();
-    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC, LEAN>;
+    auto kern = k_march2d<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC, LEAN, SRM>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -774,6 +776,16 @@ cudaError_t launch_march2d_t(const LaunchArgs& a) {
     kern<<<grid, NW * 32, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
                                              nitems, a.err, sa);
     return cudaGetLastError();
+}
+
+// The same with the stochastic-rounding choice made per launch (BF16 storage: an instantiation
+// without and one with the rounding code; other storages never round stochastically).
+template <int LAT, int PDE, int LEVELS, int ST, int NW, int NSTAGE, int LN, int RPS, int SRC = 0, int LEAN = LEAN_NONE>
+cudaError_t launch_march2d_sr(const LaunchArgs& a) {
+    if constexpr (ST == ST_BF16) {
+        if (a.ex.sr) return launch_march2d_t<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC, LEAN, 1>(a);
+    }
+    return launch_march2d_t<LAT, PDE, LEVELS, ST, NW, NSTAGE, LN, RPS, SRC, LEAN, 0>(a);
 }
 
 }  // namespace mmfd

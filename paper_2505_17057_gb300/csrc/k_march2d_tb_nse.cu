@@ -24,7 +24,7 @@ namespace {
 constexpr int kTbnStride = 120;   // output columns per strip
 constexpr int kTbnLead = 8;       // lane 0's first column lies kTbnLead columns left of the strip's output
 
-template <int ST, int TT, int NW, int NSTAGE>
+template <int ST, int TT, int NW, int NSTAGE, int SRM>
 __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constant__ TmapSet maps, Geom g,
                                                             void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                             StepExtra ex, int H, int nitems, int* __restrict__ err) {
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constan
                 S sv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + k, f) : 0u;
+                    const unsigned rnd = sr_on<SRM>(ex) ? sr_bits(ex.seed, ex.step, nb + xb + k, f) : 0u;
                     sv[k] = kpack<ST, PDE>(raw[1 + k][f], cf.ref[f], rnd);
                 }
                 es.put(out + (size_t)f * g.fs, g, xb, yo, 0, sv);
@@ -220,13 +220,13 @@ constexpr size_t tbn_smem() {
     return 128 + 128 * ((NW * NSTAGE * 8 + 127) / 128) + (size_t)NW * NSTAGE * 3 * SLOT;
 }
 
-template <int ST, int TT>
-cudaError_t launch_tbn(const LaunchArgs& a) {
+template <int ST, int TT, int SRM>
+cudaError_t launch_tbn_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NW = 4;
     constexpr int NSTAGE = 3;
     constexpr size_t smem = tbn_smem<ST, NW, NSTAGE>();
-    auto kern = k_march2d_tb_nse<ST, TT, NW, NSTAGE>;
+    auto kern = k_march2d_tb_nse<ST, TT, NW, NSTAGE, SRM>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -262,6 +262,15 @@ cudaError_t launch_tbn(const LaunchArgs& a) {
     kern<<<grid, NW * 32, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
                                              nitems, a.err);
     return cudaGetLastError();
+}
+
+// stochastic rounding chosen per launch: BF16 has a kernel without and one with the rounding code
+template <int ST, int TT>
+cudaError_t launch_tbn(const LaunchArgs& a) {
+    if constexpr (ST == ST_BF16) {
+        if (a.ex.sr) return launch_tbn_t<ST, TT, 1>(a);
+    }
+    return launch_tbn_t<ST, TT, 0>(a);
 }
 
 }  // namespace

@@ -28,7 +28,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // The lean NSE variants are held to four CTAs per SM (96 registers): on nse3d_512 FP32 that ran
 // 136 GLUPS against 129 at three CTAs (119 registers).
-template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE>
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE, int SRM = 2>
 __global__ void __launch_bounds__((TY + 1) * 32, LEAN != LEAN_NONE ? 4 : 1) k_march3d(const __grid_constant__ TmapSet maps, Geom g,
                                                            void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                            StepExtra ex, int H, int nitems, int* __restrict__ err,
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__((TY + 1) * 32, LEAN != LEAN_NONE ? 4 : 1) k_ma
                     S sv[4];
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
-                        const unsigned rnd = ex.sr ? sr_bits(ex.seed, ex.step, nb + xb + n, f) : 0u;
+                        const unsigned rnd = sr_on<SRM>(ex) ? sr_bits(ex.seed, ex.step, nb + xb + n, f) : 0u;
                         T v = accP[n][f];
                         if constexpr (SRC != 0) {
                             if (f == 0) v += add[n];
@@ -342,13 +342,13 @@ constexpr int march3d_stages() {
     return n < 2 ? 2 : (n > 8 ? 8 : (int)n);
 }
 
-template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE>
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE, int SRM = 2>
 cudaError_t launch_march3d_t(const LaunchArgs& a) {
     using T = typename Storage<ST>::T;
     constexpr int NF = pde_nf(PDE, LAT);
     constexpr size_t smem = march3d_smem<ST, LEVELS, NF, TY, NSTAGE>();
     constexpr int THREADS = (TY + 1) * 32;
-    auto kern = k_march3d<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC, LEAN>;
+    auto kern = k_march3d<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC, LEAN, SRM>;
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -388,6 +388,15 @@ cudaError_t launch_march3d_t(const LaunchArgs& a) {
     kern<<<grid, THREADS, smem, a.stream>>>(*a.maps, a.g, a.out, *static_cast<const Coef<T>*>(a.coef), a.ex, H,
                                             nitems, a.err, sa);
     return cudaGetLastError();
+}
+
+// The same with the stochastic-rounding choice made per launch (see launch_march2d_sr).
+template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE>
+cudaError_t launch_march3d_sr(const LaunchArgs& a) {
+    if constexpr (ST == ST_BF16) {
+        if (a.ex.sr) return launch_march3d_t<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC, LEAN, 1>(a);
+    }
+    return launch_march3d_t<LAT, PDE, LEVELS, ST, TY, NSTAGE, SRC, LEAN, 0>(a);
 }
 
 }  // namespace mmfd

@@ -9,13 +9,13 @@ namespace {
 
 template <int LEVELS, int ST, int LEAN>
 LaunchFn pick2() {
-    return launch_march2d_t<LAT_D2Q9, PDE_NSE, LEVELS, ST, 4, march2d_stages<LAT_D2Q9, PDE_NSE, LEVELS, ST, 4>(), 4,
+    return launch_march2d_sr<LAT_D2Q9, PDE_NSE, LEVELS, ST, 4, march2d_stages<LAT_D2Q9, PDE_NSE, LEVELS, ST, 4>(), 4,
                             rows_per_stage(PDE_NSE), 0, LEAN>;
 }
 
 template <int LEVELS, int ST, int LEAN>
 LaunchFn pick3() {
-    return launch_march3d_t<LAT_D3Q19, PDE_NSE, LEVELS, ST, tile_rows(PDE_NSE),
+    return launch_march3d_sr<LAT_D3Q19, PDE_NSE, LEVELS, ST, tile_rows(PDE_NSE),
                             march3d_stages<LAT_D3Q19, PDE_NSE, LEVELS, ST>(), 0, LEAN>;
 }
 

@@ -68,6 +68,14 @@ __device__ __forceinline__ typename Storage<ST>::S kpack(typename Storage<ST>::T
     else return Storage<ST>::pack_raw(v, rnd);
 }
 
+// Whether a BF16 store rounds stochastically.  SRM is a kernel's compile-time choice: 0 never, 1
+// always (the launcher picks the instantiation from the step's flag, so the rounding-off kernel
+// carries no hashing code), 2 decided per store from ex.sr.
+template <int SRM>
+__device__ __forceinline__ bool sr_on(const StepExtra& ex) {
+    return SRM == 1 || (SRM == 2 && ex.sr != 0);
+}
+
 // SplitMix64 finaliser as a counter-based hash (stochastic rounding bits).
 __device__ __forceinline__ unsigned sr_bits(unsigned long long seed, long long step, long long node, int f) {
     unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(step * 8 + f + 1) +
