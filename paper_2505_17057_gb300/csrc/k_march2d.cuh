@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
 #pragma unroll
         for (int k = 0; k < LN; ++k)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc0[k][f] = acc1[k][f] = acc2[k][f] = acc3[k][f] = T(0);
+            for (int f = 0; f < NF; ++f) acc0[k][f] = acc1[k][f] = acc2[k][f] = acc3[k][f] = acc_zero<T>();
         for (int i = 0; i < nrows; i += RPS) {
             const int s = cs;
             if constexpr (SRC == 1) src_load(y0, i, xb);
@@ -687,12 +687,12 @@ __global__ void __launch_bounds__(NW * 32) k_march2d(const __grid_constant__ Tma
                     if constexpr (RPS == 1) {
                         acc0[k][f] = acc1[k][f];
                         acc1[k][f] = acc2[k][f];
-                        acc2[k][f] = T(0);
+                        acc2[k][f] = acc_zero<T>();
                     } else {
                         acc0[k][f] = acc2[k][f];
                         acc1[k][f] = acc3[k][f];
-                        acc2[k][f] = T(0);
-                        acc3[k][f] = T(0);
+                        acc2[k][f] = acc_zero<T>();
+                        acc3[k][f] = acc_zero<T>();
                     }
                 }
         }

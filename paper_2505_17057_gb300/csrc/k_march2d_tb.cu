@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
                 raw[1 + k] = accP[t][k];   // row r-1 of level t + 1 is complete
                 accP[t][k] = accC[t][k];
                 accC[t][k] = accN[t][k];
-                accN[t][k] = T(0);
+                accN[t][k] = acc_zero<T>();
             }
             if constexpr (JAC) {
 #pragma unroll
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb(const __grid_constant__ 
 #pragma unroll
         for (int t = 0; t < TT; ++t)
 #pragma unroll
-            for (int k = 0; k < LN; ++k) accP[t][k] = accC[t][k] = accN[t][k] = T(0);
+            for (int k = 0; k < LN; ++k) accP[t][k] = accC[t][k] = accN[t][k] = acc_zero<T>();
         if constexpr (JAC) {
 #pragma unroll
             for (int t = 0; t < TT; ++t) rhs_row(y0 - TT - 1 - t, xb, rwin[t]);

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constan
                     raw[1 + k][f] = accP[t][k][f];   // row r-1 of level t + 1 is complete
                     accP[t][k][f] = accC[t][k][f];
                     accC[t][k][f] = accN[t][k][f];
-                    accN[t][k][f] = T(0);
+                    accN[t][k][f] = acc_zero<T>();
                 }
         }
         const int yo = y0 - 2 * TT + i;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constan
 #pragma unroll
             for (int k = 0; k < LN; ++k)
 #pragma unroll
-                for (int f = 0; f < NF; ++f) accP[t][k][f] = accC[t][k][f] = accN[t][k][f] = T(0);
+                for (int f = 0; f < NF; ++f) accP[t][k][f] = accC[t][k][f] = accN[t][k][f] = acc_zero<T>();
         for (int i = 0; i < nrows; i += RPS) {
             const bool ok = mbar_wait_bounded(&full[cs], cphase);
             if (__any_sync(0xffffffffu, !ok)) {

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__((TY + 1) * 32, LEAN != LEAN_NONE ? 4 : 1) k_ma
 #pragma unroll
         for (int n = 0; n < LN; ++n)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) accP[n][f] = accC[n][f] = accN[n][f] = T(0);
+            for (int f = 0; f < NF; ++f) accP[n][f] = accC[n][f] = accN[n][f] = acc_zero<T>();
         for (int i = 0; i < np; ++i, ++k) {
             const int s = (int)(k % NSTAGE);
             const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / NSTAGE) & 1));
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__((TY + 1) * 32, LEAN != LEAN_NONE ? 4 : 1) k_ma
                 for (int f = 0; f < NF; ++f) {
                     accP[n][f] = accC[n][f];
                     accC[n][f] = accN[n][f];
-                    accN[n][f] = T(0);
+                    accN[n][f] = acc_zero<T>();
                 }
         }
     }

@@ -68,6 +68,14 @@ __device__ __forceinline__ typename Storage<ST>::S kpack(typename Storage<ST>::T
     else return Storage<ST>::pack_raw(v, rnd);
 }
 
+// Starting value of a fresh accumulator: -0 is the additive identity of IEEE arithmetic (-0 + x == x
+// for every x, +0 and -0 included), so the compiler can drop the first addition into it, which it
+// may not do for +0 (+0 + -0 is +0).
+template <typename T>
+__device__ __forceinline__ constexpr T acc_zero() {
+    return T(-0.0);
+}
+
 // Whether a BF16 store rounds stochastically.  SRM is a kernel's compile-time choice: 0 never, 1
 // always (the launcher picks the instantiation from the step's flag, so the rounding-off kernel
 // carries no hashing code), 2 decided per store from ex.sr.
