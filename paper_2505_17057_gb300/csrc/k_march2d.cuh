@@ -226,6 +226,31 @@ __host__ __device__ constexpr int pushed_pairs(int C) {
     return m;
 }
 
+// Pieces of the lean He-Luo node update (Coef::nA) for 2D rows, written once so that every kernel
+// that evaluates them rounds alike: |u|^2, the class base B_k = nU |u|^2 + nA rho, and the even /
+// odd parts of pair P, E = nk (e_p . u)^2 + B_k and O = no (e_p . u).
+// Every piece is rounded as written (rmul / rfma), so a value computed once and used twice rounds
+// as when computed for each use.
+template <typename T>
+__device__ __forceinline__ T lean_u2(T ux, T uy) {
+    return rfma(uy, uy, rmul(ux, ux));
+}
+template <typename T>
+__device__ __forceinline__ T lean_base(const Coef<T>& cf, int l, int k, T U, T rho) {
+    return rfma(cf.nU[l][k], U, rmul(cf.nA[l][k], rho));
+}
+// e_p . u and E_p of pair P
+template <int LAT, int P, typename T>
+__device__ __forceinline__ void lean_e2d(const Coef<T>& cf, int l, T ux, T uy, T base, T& cu, T& E) {
+    cu = edot<LAT, P>(ux, uy, T(0));
+    E = rfma(cf.nk[l][P], rmul(cu, cu), base);
+}
+// The streaming contribution E_p +- O_p = E_p +- no (e_p . u), one fused rounding.
+template <int P, int SIGN, typename T>
+__device__ __forceinline__ T lean_sv2d(const Coef<T>& cf, int l, T cu, T E) {
+    return rfma(SIGN > 0 ? cf.no[l][P] : -cf.no[l][P], cu, E);
+}
+
 // One input node of a 2D row (column C of the lane's window, fields f = rho, ux, uy) in the
 // lean He-Luo form (Coef::nA), pushed into the accumulators of output rows r-1 (P), r (C) and
 // r+1 (N): per node |u|^2 and the class bases, per pair e_p . u, E_p as one FMA on the base and
@@ -239,37 +264,32 @@ __device__ __forceinline__ void lean_push_node2d(const Coef<T>& cf, int l, const
     constexpr bool OWN = C >= 0 && C < LN;
     constexpr int MASK = pushed_pairs<LAT, LN>(C);
     const T rho = f[0], ux = f[1], uy = f[2];
-    const T U = uy * uy + ux * ux;
+    const T U = lean_u2(ux, uy);
     if constexpr (OWN) {
-        accC[C][0] += cf.nc[l][1] * U + cf.nc[l][0] * rho;
-        accC[C][1] += cf.ab0[l] * ux;
-        accC[C][2] += cf.ab0[l] * uy;
+        accC[C][0] = radd(accC[C][0], rfma(cf.nc[l][1], U, rmul(cf.nc[l][0], rho)));
+        accC[C][1] = rfma(cf.ab0[l], ux, accC[C][1]);
+        accC[C][2] = rfma(cf.ab0[l], uy, accC[C][2]);
     }
     constexpr bool AX = (MASK & 3) != 0, DG = (MASK & 12) != 0;
     [[maybe_unused]] T Bk[2];
-    if constexpr (AX) Bk[0] = cf.nU[l][0] * U + cf.nA[l][0] * rho;
-    if constexpr (DG) Bk[1] = cf.nU[l][1] * U + cf.nA[l][1] * rho;
+    if constexpr (AX) Bk[0] = lean_base(cf, l, 0, U, rho);
+    if constexpr (DG) Bk[1] = lean_base(cf, l, 1, U, rho);
     static_for<0, NP>([&](auto pcc) {
         constexpr int P_ = decltype(pcc)::value;
         constexpr int EX = pair_e(LAT, P_, 0), EY = pair_e(LAT, P_, 1);
         constexpr int TP = C - EX, TM = C + EX;
         constexpr bool HP = TP >= 0 && TP < LN, HM = TM >= 0 && TM < LN;
         if constexpr (HP || HM) {
-            const T cu = edot<LAT, P_>(ux, uy, T(0));
-            const T E = cf.nk[l][P_] * (cu * cu) + Bk[pair_class(LAT, P_)];
-            const T O = cf.no[l][P_] * cu;
-            [[maybe_unused]] T sE = T(0), mO = T(0);
-            if constexpr (LEAN == LEAN_GENERAL) {
-                sE = cf.ap[l] * E;
-                mO = cf.abp[l] * O;
-            }
-            if constexpr (HP) {
-                T* acc = EY == 1 ? accP[TP] : accC[TP];
-                lean_push<LAT, LEAN, P_, 1, NF>(acc, cf, l, E, O, sE, mO);
-            }
-            if constexpr (HM) {
-                T* acc = EY == 1 ? accN[TM] : accC[TM];
-                lean_push<LAT, LEAN, P_, -1, NF>(acc, cf, l, E, O, sE, mO);
+            T cu, E;
+            lean_e2d<LAT, P_>(cf, l, ux, uy, Bk[pair_class(LAT, P_)], cu, E);
+            if constexpr (LEAN == LEAN_STREAM) {
+                if constexpr (HP) lean_push_sv<LAT, P_, 1>(EY == 1 ? accP[TP] : accC[TP], cf, l, lean_sv2d<P_, 1>(cf, l, cu, E));
+                if constexpr (HM) lean_push_sv<LAT, P_, -1>(EY == 1 ? accN[TM] : accC[TM], cf, l, lean_sv2d<P_, -1>(cf, l, cu, E));
+            } else {
+                const T O = rmul(cf.no[l][P_], cu);
+                const T sE = cf.ap[l] * E, mO = cf.abp[l] * O;
+                if constexpr (HP) lean_push<LAT, LEAN, P_, 1, NF>(EY == 1 ? accP[TP] : accC[TP], cf, l, E, O, sE, mO);
+                if constexpr (HM) lean_push<LAT, LEAN, P_, -1, NF>(EY == 1 ? accN[TM] : accC[TM], cf, l, E, O, sE, mO);
             }
         }
     });

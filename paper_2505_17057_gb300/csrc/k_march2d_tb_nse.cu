@@ -9,8 +9,11 @@
 // - It keeps TT sets of three accumulator rows of the three fields. An input row is pushed into
 //   level 1 with the node update of the marching kernel (lean_push_node2d); the level-1 row it
 //   completes is pushed into level 2; and so on -- a wavefront of TT steps one row apart.
-// - The x neighbours at the intermediate levels come from the neighbouring lanes by shuffle.
-//   Strips overlap: lanes cover columns X0 .. X0+127 (X0 = 120 s - 8), lanes 1 .. 30 store.
+// - The pushes that cross into a neighbouring lane's columns come from that lane by shuffle, at
+//   every level (tb_push_row), so no lane evaluates a halo node.  Strips overlap: lanes cover
+//   columns X0 .. X0+127 (X0 = 120 s - 8), lanes 1 .. 30 store.  Lanes 0 and 31 receive their
+//   own values in place of the missing neighbours: at level t the first (last) t columns of
+//   lane 0 (31) are wrong, which lane 1 (30) does not read for t < 4.
 // - Columns within TT of the x edges are read from the ghost columns, which every writer keeps
 //   current to the ghost depth.
 // - Intermediate levels stay in FP32 (never stored), so BF16 storage rounds once per TT steps.
@@ -23,6 +26,57 @@ namespace {
 
 constexpr int kTbnStride = 120;   // output columns per strip
 constexpr int kTbnLead = 8;       // lane 0's first column lies kTbnLead columns left of the strip's output
+
+// The lane's LN input nodes of one row at one level, pushed into the accumulators of the output
+// rows r-1 (P), r (C) and r+1 (N).  The pushes that land one column outside the lane's window are
+// not recomputed by the neighbouring lane from a halo node: lane l hands the contributions of its
+// node LN-1 to lane l+1's column 0 and those of its node 0 to lane l-1's column LN-1 by shuffle.
+// Every accumulator still receives its contributions in the order of their input column (the left
+// neighbour's first, the right neighbour's last), with the expressions of lean_push_node2d, so
+// this kernel and the one-step marching kernel round alike.  Lanes 0 and 31 get their own values
+// in place of the missing neighbours; they hold no output.
+template <int LN, typename T>
+__device__ __forceinline__ void tb_push_row(const Coef<T>& cf, const T (&raw)[LN + 2][3], T (&accP)[LN][3],
+                                            T (&accC)[LN][3], T (&accN)[LN][3]) {
+    constexpr int LAT = LAT_D2Q9;
+    constexpr unsigned FULL = 0xffffffffu;
+    {
+        // node LN-1 -> column LN: pair x minus (row r), (1,1) minus (row r+1), (-1,1) plus (row r-1)
+        const T* f = raw[LN];
+        const T U = lean_u2(f[1], f[2]);
+        T c0, E0, c2, E2, c3, E3;
+        lean_e2d<LAT, 0>(cf, 0, f[1], f[2], lean_base(cf, 0, 0, U, f[0]), c0, E0);
+        const T b1 = lean_base(cf, 0, 1, U, f[0]);
+        lean_e2d<LAT, 2>(cf, 0, f[1], f[2], b1, c2, E2);
+        lean_e2d<LAT, 3>(cf, 0, f[1], f[2], b1, c3, E3);
+        const T vC = __shfl_up_sync(FULL, lean_sv2d<0, -1>(cf, 0, c0, E0), 1);
+        const T vN = __shfl_up_sync(FULL, lean_sv2d<2, -1>(cf, 0, c2, E2), 1);
+        const T vP = __shfl_up_sync(FULL, lean_sv2d<3, 1>(cf, 0, c3, E3), 1);
+        lean_push_sv<LAT, 0, -1>(accC[0], cf, 0, vC);
+        lean_push_sv<LAT, 2, -1>(accN[0], cf, 0, vN);
+        lean_push_sv<LAT, 3, 1>(accP[0], cf, 0, vP);
+    }
+    static_for<0, LN>([&](auto cc) {
+        constexpr int C = decltype(cc)::value;
+        lean_push_node2d<LAT, LEAN_STREAM, LN, C>(cf, 0, raw[C + 1], accP, accC, accN);
+    });
+    {
+        // node 0 -> column -1: pair x plus (row r), (1,1) plus (row r-1), (-1,1) minus (row r+1)
+        const T* f = raw[1];
+        const T U = lean_u2(f[1], f[2]);
+        T c0, E0, c2, E2, c3, E3;
+        lean_e2d<LAT, 0>(cf, 0, f[1], f[2], lean_base(cf, 0, 0, U, f[0]), c0, E0);
+        const T b1 = lean_base(cf, 0, 1, U, f[0]);
+        lean_e2d<LAT, 2>(cf, 0, f[1], f[2], b1, c2, E2);
+        lean_e2d<LAT, 3>(cf, 0, f[1], f[2], b1, c3, E3);
+        const T vC = __shfl_down_sync(FULL, lean_sv2d<0, 1>(cf, 0, c0, E0), 1);
+        const T vP = __shfl_down_sync(FULL, lean_sv2d<2, 1>(cf, 0, c2, E2), 1);
+        const T vN = __shfl_down_sync(FULL, lean_sv2d<3, -1>(cf, 0, c3, E3), 1);
+        lean_push_sv<LAT, 0, 1>(accC[LN - 1], cf, 0, vC);
+        lean_push_sv<LAT, 2, 1>(accP[LN - 1], cf, 0, vP);
+        lean_push_sv<LAT, 3, -1>(accN[LN - 1], cf, 0, vN);
+    }
+}
 
 template <int ST, int TT, int NW, int NSTAGE, int SRM>
 __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constant__ TmapSet maps, Geom g,
@@ -45,6 +99,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constan
     constexpr uint32_t kTx = (uint32_t)(NF * RPS * ROWB);
     constexpr size_t kRingBytes = (size_t)NSTAGE * NF * SLOT;
     static_assert(TT >= 2 && TT <= 3, "three fields: at most three levels in registers");
+    static_assert(TT < LN, "the wrong columns of the edge lanes must not reach lanes 1 and 30");
     static_assert(TT <= ALIGN, "ghost columns of 16 bytes hold at most 16 / sizeof(S) levels");
     static_assert(ST == ST_F32 || ST == ST_BF16, "the lean form runs in FP32 arithmetic");
 
@@ -116,17 +171,7 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constan
     auto cascade = [&](T (&raw)[LN + 2][NF], int i, int xb, int y0, int hrows) {
 #pragma unroll
         for (int t = 0; t < TT; ++t) {
-            if (t > 0) {
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    raw[0][f] = __shfl_up_sync(0xffffffffu, raw[LN][f], 1);
-                    raw[LN + 1][f] = __shfl_down_sync(0xffffffffu, raw[1][f], 1);
-                }
-            }
-            static_for<0, LN + 2>([&](auto cc) {
-                constexpr int C = decltype(cc)::value - 1;
-                lean_push_node2d<LAT, LEAN_STREAM, LN, C>(cf, 0, raw[C + 1], accP[t], accC[t], accN[t]);
-            });
+            tb_push_row<LN>(cf, raw, accP[t], accC[t], accN[t]);
 #pragma unroll
             for (int k = 0; k < LN; ++k)
 #pragma unroll
@@ -157,15 +202,12 @@ __global__ void __launch_bounds__(NW * 32) k_march2d_tb_nse(const __grid_constan
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const unsigned char* base = slot(s, f) + (size_t)j * ROWB;
-            const S* sp = reinterpret_cast<const S*>(base);
             T v4[4];
             lds4<ST, PDE>(base + (size_t)(ALIGN + lane * LN) * ES, cf.ref[f], v4);
             raw[1][f] = v4[0];
             raw[2][f] = v4[1];
             raw[3][f] = v4[2];
             raw[4][f] = v4[3];
-            raw[0][f] = kload<ST, PDE>(sp + ALIGN + lane * LN - 1, cf.ref[f]);
-            raw[LN + 1][f] = kload<ST, PDE>(sp + ALIGN + lane * LN + LN, cf.ref[f]);
         }
     };
 

@@ -198,15 +198,39 @@ __device__ __forceinline__ T edot(T ux, T uy, T uz) {
 // General: sE = a+ E and mO = abar+ O (formed once per pair and node), the scalar contribution
 // a- O +- ... and the momentum abar- E +- ... of Eq. (2-4-1) as in the general pair form.
 // acc points at the output node's NF accumulators.
+// Arithmetic with its rounding fixed by the source: one rounding per multiply, add or fused
+// multiply-add, none left to the compiler's choice of contraction.  Kernels that evaluate the same
+// node's contributions in different contexts (a value with one use in one kernel, two in another)
+// then round alike.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Streaming momentum: a contribution sv of pair P in direction SIGN into one output node's
+// accumulators (scalar sv, momentum +-kappa c_a / rho0 times sv).
+template <int LAT, int P, int SIGN, typename T>
+__device__ __forceinline__ void lean_push_sv(T* acc, const Coef<T>& cf, int l, T sv) {
+    constexpr int D = lat_dim(LAT);
+    acc[0] = radd(acc[0], sv);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        if (pair_e(LAT, P, a) != 0) acc[1 + a] = rfma(T(SIGN * pair_e(LAT, P, a)) * cf.nsm[l][a], sv, acc[1 + a]);
+}
+
+// The streaming contribution of pair P in direction SIGN from its even / odd parts.
+template <int SIGN, typename T>
+__device__ __forceinline__ T lean_sv(T E, T O) {
+    return SIGN > 0 ? E + O : E - O;
+}
+
 template <int LAT, int LEAN, int P, int SIGN, int NF, typename T>
 __device__ __forceinline__ void lean_push(T* acc, const Coef<T>& cf, int l, T E, T O, T sE, T mO) {
     constexpr int D = lat_dim(LAT);
     if constexpr (LEAN == LEAN_STREAM) {
-        const T sv = SIGN > 0 ? E + O : E - O;
-        acc[0] += sv;
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            if (pair_e(LAT, P, a) != 0) acc[1 + a] += (T(SIGN * pair_e(LAT, P, a)) * cf.nsm[l][a]) * sv;
+        lean_push_sv<LAT, P, SIGN>(acc, cf, l, lean_sv<SIGN>(E, O));
     } else {
         const T sv = SIGN > 0 ? cf.am[l] * O + sE : sE - cf.am[l] * O;
         const T mv = SIGN > 0 ? cf.abm[l] * E + mO : mO - cf.abm[l] * E;
