@@ -207,6 +207,9 @@ typedef struct {
     long long steps_done;        /* time levels advanced so far */
     char kernel[32];             /* name of the step kernel family in use */
     int sweeps;                  /* theta-scheme: Jacobi sweeps per step (0: explicit scheme) */
+    int tile_rows;               /* 3D marching kernels: rows of the x-y tile a CTA stages per plane
+                                    (16 for the lean NSE kernels on large grids, else 4 or 8); 0 for
+                                    the other kernel families */
 } mmfd_info_t;
 
 typedef struct mmfd_solver mmfd_solver;
@@ -227,10 +230,14 @@ int mmfd_desc_init(mmfd_desc* d);
  * the marching kernels run a lean form of the same update: the uu terms of Eq. (3-3) through
  * |u|^2 and (e_p . u)^2, a+ / a- folded into the pair parts, and, when the momentum set is
  * proportional to the scalar one ((abar-, abar+) = kappa (a+, a-), e.g. LBGK tau = 1), the
- * momentum taken from the scalar contributions (kernel names *_nse_s, else *_nse_g).  Setting
+ * momentum taken from the scalar contributions (kernel names *_nse_s, else *_nse_g).  The 3D lean
+ * kernels stage 16-row tiles at one CTA per SM where the grid has enough of them to fill the GPU
+ * (x strips x 16-row tiles x 32-plane segments >= 256, ny >= 128), 4-row tiles at four CTAs per
+ * SM otherwise; the tile changes only which warp computes a node, not its arithmetic.  Setting
  * the environment variable MMFD_FORCE_KERNEL=direct before mmfd_create selects the direct
- * kernel for any grid, MMFD_FORCE_KERNEL=generic the general pair form (for comparisons; both
- * compute the same update). */
+ * kernel for any grid, MMFD_FORCE_KERNEL=generic the general pair form,
+ * MMFD_FORCE_KERNEL=lean3d_rows16 / lean3d_rows4 the 3D lean tile (for comparisons; all compute
+ * the same update). */
 int mmfd_create(const mmfd_desc* desc, mmfd_solver** out);
 
 /* Copy one level into the solver.  level 0 = t_n, level 1 = t_{n-1} (three-level only).
@@ -362,7 +369,7 @@ int mmfd_wave_coefficients(double gamma, double a[3], double ahat[3]);
  * 2D, planes in 3D, streamed per warp or CTA item; 0 = the launcher's occupancy-based choice).
  * mmfd_autotune times candidate pairs on this solver's own grid -- depths 1 .. the deepest the
  * solver allows when it was created with temporal_depth = 0, else the depth in use; heights 0,
- * 4, 8, 16, 32, 64, 128 (2D) or 0, 8, 16, 32, 64 (3D marching kernels) -- and keeps the fastest for
+ * 4, 8, 16, 32, 64, 128 (2D) or 0, 8, 16, 32, 64, 128 (3D marching kernels) -- and keeps the fastest for
  * later mmfd_step calls.  Trial launches read the current level(s) and write only the spare
  * buffer, so the solver's fields and step count are unchanged; the call synchronises the
  * solver's stream.  Any solver can be tuned, before or after its fields are set.

@@ -26,10 +26,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// The lean NSE variants are held to four CTAs per SM (96 registers): on nse3d_512 FP32 that ran
-// 136 GLUPS against 129 at three CTAs (119 registers).
+// The lean NSE variants with 4-row tiles are held to four CTAs per SM (96 registers): on nse3d_512
+// FP32 that ran 136 GLUPS against 129 at three CTAs (119 registers).  With 16-row tiles a CTA of
+// 17 warps fills the SM on its own.
 template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE, int SRM = 2>
-__global__ void __launch_bounds__((TY + 1) * 32, LEAN != LEAN_NONE ? 4 : 1) k_march3d(const __grid_constant__ TmapSet maps, Geom g,
+__global__ void __launch_bounds__((TY + 1) * 32, (LEAN != LEAN_NONE && TY <= 4) ? 4 : 1) k_march3d(const __grid_constant__ TmapSet maps, Geom g,
                                                            void* __restrict__ outv, Coef<typename Storage<ST>::T> cf,
                                                            StepExtra ex, int H, int nitems, int* __restrict__ err,
                                                            const __grid_constant__ SrcParam<typename Storage<ST>::T, SRC> sa) {
@@ -334,13 +335,22 @@ constexpr size_t march3d_smem() {
 // Rows per CTA tile: 8 for the light linear stencil, 4 where registers are scarce.
 constexpr int tile_rows(int pde) { return pde == PDE_LCDE ? 8 : 4; }
 
-// Ring depth: about 48 KB of stages per CTA, between 2 and 8 planes in flight.
-template <int LAT, int PDE, int LEVELS, int ST>
+// Ring depth: about BUDGET bytes of stages per CTA (48 KB where several CTAs share an SM), between
+// 2 and 8 planes in flight.
+template <int LAT, int PDE, int LEVELS, int ST, int TY = tile_rows(PDE), size_t BUDGET = 49152>
 constexpr int march3d_stages() {
-    constexpr size_t per = march3d_smem<ST, LEVELS, pde_nf(PDE, LAT), tile_rows(PDE), 1>() - 256;
-    constexpr size_t n = 49152 / per;
+    constexpr size_t per = march3d_smem<ST, LEVELS, pde_nf(PDE, LAT), TY, 1>() - 256;
+    constexpr size_t n = BUDGET / per;
     return n < 2 ? 2 : (n > 8 ? 8 : (int)n);
 }
+
+// Tiles of 16 rows for the lean D3Q19 NSE kernels: one CTA of 16 row warps and the producer per
+// SM, its ring given about 200 KB of shared memory.  Streaming the lean step's loads and stores
+// alone (no arithmetic) through such tiles ran at 6.1 TB/s of useful bytes on 512^3, against
+// 4.6 TB/s through 4-row tiles at four CTAs per SM: the y halo rows fall from 1.5x to 1.125x the
+// tile and the SM holds a quarter of the concurrent plane streams.
+constexpr int kLeanWideRows = 16;
+constexpr size_t kLeanWideRing = 200 * 1024;
 
 template <int LAT, int PDE, int LEVELS, int ST, int TY, int NSTAGE, int SRC = 0, int LEAN = LEAN_NONE, int SRM = 2>
 cudaError_t launch_march3d_t(const LaunchArgs& a) {

@@ -65,8 +65,14 @@ LaunchFn find_march3d_src(int lat, int pde, int levels, int st, int src);
 int march3d_tile_rows(int pde);
 // The 2D (D2Q9) and 3D (D3Q19) marching kernels in the lean He-Luo NSE form (lean = LEAN_STREAM
 // or LEAN_GENERAL, see Coef::nA; FP32 / BF16 storage, two or three levels; nullptr elsewhere).
-// They take the same tensor maps and launch arguments as find_march2d / find_march3d.
-LaunchFn find_march_lean(int lat, int levels, int st, int lean);
+// They take the same tensor maps and launch arguments as find_march2d / find_march3d, except that
+// in 3D `rows` picks the CTA tile: march3d_tile_rows(PDE_NSE) rows at four CTAs per SM, or 16 rows
+// at one CTA per SM (tensor-map boxes of rows + 2 rows either way; 2D ignores it).
+LaunchFn find_march_lean(int lat, int levels, int st, int lean, int rows = 4);
+// Tile rows a 3D lean solver of this grid runs with: 16 where the grid has enough 16-row tiles to
+// fill the GPU with one CTA per SM, march3d_tile_rows(PDE_NSE) otherwise; force > 0 asks for the
+// 16-row tiles and force < 0 for the narrow ones whatever the grid (for comparisons).
+int march3d_lean_tile_rows(int nx, int ny, int nz, int force = 0);
 
 // Encode a 2D / 3D tiled TMA descriptor over one field of a ghosted level buffer
 // (box = boxw x 1 [x 1] elements).  Returns 0 on success.

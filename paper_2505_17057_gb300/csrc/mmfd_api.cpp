@@ -181,6 +181,7 @@ int mmfd_describe(const mmfd_desc* desc, mmfd_info_t* out) {
         const bool lean = r->lean != LEAN_NONE && r->st != ST_F64;
         if (r->dim == 2) name = !lean ? "k_march2d" : r->lean == LEAN_STREAM ? "k_march2d_nse_s" : "k_march2d_nse_g";
         else name = !lean ? "k_march3d" : r->lean == LEAN_STREAM ? "k_march3d_nse_s" : "k_march3d_nse_g";
+        if (r->dim == 3) out->tile_rows = lean ? march3d_lean_tile_rows(r->n[0], r->n[1], r->n[2]) : march3d_tile_rows(r->pde);
     }
     std::strncpy(out->kernel, name, sizeof(out->kernel) - 1);
     delete r;
@@ -335,6 +336,7 @@ int mmfd_get_info(const mmfd_solver* h, mmfd_info_t* o) {
     o->temporal_depth = s->depth;
     o->steps_done = s->steps_done;
     std::strncpy(o->kernel, s->kernel_name, sizeof(o->kernel) - 1);
+    o->tile_rows = s->use_tma && s->r.dim == 3 ? s->tile_rows : 0;
     return MMFD_OK;
 }
 

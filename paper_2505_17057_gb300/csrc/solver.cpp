@@ -554,7 +554,13 @@ int solver_pick_kernels(Solver* s) {
     // general pair form, for comparisons; it computes the same update)
     const bool want_generic = force && std::strcmp(force, "generic") == 0;
     const int lean = (!want_generic && !srcv && !s->r.theta_on) ? s->r.lean : LEAN_NONE;
-    LaunchFn fn_lean = lean != LEAN_NONE ? find_march_lean(s->r.lat, s->r.levels, s->r.st, lean) : nullptr;
+    // 3D lean solvers of large grids run 16-row tiles at one CTA per SM (march3d_lean_tile_rows;
+    // MMFD_FORCE_KERNEL=lean3d_rows16 / lean3d_rows4 picks the tile whatever the grid, for
+    // comparisons: both compute every node with the same arithmetic in the same order)
+    const int force_rows = !force ? 0 : std::strcmp(force, "lean3d_rows16") == 0 ? 1 : std::strcmp(force, "lean3d_rows4") == 0 ? -1 : 0;
+    const int lean_rows = s->r.dim == 3 ? march3d_lean_tile_rows(s->g.nx, s->g.ny, s->g.nz, force_rows) : 0;
+    LaunchFn fn_lean =
+        lean != LEAN_NONE ? find_march_lean(s->r.lat, s->r.levels, s->r.st, lean, s->r.dim == 3 ? lean_rows : 4) : nullptr;
     s->lean = fn_lean ? lean : LEAN_NONE;
     if (s->r.dim == 2 && s->g.nx >= 128 && !want_direct) {
         s->fn = fn_lean ? fn_lean
@@ -617,7 +623,8 @@ int solver_pick_kernels(Solver* s) {
         if (s->fn) {
             const int es = s->g.es;
             const int boxw = 128 + 2 * (16 / es);
-            const int rows = march3d_tile_rows(s->r.pde) + 2;
+            s->tile_rows = fn_lean ? lean_rows : march3d_tile_rows(s->r.pde);
+            const int rows = s->tile_rows + 2;
             for (int b = 0; b < s->nlev && s->fn; ++b)
                 for (int f = 0; f < s->g.nf; ++f) {
                     char* base = static_cast<char*>(s->lev[b]) + (size_t)f * s->g.fs * es;

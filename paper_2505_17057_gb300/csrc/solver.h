@@ -33,6 +33,7 @@ struct Solver {
     LaunchFn fn_block = nullptr;                 // temporally blocked kernel (depth > 1)
     int variant = 0;
     const char* kernel_name = "k_direct";
+    int tile_rows = 0;  // 3D marching kernels: rows of the CTA tile (mmfd_info_t::tile_rows)
     int* d_flag = nullptr;                       // device error flag written by kernels
     bool fields_set = false;
     bool use_tma = false;                        // kernel family consumes tensor maps

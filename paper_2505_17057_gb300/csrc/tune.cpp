@@ -85,7 +85,7 @@ int solver_autotune(Solver* s, const char* cache_path, mmfd_tune_info* out) {
     std::vector<int> heights = {0};
     if (s->use_tma) {
         if (s->r.dim == 2) heights.insert(heights.end(), {4, 8, 16, 32, 64, 128});
-        else heights.insert(heights.end(), {8, 16, 32, 64});
+        else heights.insert(heights.end(), {8, 16, 32, 64, 128});
     }
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;

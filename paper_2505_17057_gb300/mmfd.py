@@ -82,7 +82,7 @@ class mmfd_info_t(C.Structure):
         ("c", C.c_double * 3), ("d0", C.c_double * 3), ("cs2", C.c_double * 3), ("w", C.c_double * 19),
         ("Cmat", (C.c_double * 3) * 3), ("m2", C.c_double * 5), ("max_lambda", C.c_double),
         ("bytes_per_lu", C.c_double), ("device_bytes", C.c_longlong), ("temporal_depth", C.c_int),
-        ("steps_done", C.c_longlong), ("kernel", C.c_char * 32), ("sweeps", C.c_int),
+        ("steps_done", C.c_longlong), ("kernel", C.c_char * 32), ("sweeps", C.c_int), ("tile_rows", C.c_int),
     ]
 
 

@@ -137,3 +137,61 @@ def test_lean_d2q9_any_isotropic_d0(mm, mode):
     assert kern == f"k_march2d_nse_{mode}", kern
     ref, _ = orc.run(prob, s0, None, nsteps=3)
     assert G.rel_err(out, ref) < 1e-5, G.rel_err(out, ref)
+
+
+# The 3D lean kernels stage 16-row tiles at one CTA per SM on large grids, 4-row tiles otherwise;
+# MMFD_FORCE_KERNEL picks either on any grid.  Ragged shapes: partial x strips, partial 16-row
+# tiles, one-row and few-plane grids.
+WIDE_SHAPES = [[150, 21, 9], [131, 1, 3], [256, 40, 12], [130, 17, 33]]
+
+
+@pytest.mark.parametrize("mode,levels", [("s", 2), ("g", 2), ("g", 3), ("s", 3)])
+def test_lean3d_wide_tiles_fp32_vs_oracle(mm, mode, levels):
+    rng = np.random.default_rng(hash(("wide", mode, levels)) % (1 << 31))
+    for n in WIDE_SHAPES:
+        kw, prob = case("D3Q19", mode, levels, n, "fp32")
+        L0 = G.random_level(prob, rng)
+        L1 = G.random_level(prob, rng) if levels == 3 else None
+        kern, s0, s1, out = run(mm, kw, L0, L1, force="lean3d_rows16")
+        assert kern == f"k_march3d_nse_{mode}", (kern, n)
+        ref, _ = orc.run(prob, s0, s1, nsteps=3)
+        assert G.rel_err(out, ref) < 1e-5, (n, G.rel_err(out, ref))
+
+
+@pytest.mark.parametrize("mode,levels", [("s", 2), ("g", 3)])
+@pytest.mark.parametrize("sr", [False, True])
+def test_lean3d_wide_tiles_bf16_one_step(mm, mode, levels, sr):
+    rng = np.random.default_rng(91 + levels)
+    n = [140, 37, 7]
+    kw, prob = case("D3Q19", mode, levels, n, "bf16")
+    refs = [1.0] + [0.0] * (prob.nf - 1)
+    L0 = G.random_level(prob, rng)
+    L1 = G.random_level(prob, rng) if levels == 3 else None
+    flags = mm.MMFD_FLAG_STOCHASTIC_ROUND if sr else 0
+    kern, s0, s1, out = run(mm, kw, L0, L1, steps=1, force="lean3d_rows16", flags=flags, ref=refs)
+    assert kern.endswith(f"_nse_{mode}"), kern
+    ref, _ = orc.run(prob, s0, s1, nsteps=1)
+    for f in range(prob.nf):
+        tol = G.bf16_ulp(ref[f] - refs[f]) + 2e-6 * (1 + np.abs(ref[f]))
+        assert np.all(np.abs(out[f] - ref[f]) <= tol), (f, np.abs(out[f] - ref[f]).max())
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_lean3d_wide_tiles_match_narrow(mm, storage):
+    # the tile decides which warp computes a node, not the node's arithmetic: the two agree to
+    # FP32 rounding over five steps (BF16: one step, within one bf16 ulp of the stored offset)
+    rng = np.random.default_rng(5)
+    n = [300, 37, 11]
+    kw, prob = case("D3Q19", "s", 2, n, storage)
+    extra = dict(ref=[1.0, 0.0, 0.0, 0.0]) if storage == "bf16" else {}
+    L0 = G.random_level(prob, rng)
+    steps = 5 if storage == "fp32" else 1
+    _, _, _, a = run(mm, kw, L0, steps=steps, force="lean3d_rows16", **extra)
+    _, _, _, b = run(mm, kw, L0, steps=steps, force="lean3d_rows4", **extra)
+    if storage == "fp32":
+        assert G.rel_err(a, b) < 1e-6, G.rel_err(a, b)
+    else:
+        for f in range(prob.nf):
+            r = extra["ref"][f]
+            tol = G.bf16_ulp(np.maximum(np.abs(a[f] - r), np.abs(b[f] - r)))
+            assert np.all(np.abs(a[f] - b[f]) <= tol), (f, np.abs(a[f] - b[f]).max())

@@ -51,3 +51,28 @@ def test_other_pdes_use_the_general_kernels():
                   targets=[0, -1, -1, 0, 0.5]) == "k_march2d"
     assert kernel("D3Q19", 2, [128, 8, 8], pde="NCDE", flux=[[0, 0.05, 0.1, 0]] * 3, diff=[0.15, 0, 0.05, 0],
                   a=(0.95, 0.1, -0.05)) == "k_march3d"
+
+
+def info(lat, levels, n, storage="fp32", pde="NSE", **co):
+    dim = len(n)
+    kw = dict(pde=pde, lattice=lat, levels=levels, n=n, dt=1.0, dx=[1.0] * dim, storage=storage, **co)
+    if pde == "NSE":
+        kw["flags"] = mmfd.MMFD_FLAG_ALLOW_UNSTABLE
+    return mmfd.mmfd_describe(mmfd.make_desc(**kw))
+
+
+def test_3d_lean_tile_rows():
+    # 16-row tiles at one CTA per SM where the grid has enough of them (x strips x 16-row tiles x
+    # 32-plane segments >= 256, ny >= 128), 4-row tiles at four CTAs per SM otherwise
+    assert info("D3Q19", 2, [512, 512, 512], **LBGK).tile_rows == 16
+    assert info("D3Q19", 2, [512, 512, 512], storage="bf16", **LBGK).tile_rows == 16
+    assert info("D3Q19", 3, [384, 384, 384], **THREE).tile_rows == 16
+    assert info("D3Q19", 2, [256, 256, 256], **GEN).tile_rows == 16
+    assert info("D3Q19", 2, [128, 128, 128], **LBGK).tile_rows == 4
+    assert info("D3Q19", 2, [512, 64, 512], **LBGK).tile_rows == 4      # ny < 128
+    assert info("D3Q19", 2, [256, 256, 16], **LBGK).tile_rows == 4      # too few planes
+    # the general pair form, FP64 storage and the scalar PDEs keep their tiles; 2D reports none
+    assert info("D3Q19", 2, [512, 512, 512], storage="fp64", **LBGK).tile_rows == 4
+    assert info("D3Q7", 2, [256, 256, 256], pde="LCDE", K=[[0.01, 0, 0], [0, 0.01, 0], [0, 0, 0.01]],
+                u=[0.01, 0.0, 0.0], targets=[0, -1, -1, 0, 0.5]).tile_rows == 8
+    assert info("D2Q9", 2, [4096, 4096], **LBGK).tile_rows == 0
