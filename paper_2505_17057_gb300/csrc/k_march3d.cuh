@@ -62,9 +62,32 @@ __global__ void __launch_bounds__((TY + 1) * 32, (LEAN != LEAN_NONE && TY <= 4) 
     const int lane = threadIdx.x & 31;
     const int xs = (g.nx + COLS - 1) / COLS;       // x strips
     const int ys = (g.ny + TY - 1) / TY;           // y tiles
-    auto item_planes = [&](int item) {
-        const int zseg = item / (xs * ys);
-        return min(H, g.nz - zseg * H) + 2;
+    // This CTA's segments (tile, planes z0 .. z0 + nzs - 1), each streamed with one halo plane on
+    // either side: items of H planes dealt round-robin (H > 0), or one balanced range of the
+    // (tile, plane) pairs, tile-major (H < 0).  Producer and consumers walk the same sequence.
+    const long long tiles = (long long)xs * ys;
+    int item = blockIdx.x;
+    long long w = 0, whi = 0;
+    if (H < 0) {
+        const long long total = tiles * g.nz;
+        w = total * blockIdx.x / gridDim.x;
+        whi = total * (blockIdx.x + 1) / gridDim.x;
+    }
+    auto next_seg = [&](int& tile, int& z0, int& nzs) -> bool {
+        if (H > 0) {
+            if (item >= nitems) return false;
+            tile = (int)(item % tiles);
+            z0 = (int)(item / tiles) * H;
+            nzs = min(H, g.nz - z0);
+            item += gridDim.x;
+            return true;
+        }
+        if (w >= whi) return false;
+        tile = (int)(w / g.nz);
+        z0 = (int)(w % g.nz);
+        nzs = (int)min((long long)(g.nz - z0), whi - w);
+        w += nzs;
+        return true;
     };
 
     if (threadIdx.x == 0) {
@@ -84,11 +107,11 @@ __global__ void __launch_bounds__((TY + 1) * 32, (LEAN != LEAN_NONE && TY <= 4) 
         if (lane != 0) return;
         long long k = 0;
         bool failed = false;
-        for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
-            const int xcol = (item % xs) * COLS;
-            const int yrow = ((item / xs) % ys) * TY;      // padded row of interior y0 - 1
-            const int z0 = (item / (xs * ys)) * H;
-            const int np = item_planes(item);
+        int tile = 0, z0 = 0, nzs = 0;
+        while (!failed && next_seg(tile, z0, nzs)) {
+            const int xcol = (tile % xs) * COLS;
+            const int yrow = (tile / xs) * TY;      // padded row of interior y0 - 1
+            const int np = nzs + 2;
             for (int i = 0; i < np; ++i, ++k) {
                 const int s = (int)(k % NSTAGE);
                 if (!mbar_wait_bounded(&empty[s], (uint32_t)(((k / NSTAGE) & 1) ^ 1))) {
@@ -114,11 +137,11 @@ __global__ void __launch_bounds__((TY + 1) * 32, (LEAN != LEAN_NONE && TY <= 4) 
     S* out = static_cast<S*>(outv);
     long long k = 0;
     bool failed = false;
-    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
-        const int x0 = (item % xs) * COLS;
-        const int y0 = ((item / xs) % ys) * TY;
-        const int z0 = (item / (xs * ys)) * H;
-        const int np = item_planes(item);
+    int tile = 0, z0 = 0, nzs = 0;
+    while (!failed && next_seg(tile, z0, nzs)) {
+        const int x0 = (tile % xs) * COLS;
+        const int y0 = (tile / xs) * TY;
+        const int np = nzs + 2;
         const int xb = x0 + lane * LN;
         es.init(g, xb, true);
         const int y = y0 + warp;
@@ -373,7 +396,19 @@ cudaError_t launch_march3d_t(const LaunchArgs& a) {
     const int xs = (a.g.nx + 127) / 128;
     const int ys = (a.g.ny + TY - 1) / TY;
     int H = a.H;
-    if (H <= 0) {
+    int nitems = 0, grid = 0;
+    if (H <= 0 && TY == kLeanWideRows && ST == ST_BF16) {
+        // 16-row BF16 tiles, one CTA per SM: each CTA streams one balanced range of the (tile,
+        // plane) pairs, so every SM gets the same work and a tile's halo planes are read once per
+        // range.  nse3d_512: 136 GLUPS against 128 with items of 64 planes.  The BF16 step is bound
+        // by instruction issue; the FP32 step is not, and there the ranges cost more than they
+        // save (106 against 136 GLUPS): CTAs at unrelated planes share no halo rows or TMA
+        // segments in L2, and the reads rose to 3.4x the level (384^3 capture).
+        const long long total = (long long)xs * ys * a.g.nz;
+        H = -1;
+        grid = (int)(total < resident ? total : resident);
+        nitems = grid;
+    } else if (H <= 0) {
         double best = -1.0;
         for (int h = 4; h <= 512; ++h) {
             const long long items = (long long)xs * ys * ((a.g.nz + h - 1) / h);
@@ -387,8 +422,10 @@ cudaError_t launch_march3d_t(const LaunchArgs& a) {
             if (h >= a.g.nz) break;
         }
     }
-    const int nitems = xs * ys * ((a.g.nz + H - 1) / H);
-    const int grid = nitems < resident ? nitems : resident;
+    if (H > 0) {
+        nitems = xs * ys * ((a.g.nz + H - 1) / H);
+        grid = nitems < resident ? nitems : resident;
+    }
     SrcParam<T, SRC> sa{};
     if constexpr (SRC != 0) {
         sa.s[0] = static_cast<const T*>(a.src[0]);

@@ -76,7 +76,11 @@ int march3d_lean_tile_rows(int nx, int ny, int nz, int force = 0);
 
 // Encode a 2D / 3D tiled TMA descriptor over one field of a ghosted level buffer
 // (box = boxw x 1 [x 1] elements).  Returns 0 on success.
-int encode_field_map(CUtensorMap* m, void* field_base, int st, const Geom& g, int boxw, int boxh, int boxd);
+// promote_l2 = false: no L2 promotion of the box's requests (only the box's own sectors are
+// fetched), for kernels whose neighbouring CTAs do not read the surrounding bytes at about the
+// same time.
+int encode_field_map(CUtensorMap* m, void* field_base, int st, const Geom& g, int boxw, int boxh, int boxd,
+                     bool promote_l2 = true);
 
 // Utility kernels (k_util.cu).
 // Rows r (r = y + z ny) in [r_lo, r_hi) only (r_hi < 0: every row); the dense buffer holds those
