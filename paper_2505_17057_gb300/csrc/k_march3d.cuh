@@ -63,15 +63,20 @@ __global__ void __launch_bounds__((TY + 1) * 32, (LEAN != LEAN_NONE && TY <= 4) 
     const int xs = (g.nx + COLS - 1) / COLS;       // x strips
     const int ys = (g.ny + TY - 1) / TY;           // y tiles
     // This CTA's segments (tile, planes z0 .. z0 + nzs - 1), each streamed with one halo plane on
-    // either side: items of H planes dealt round-robin (H > 0), or one balanced range of the
-    // (tile, plane) pairs, tile-major (H < 0).  Producer and consumers walk the same sequence.
+    // either side: items of H planes dealt round-robin (H > 0), or (H < 0) one balanced range of
+    // the (y tile, plane) pairs, y-tile-major, per group of xs CTAs: the CTAs of a group take the
+    // xs strips of the same range, so the strips of a row advance plane by plane together and
+    // meet each other's halo columns in L2 (gridDim.x is a multiple of xs then).  Producer and
+    // consumers walk the same sequence.
     const long long tiles = (long long)xs * ys;
     int item = blockIdx.x;
     long long w = 0, whi = 0;
+    const int strip = blockIdx.x % xs;
     if (H < 0) {
-        const long long total = tiles * g.nz;
-        w = total * blockIdx.x / gridDim.x;
-        whi = total * (blockIdx.x + 1) / gridDim.x;
+        const long long total = (long long)ys * g.nz;
+        const long long groups = gridDim.x / xs, grp = blockIdx.x / xs;
+        w = total * grp / groups;
+        whi = total * (grp + 1) / groups;
     }
     auto next_seg = [&](int& tile, int& z0, int& nzs) -> bool {
         if (H > 0) {
@@ -83,7 +88,7 @@ __global__ void __launch_bounds__((TY + 1) * 32, (LEAN != LEAN_NONE && TY <= 4) 
             return true;
         }
         if (w >= whi) return false;
-        tile = (int)(w / g.nz);
+        tile = (int)(w / g.nz) * xs + strip;
         z0 = (int)(w % g.nz);
         nzs = (int)min((long long)(g.nz - z0), whi - w);
         w += nzs;
@@ -398,15 +403,17 @@ cudaError_t launch_march3d_t(const LaunchArgs& a) {
     int H = a.H;
     int nitems = 0, grid = 0;
     if (H <= 0 && TY == kLeanWideRows && ST == ST_BF16) {
-        // 16-row BF16 tiles, one CTA per SM: each CTA streams one balanced range of the (tile,
-        // plane) pairs, so every SM gets the same work and a tile's halo planes are read once per
-        // range.  nse3d_512: 136 GLUPS against 128 with items of 64 planes.  The BF16 step is bound
-        // by instruction issue; the FP32 step is not, and there the ranges cost more than they
-        // save (106 against 136 GLUPS): CTAs at unrelated planes share no halo rows or TMA
-        // segments in L2, and the reads rose to 3.4x the level (384^3 capture).
-        const long long total = (long long)xs * ys * a.g.nz;
+        // 16-row BF16 tiles, one CTA per SM: each group of xs CTAs streams one balanced range of the
+        // (y tile, plane) pairs, so every SM gets the same work and a tile's halo planes are read
+        // once per range.  nse3d_512: 135-136 GLUPS against 128 with items of 64 planes; DRAM
+        // reads 1.26x the level (384^3 capture), 1.9x when the strips of a row did not share a
+        // range.  The BF16 step is bound by instruction issue; the FP32 step is not, and there
+        // items of planes stay faster (135 against 132 GLUPS with the ranges): neighbouring y
+        // tiles' ranges sit at unrelated planes and no longer meet each other's halo rows in L2.
+        const long long total = (long long)ys * a.g.nz;     // (y tile, plane) pairs per strip
+        const long long groups = resident >= xs ? resident / xs : 1;
         H = -1;
-        grid = (int)(total < resident ? total : resident);
+        grid = (int)(total < groups ? total : groups) * xs;
         nitems = grid;
     } else if (H <= 0) {
         double best = -1.0;

@@ -625,8 +625,9 @@ int solver_pick_kernels(Solver* s) {
             const int boxw = 128 + 2 * (16 / es);
             s->tile_rows = fn_lean ? lean_rows : march3d_tile_rows(s->r.pde);
             const int rows = s->tile_rows + 2;
-            // the 16-row BF16 kernel streams balanced per-CTA ranges (k_march3d.cuh): its CTAs sit
-            // at unrelated planes, so L2 promotion would fetch bytes no neighbour reads in time
+            // the 16-row BF16 kernel streams balanced per-group ranges (k_march3d.cuh): neighbouring
+            // y tiles sit at unrelated planes, so L2 promotion would fetch bytes no neighbour reads
+            // in time
             const bool promote = !(fn_lean && s->tile_rows > march3d_tile_rows(s->r.pde) && s->r.st == ST_BF16);
             for (int b = 0; b < s->nlev && s->fn; ++b)
                 for (int f = 0; f < s->g.nf; ++f) {
