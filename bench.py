@@ -121,6 +121,48 @@ def traffic_from_profile(kernel: str, workload: str, depth: int = 1, sweeps: int
     return e.get("dram_bytes_per_launch")
 
 
+def e2e_two_streams(mmfd, desc_kw, s0, fields, host_ptrs, back_ptrs, steps, nodes):
+    """The end-to-end job (upload the level from page-locked host memory, advance it one step,
+    read the stepped level back into page-locked host memory) on two solvers, each on its own
+    stream and driven by its own host thread, so that one job's upload overlaps the other's
+    read-back over the host link (the read-back call is synchronous).  Returns the aggregate MLUPS
+    of both and the per-job bytes."""
+    import threading
+    import torch
+    s1 = mmfd.Solver(mmfd.make_desc(**desc_kw), stream=torch.cuda.Stream())
+    try:
+        s1.set_fields(fields)
+        back1 = [torch.empty(tuple(f.shape), dtype=torch.float32).pin_memory() for f in fields]
+        jobs = [(s0, back_ptrs), (s1, [b.data_ptr() for b in back1])]
+
+        def job(sv, back):
+            mmfd.mmfd_set_fields(sv.h, 0, host_ptrs, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
+            sv.step(1)
+            mmfd.mmfd_fields(sv.h, 0, back, mmfd.MMFD_HOST, mmfd.MMFD_DT_F32)
+
+        for sv, back in jobs:   # warm both solvers (first-launch set-up happens here, one thread)
+            job(sv, back)
+        torch.cuda.synchronize()
+
+        def worker(sv, back):
+            for _ in range(steps):
+                job(sv, back)
+
+        threads = [threading.Thread(target=worker, args=j) for j in jobs]
+        t0 = time.perf_counter()
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+    finally:
+        s1.close()
+    return {"value": 2 * steps * nodes / secs / 1e6, "unit": UNIT, "jobs": 2 * steps,
+            "how": "two solvers on two streams, one host thread each; every job uploads the level, "
+                   "steps it once and reads the stepped level back (FP32, page-locked host memory)"}
+
+
 class ClockSampler:
     def __init__(self, device_index: int):
         self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -702,6 +744,9 @@ def run_ours(args):
         e2e_value = e2e_run(True)
         d2h = sum(b.numel() * 4 for b in back)
         e2e_sums_value = e2e_run(False)
+        e2e_pipe = None
+        if not has_src and ws == 1:
+            e2e_pipe = e2e_two_streams(mmfd, desc_kw, s, fields, host_ptrs, back_ptrs, e2e_steps, nodes)
         s.close()
 
         # the plain one-step-per-launch kernel on the same workload, when the headline launch
@@ -769,6 +814,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps, "read_back": "the stepped level, FP32, into page-locked host memory",
+                **({"two_streams": e2e_pipe} if e2e_pipe else {}),
                 "sums_only": {"value": e2e_sums_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                               "d2h_bytes_per_step": 8 * len(pinned),
                               "read_back": "the FP64 field sums of the stepped level"}},
