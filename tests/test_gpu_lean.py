@@ -195,3 +195,24 @@ def test_lean3d_wide_tiles_match_narrow(mm, storage):
             r = extra["ref"][f]
             tol = G.bf16_ulp(np.maximum(np.abs(a[f] - r), np.abs(b[f] - r)))
             assert np.all(np.abs(a[f] - b[f]) <= tol), (f, np.abs(a[f] - b[f]).max())
+
+
+def test_lean3d_wide_bf16_ranges_crossing_tiles(mm):
+    # 16-row BF16 tiles stream balanced ranges of (y tile, plane) pairs per group of strip CTAs;
+    # on 300 x 50 x 120 (ragged strips and tiles) the ranges hold 9-10 planes and six of them run
+    # from one y tile into the next.  One step against the oracle (one bf16 ulp) and against the
+    # 4-row tiles (items of planes).
+    rng = np.random.default_rng(404)
+    n = [300, 50, 120]
+    kw, prob = case("D3Q19", "s", 2, n, "bf16")
+    refs = [1.0, 0.0, 0.0, 0.0]
+    L0 = G.random_level(prob, rng)
+    kern, s0, _, a = run(mm, kw, L0, steps=1, force="lean3d_rows16", ref=refs)
+    assert kern == "k_march3d_nse_s", kern
+    _, _, _, b = run(mm, kw, L0, steps=1, force="lean3d_rows4", ref=refs)
+    ref, _ = orc.run(prob, s0, None, nsteps=1)
+    for f in range(prob.nf):
+        tol = G.bf16_ulp(ref[f] - refs[f]) + 2e-6 * (1 + np.abs(ref[f]))
+        assert np.all(np.abs(a[f] - ref[f]) <= tol), (f, np.abs(a[f] - ref[f]).max())
+        tab = G.bf16_ulp(np.maximum(np.abs(a[f] - refs[f]), np.abs(b[f] - refs[f])))
+        assert np.all(np.abs(a[f] - b[f]) <= tab), (f, np.abs(a[f] - b[f]).max())
