@@ -5,7 +5,8 @@ corner and samples of every edge row/column (and face) -- and, for the temporall
 path, with the unblocked GPU path on the whole grid (a property that holds at any size).
 
 Tolerance: FP32 storage, 1e-5 relative to the field's max |value| (one step from the
-FP32-rounded initial state, which is what the oracle is given).
+FP32-rounded initial state, which is what the oracle is given); BF16-offset storage, one bf16
+ulp of the stored offset (one step from the BF16-rounded state).
 """
 import numpy as np
 import pytest
@@ -158,3 +159,30 @@ def test_more_than_2_31_nodes(mm, lat, n):
     ph = theta[0] * xs + theta[1] * ys + (theta[2] * (idx // plane) if dim == 3 else 0.0)
     ref = np.abs(lam) * np.cos(ph + np.angle(lam))
     assert np.abs(got - ref).max() < 2e-6, np.abs(got - ref).max()
+
+
+def bf16_ulp(x):
+    """Spacing of bf16 numbers at |x| (8 significand bits)."""
+    ax = np.maximum(np.abs(x), 1e-38)
+    return 2.0 ** (np.floor(np.log2(ax)) - 7)
+
+
+@pytest.mark.parametrize("name,maker,n,kernel", [FULL[0], FULL[3]], ids=["tgv2d", "nse3d"])
+def test_full_size_bf16_one_step_matches_oracle_on_samples(mm, name, maker, n, kernel):
+    # BF16-offset storage at the bench sizes, in the bench's launch configuration (on nse3d_512
+    # the 16-row tiles with balanced per-group ranges, several of which run across y tiles):
+    # within one bf16 ulp of the stored offset of the oracle's step from the stored state
+    kw, fields, _ = maker(n=n, storage="bf16")
+    info, stored, out = solve_one(mm, kw, fields, 1, 1)
+    assert info.kernel.decode() == kernel
+    if name == "nse3d":
+        assert info.tile_rows == 16
+    prob = oracle_problem(kw)
+    rng = np.random.default_rng(4321)
+    nodes = sample_nodes(stored[0].shape, rng)
+    ref = orc.step_nodes(prob, stored, None, nodes)
+    refs = kw["ref"]
+    for f in range(len(out)):
+        got = out[f].reshape(-1)[nodes]
+        tol = bf16_ulp(ref[:, f] - refs[f]) + 2e-6 * (1 + np.abs(ref[:, f]))
+        assert np.all(np.abs(got - ref[:, f]) <= tol), (name, f, np.abs(got - ref[:, f]).max())
