@@ -163,6 +163,19 @@ def e2e_two_streams(mmfd, desc_kw, s0, fields, host_ptrs, back_ptrs, steps, node
                    "steps it once and reads the stepped level back (FP32, page-locked host memory)"}
 
 
+CLOCK_WINDOW_S = 1.0   # untimed launches after a timed region, so that the clock record sees the load
+
+
+def clock_window(step_fn, ms_per_call):
+    """Keep the GPU on the timed region's launches for about CLOCK_WINDOW_S after it (untimed),
+    so that the clock samples, taken every 200 ms, see this load even when the timed region is
+    shorter than one sampling interval."""
+    import torch
+    calls = max(1, int(CLOCK_WINDOW_S * 1e3 / max(ms_per_call, 1e-3)))
+    step_fn(calls)
+    torch.cuda.synchronize()
+
+
 class ClockSampler:
     def __init__(self, device_index: int):
         self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -176,6 +189,12 @@ class ClockSampler:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # wait (at most 3 s) for the first sample, so that sampling is live when the timed region
+        # starts
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and os.path.getsize(self.fh.name) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -542,8 +561,17 @@ def run_split(args):
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        clocks = sampler.stop()
         total_ms = max_over_ranks(t0.elapsed_time(t1), "cuda")
+
+        def more_steps(k):
+            for _ in range(k):
+                step()
+
+        # every rank runs the same number of exchange steps (the count comes from the max over ranks)
+        clock_window(more_steps, total_ms / args.steps)
+        barrier()
+        clocks = sampler.stop()
+        clocks["window"] = f"the timed region and about {CLOCK_WINDOW_S:.0f} s of the same steps after it (untimed)"
         nodes_all = int(np.prod(desc_kw["n"]))
         value = nodes_all * args.steps / (total_ms / 1e3) / 1e6
         s.close()
@@ -658,8 +686,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        clocks = sampler.stop()
         total_ms = t_start.elapsed_time(t_end)
+        clock_window(lambda k: s.step(k * depth), total_ms / args.steps)
+        clocks = sampler.stop()
+        clocks["window"] = f"the timed region and about {CLOCK_WINDOW_S:.0f} s of the same launches after it (untimed)"
         launch_ms = [a.elapsed_time(b) for a, b in ev] if ev is not None else [t_start.elapsed_time(t_end) / args.steps]
         total_ms = max_over_ranks(total_ms, "cuda")
         steps_done = args.steps * depth
