@@ -144,9 +144,14 @@ def e2e_two_streams(mmfd, desc_kw, s0, fields, host_ptrs, back_ptrs, steps, node
             job(sv, back)
         torch.cuda.synchronize()
 
+        errors = []
+
         def worker(sv, back):
-            for _ in range(steps):
-                job(sv, back)
+            try:
+                for _ in range(steps):
+                    job(sv, back)
+            except Exception as e:   # reported after the join: a failed job voids the figure
+                errors.append(e)
 
         threads = [threading.Thread(target=worker, args=j) for j in jobs]
         t0 = time.perf_counter()
@@ -156,6 +161,8 @@ def e2e_two_streams(mmfd, desc_kw, s0, fields, host_ptrs, back_ptrs, steps, node
             t.join()
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
+        if errors:
+            raise errors[0]
     finally:
         s1.close()
     return {"value": 2 * steps * nodes / secs / 1e6, "unit": UNIT, "jobs": 2 * steps,
