@@ -173,13 +173,27 @@ def e2e_two_streams(mmfd, desc_kw, s0, fields, host_ptrs, back_ptrs, steps, node
 CLOCK_WINDOW_S = 1.0   # untimed launches after a timed region, so that the clock record sees the load
 
 
+def l2_note(device_bytes: float, levels: int):
+    """The config's statement about L2 and the roofline's bound: levels larger than the L2 are
+    streamed from HBM each step (no flush needed); levels that fit are L2-resident, reported in
+    MLUPS only."""
+    if device_bytes > L2_BYTES:
+        return f"inputs larger than L2 ({device_bytes / levels / 1e6:.0f} MB per level), no flush", "hbm"
+    return (f"L2-resident ({device_bytes / 1e6:.0f} MB of levels in the {L2_BYTES / 1e6:.0f} MB L2): "
+            "MLUPS only, the HBM roofline does not bound it", "l2-resident")
+
+
+def clock_window_calls(ms_per_call: float) -> int:
+    """Calls of the timed region's launch group that fill about CLOCK_WINDOW_S."""
+    return max(1, int(CLOCK_WINDOW_S * 1e3 / max(ms_per_call, 1e-3)))
+
+
 def clock_window(step_fn, ms_per_call):
     """Keep the GPU on the timed region's launches for about CLOCK_WINDOW_S after it (untimed),
     so that the clock samples, taken every 200 ms, see this load even when the timed region is
     shorter than one sampling interval."""
     import torch
-    calls = max(1, int(CLOCK_WINDOW_S * 1e3 / max(ms_per_call, 1e-3)))
-    step_fn(calls)
+    step_fn(clock_window_calls(ms_per_call))
     torch.cuda.synchronize()
 
 
@@ -834,11 +848,8 @@ def run_ours(args):
                        "sweeps_per_launch": jd} if theta else {}),
                    "autotuned": tuned,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "l2": (f"inputs larger than L2 ({info.device_bytes / info.levels_stored / 1e6:.0f} MB per level), no flush"
-                          if info.device_bytes > L2_BYTES else
-                          f"L2-resident ({info.device_bytes / 1e6:.0f} MB of levels in the {L2_BYTES / 1e6:.0f} MB L2): "
-                          "MLUPS only, the HBM roofline does not bound it")},
-        "roofline": {"bound": "hbm" if info.device_bytes > L2_BYTES else "l2-resident", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                   "l2": l2_note(info.device_bytes, info.levels_stored)[0]},
+        "roofline": {"bound": l2_note(info.device_bytes, info.levels_stored)[1], "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "kernel": theta_launches if theta else kernel_name,

@@ -54,3 +54,14 @@ def test_traffic_is_null_once_a_source_changes(monkeypatch):
 @pytest.mark.parametrize("ranks,nodes,steps,seconds,want", [(1, 100, 10, 1.0, 1e-3), (4, 100, 10, 2.0, 2e-3)])
 def test_job_mlups_counts_every_rank(ranks, nodes, steps, seconds, want):
     assert bench.job_mlups(ranks, nodes, steps, seconds) == pytest.approx(want)
+
+
+def test_l2_note_and_clock_window():
+    import bench
+    note, bound = bench.l2_note(2 * 201_326_592, 2)      # tgv2d_4096 FP32: two 201 MB levels
+    assert bound == "hbm" and "larger than L2" in note and "201 MB per level" in note
+    note, bound = bench.l2_note(3 * 4_300_000, 3)        # ncde2d_1024: three 4 MB levels
+    assert bound == "l2-resident" and note.startswith("L2-resident")
+    assert bench.clock_window_calls(0.1364) == 7331      # about one second of 0.136 ms launches
+    assert bench.clock_window_calls(5000.0) == 1         # at least one call
+    assert bench.clock_window_calls(0.0) == 1_000_000    # no division by zero
